@@ -1,0 +1,168 @@
+/* fastresolve: GB300-native measurement operator of fast-resolve (arXiv 2406.09144).
+ *
+ * C ABI of libfastresolve.so. Every entry point is extern "C", takes plain pointers and sizes,
+ * and returns 0 on success or a negative FR_E* code; fr_last_error() then gives a message
+ * (thread-local). All compute runs in the library's own CUDA kernels for sm_103a; there is no
+ * CPU fallback.
+ *
+ * Operators (paper sections and equations):
+ *   R          Eq. (rime), Sec. 2: sky -> visibilities, scalar gains G = 1,
+ *              V_k = sum_j I_j / n_j exp(-2 pi i (u_k l_j + v_k m_j + w_k (n_j - 1)))
+ *   R^dag N^-1 Eq. (clean), Sec. 3.2: weighted back-projection (dirty image), N^-1 = weights
+ *              (Sec. 3.1.2), the adjoint of R under the real inner product (the sky is real)
+ *   PSF *      Sec. 3.3.2: R^dag N^-1 R ~ convolution with the PSF, evaluated exactly (linear,
+ *              not circular) by zero padding to 2nx x 2ny
+ *   likelihood Eq. (ham) expanded with Eq. (clean): L(s) = 1/2 s^T (PSF * s) - s^T d,
+ *              grad = PSF * s - d; the exact variant uses R^dag N^-1 R (Algorithm 1 major cycle)
+ *
+ * Conventions:
+ *   - sky images are float32 [nsky][nx][ny], row-major, y fastest; pixel (jx, jy) sits at
+ *     l = (jx - nx/2) * pixsize_x, m = (jy - ny/2) * pixsize_y;
+ *   - nsky = nchan (one image per channel) by default, nsky = 1 with FR_MFS (one image for all
+ *     channels; R^dag sums channels);
+ *   - visibilities are complex64 [nrow][nchan] (fr_cf32), weights float32 [nrow][nchan];
+ *   - uvw are metres, freqs Hz; u, v, w in wavelengths are uvw * nu / c, c = 299792458 m/s,
+ *     scaled in FP64.
+ *
+ * Ownership: fr_plan_create copies its host inputs; the plan owns all device-resident data
+ * (sorted visibility coordinates, permutation, correction tables, PSF and its transfer
+ * function) and per-stream workspaces. Every other pointer argument is a caller-owned DEVICE
+ * buffer (e.g. torch.Tensor.data_ptr()), contiguous, in the layout stated; the library never
+ * frees it. Host outputs are marked "host". Calls are asynchronous on `stream` (a cudaStream_t,
+ * NULL = legacy default stream) unless they return host values, in which case they synchronise
+ * that stream before returning. A plan is immutable after creation; calls on one plan from
+ * different host threads must use different streams.
+ */
+#ifndef FASTRESOLVE_H
+#define FASTRESOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fr_plan *fr_plan_t;
+typedef struct {
+  float re, im;
+} fr_cf32;
+
+/* return codes */
+#define FR_OK 0
+#define FR_EINVAL (-1)        /* bad argument: size, null pointer, NaN/Inf coordinate, uv outside the grid */
+#define FR_ENOMEM (-2)        /* device or host allocation failed */
+#define FR_ECUDA (-3)         /* a CUDA runtime/driver call failed */
+#define FR_EUNSUPPORTED (-4)  /* size outside the supported range (see fr_plan_create) */
+#define FR_ETIMEOUT (-5)      /* a bounded device-side wait gave up; the call's output is invalid */
+
+/* plan flags */
+#define FR_WTERM 1u          /* apply the w-term exp(-2 pi i w (n - 1)) of Eq. (rime) */
+#define FR_NTERM 2u          /* apply the 1/n factor of Eq. (rime) */
+#define FR_MFS 4u            /* one sky image for all channels (nsky = 1) */
+#define FR_DROP_OOB 8u       /* drop visibilities whose kernel footprint leaves the grid instead of failing */
+#define FR_NO_PSF 16u        /* skip building the PSF (fr_psf_apply / approximate likelihood unavailable) */
+
+/* Build a plan (plan time, Sec. 3.3.4: done once per observation).
+ *   uvw      host float64 [nrow][3] metres
+ *   freqs    host float64 [nchan] Hz, all > 0
+ *   weights  host float32 [nrow][nchan] (N^-1 as visibility weights, Sec. 3.1.2), >= 0;
+ *            NULL means all ones; weight 0 marks flagged data
+ *   nx, ny   image size; powers of two in [16, 4096]
+ *   pixsize_x, pixsize_y  pixel size in radians (direction cosines), > 0
+ *   eps      requested relative L2 accuracy of R and R^dag, in [1e-6, 1e-2]
+ *   flags    FR_WTERM | FR_NTERM | FR_MFS | FR_DROP_OOB | FR_NO_PSF
+ *   stream   stream for the plan's device work; the call synchronises it before returning
+ *   out      receives the plan handle
+ * Errors: FR_EINVAL for bad sizes/pointers, non-finite uvw or freqs, negative weights, or a
+ * visibility whose gridding-kernel footprint leaves the oversampled grid (|u| too close to
+ * 1 / (2 pixsize_x)) unless FR_DROP_OOB; FR_EUNSUPPORTED for sizes outside the range above;
+ * FR_ENOMEM, FR_ECUDA. On error *out is NULL. */
+int fr_plan_create(const double *uvw, int64_t nrow, const double *freqs, int32_t nchan,
+                   const float *weights, int32_t nx, int32_t ny, double pixsize_x,
+                   double pixsize_y, double eps, uint32_t flags, void *stream, fr_plan_t *out);
+
+/* R, Eq. (rime): sky [nsky][nx][ny] (device) -> vis [nrow][nchan] (device, overwritten). */
+int fr_degrid(fr_plan_t plan, const float *sky, fr_cf32 *vis, void *stream);
+
+/* R^dag (N^-1 if apply_weights != 0), Eq. (clean): vis [nrow][nchan] (device) ->
+ * dirty [nsky][nx][ny] (device, overwritten): D_j = Re sum_k w_k y_k exp(+2 pi i phase_kj) / n_j. */
+int fr_grid(fr_plan_t plan, const fr_cf32 *vis, int32_t apply_weights, float *dirty, void *stream);
+
+/* Dirty image I^D = R^dag N^-1 V (Algorithm 1, first step) and the PSF (Sec. 3.3.2).
+ *   dirty    device [nsky][nx][ny] or NULL
+ *   psf      device [nsky][2nx][2ny] or NULL; unnormalised PSF(a, b) = sum_k w_k
+ *            cos(2 pi (u_k a dx + v_k b dy)) at w = 0, offset (a, b) stored at (a + nx, b + ny);
+ *            row 0 and column 0 are zero (never used by the cropped convolution)
+ *   psf_norm host [nsky] or NULL: sum of weights per image = PSF at offset 0 (FP64)
+ * vis may be NULL when dirty is NULL. */
+int fr_dirty_psf(fr_plan_t plan, const fr_cf32 *vis, float *dirty, float *psf, double *psf_norm,
+                 void *stream);
+
+/* PSF convolution (Sec. 3.3.2): out = P^dag FFT^-1[FFT[PSF] . FFT[P sky]], i.e. the linear
+ * convolution out(p) = sum_q PSF(p - q) sky(q) cropped to the image.
+ *   sky, out  device [batch][nsky][nx][ny]; image b*nsky + s uses the PSF of image s.
+ *   batch     >= 1 */
+int fr_psf_apply(fr_plan_t plan, const float *sky, int32_t batch, float *out, void *stream);
+
+/* Likelihood value and gradient (Eq. ham with Eq. clean, constants dropped):
+ *   L_b = 1/2 s_b^T (A s_b) - s_b^T d_b,  grad_b = A s_b - d_b
+ * with A = PSF * (exact == 0, Sec. 3.3.2) or A = R^dag N^-1 R (exact != 0, Algorithm 1).
+ *   sky, dirty, grad  device [batch][nsky][nx][ny]; grad may alias neither input
+ *   value             host float64 [batch] (sum over the nsky images of element b); may be NULL
+ * Reductions are FP64. Synchronises `stream` when value != NULL. */
+int fr_likelihood_grad(fr_plan_t plan, const float *sky, const float *dirty, int32_t batch,
+                       int32_t exact, float *grad, double *value, void *stream);
+
+/* Major-cycle residual of Algorithm 1 and residual norms (FP64 reductions):
+ *   resid = dirty - R^dag N^-1 R sky   (device [nsky][nx][ny], may be NULL)
+ *   resid_norm2  host float64: sum of resid^2 over all pixels (may be NULL)
+ *   vis, vis_chi2: if vis != NULL, vis_chi2 (host float64) = sum_k w_k |V_k - (R sky)_k|^2,
+ *   the data term of Eq. (ham).
+ * Synchronises `stream` when a host output is requested. */
+int fr_major_cycle(fr_plan_t plan, const float *sky, const float *dirty, float *resid,
+                   double *resid_norm2, const fr_cf32 *vis, double *vis_chi2, void *stream);
+
+/* Plan parameters chosen at creation (for reports and tests). */
+typedef struct {
+  int32_t nx, ny, nsky, nchan;
+  int64_t nrow, nvis;
+  int32_t grid_nu, grid_nv;        /* oversampled grid (2 nx, 2 ny) */
+  int32_t support;                 /* gridding kernel support W in cells */
+  double beta;                     /* exponential-of-semicircle kernel shape */
+  int32_t wplanes_total;           /* sum over images of the w-planes */
+  int32_t wplanes_max;             /* most w-planes of any image */
+  double dw;                       /* w-plane spacing in wavelengths (0 without FR_WTERM) */
+  int64_t nvis_dropped;            /* visibilities dropped under FR_DROP_OOB */
+  int64_t work_items;              /* (tile, plane) work items over all planes */
+  uint32_t flags;
+} fr_plan_info;
+int fr_plan_get_info(fr_plan_t plan, fr_plan_info *info);
+
+/* Device memory held by the plan: resident data and the largest per-stream workspace. */
+int fr_plan_footprint(fr_plan_t plan, size_t *resident_bytes, size_t *workspace_bytes);
+
+/* Synchronise `stream` and report a device-side failure recorded by earlier calls on it
+ * (FR_ETIMEOUT after a bounded wait gave up), then clear it. */
+int fr_plan_check(fr_plan_t plan, void *stream);
+
+/* Release the plan and all its device memory. Synchronises the device. NULL is ignored. */
+void fr_plan_destroy(fr_plan_t plan);
+
+const char *fr_strerror(int code);
+const char *fr_last_error(void);
+
+/* Number of kernel launches made by this library on the calling thread since the last reset
+ * (for launch accounting in benchmarks). */
+uint64_t fr_launch_count(int reset);
+
+/* Host-only check of the FFT passes' Stockham index and butterfly arithmetic: transforms
+ * `batch` sequences of 2^log2l complex values in place (interleaved float32 re, im) on the CPU
+ * with the same stage code the kernels use. dir = -1 forward, +1 inverse (unnormalised).
+ * Returns FR_EINVAL for log2l outside [1, 14]. Test support; needs no GPU. */
+int fr_selftest_fft_host(float *data, int32_t log2l, int32_t batch, int32_t dir);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTRESOLVE_H */

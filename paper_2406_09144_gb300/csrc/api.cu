@@ -1,0 +1,872 @@
+// C ABI of libfastresolve: plan creation (kernel choice, w-stacking layout, correction tables,
+// sorted visibilities, PSF and its transfer function), the operator entry points, per-stream
+// workspaces, error reporting and small FP64 reduction kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <memory>
+
+#include "fr_internal.cuh"
+
+namespace fr {
+
+// ------------------------------------------------------------------------ errors / counters
+static thread_local std::string g_err;
+static thread_local uint64_t g_launches = 0;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+const char* get_error() { return g_err.c_str(); }
+void count_launch(int n) { g_launches += (uint64_t)n; }
+
+// ------------------------------------------------------------------------ reductions
+static constexpr int RED_T = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[RED_T / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  v = 0.0;
+  if (wid == 0) {
+    v = lane < RED_T / 32 ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+static unsigned nblocks(size_t n) {
+  size_t b = (n + RED_T - 1) / RED_T;
+  return (unsigned)std::max<size_t>(1, std::min<size_t>(b, 152 * 16));
+}
+
+__global__ void __launch_bounds__(RED_T) dot_kernel(const float* a, const float* b, size_t n,
+                                                    double scale, double* acc) {
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)RED_T + threadIdx.x; i < n; i += (size_t)gridDim.x * RED_T)
+    s += (double)a[i] * (double)(b ? b[i] : a[i]);
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(acc, s * scale);
+}
+
+int dot_images(const float* a, const float* b, size_t n, double scale, double* acc,
+               cudaStream_t s) {
+  if (n == 0) return FR_OK;
+  dot_kernel<<<nblocks(n), RED_T, 0, s>>>(a, b, n, scale, acc);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+__global__ void __launch_bounds__(RED_T) sub_kernel(const float* a, const float* b, float* out,
+                                                    size_t n) {
+  for (size_t i = blockIdx.x * (size_t)RED_T + threadIdx.x; i < n; i += (size_t)gridDim.x * RED_T)
+    out[i] = a[i] - b[i];
+}
+
+int sub_images(const float* a, const float* b, float* out, size_t n, cudaStream_t s) {
+  if (n == 0) return FR_OK;
+  sub_kernel<<<nblocks(n), RED_T, 0, s>>>(a, b, out, n);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+// exact likelihood epilogue: grad = As - d (in place over As), acc[elem] += 1/2 s.As - s.d
+__global__ void __launch_bounds__(RED_T) lik_kernel(const float* s, float* as_grad, const float* d,
+                                                    size_t n, double* acc) {
+  double v = 0.0;
+  for (size_t i = blockIdx.x * (size_t)RED_T + threadIdx.x; i < n; i += (size_t)gridDim.x * RED_T) {
+    const double si = s[i], ai = as_grad[i], di = d[i];
+    v += 0.5 * si * ai - si * di;
+    as_grad[i] = (float)(ai - di);
+  }
+  v = block_sum(v);
+  if (threadIdx.x == 0) atomicAdd(acc, v);
+}
+
+// weighted data misfit over the kept visibilities, sorted order -> user index
+__global__ void __launch_bounds__(RED_T) chi2_kernel(const float2* vis, const float2* model,
+                                                     const float* wgt, const uint32_t* perm,
+                                                     size_t n, double* acc) {
+  double v = 0.0;
+  for (size_t i = blockIdx.x * (size_t)RED_T + threadIdx.x; i < n; i += (size_t)gridDim.x * RED_T) {
+    const uint32_t k = perm[i] & 0x7fffffffu;
+    const double dr = (double)vis[k].x - model[k].x, di = (double)vis[k].y - model[k].y;
+    v += (double)wgt[i] * (dr * dr + di * di);
+  }
+  v = block_sum(v);
+  if (threadIdx.x == 0) atomicAdd(acc, v);
+}
+
+__global__ void sum_weights_kernel(const float* w, int64_t b, int64_t e, double* acc) {
+  double v = 0.0;
+  for (int64_t i = b + blockIdx.x * (int64_t)RED_T + threadIdx.x; i < e;
+       i += (int64_t)gridDim.x * RED_T)
+    v += w[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) atomicAdd(acc, v);
+}
+
+__global__ void zero_edges_kernel(float* psf, int nimg, int nx2, int ny2) {
+  const int64_t per = (int64_t)nx2 + ny2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * nimg;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t img = i / per, r = i % per;
+    float* p = psf + img * (int64_t)nx2 * ny2;
+    if (r < ny2)
+      p[r] = 0.f;  // row 0
+    else
+      p[(r - ny2) * ny2] = 0.f;  // column 0
+  }
+}
+
+int zero_psf_edges(float* psf, int nsky, int nx2, int ny2, cudaStream_t s) {
+  zero_edges_kernel<<<nblocks((size_t)(nx2 + ny2) * nsky), 256, 0, s>>>(psf, nsky, nx2, ny2);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+// ------------------------------------------------------------------------ twiddles
+static int make_twiddles(float2** out, int log2l, cudaStream_t s) {
+  const int L = 1 << log2l;
+  std::vector<float2> h(L);
+  for (int m = 0; m < L; ++m) {
+    const double a = -2.0 * M_PI * (double)m / (double)L;
+    h[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  FR_CUDA_TRY(cudaMalloc(out, L * sizeof(float2)));
+  FR_CUDA_TRY(cudaMemcpyAsync(*out, h.data(), L * sizeof(float2), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+int ensure_twiddles(fr_plan* p, int log2l, cudaStream_t s) {
+  if (log2l < fft_min_log2() || log2l > fft_max_log2()) {
+    set_error("FFT length 2^%d outside the supported range", log2l);
+    return FR_EUNSUPPORTED;
+  }
+  if (!p->tw[log2l]) {
+    FR_TRY(make_twiddles(&p->tw[log2l], log2l, s));
+    p->resident += ((size_t)1 << log2l) * sizeof(float2);
+  }
+  return FR_OK;
+}
+
+// ------------------------------------------------------------------------ workspaces
+static void free_ws(Workspace* w) {
+  cudaFree(w->b1);
+  cudaFree(w->grid);
+  cudaFree(w->vbuf);
+  cudaFree(w->h);
+  cudaFree(w->tmp_img);
+  cudaFree(w->tmp_vis);
+  cudaFree(w->red);
+  delete w;
+}
+
+template <class T>
+static int ws_alloc(T** p, size_t n, Workspace* w) {
+  if (n == 0) return FR_OK;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error("workspace allocation of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+    return FR_ENOMEM;
+  }
+  w->bytes += n * sizeof(T);
+  return FR_OK;
+}
+
+static int get_ws(fr_plan* p, cudaStream_t s, Workspace** out) {
+  std::lock_guard<std::mutex> lk(p->mu);
+  for (Workspace* w : p->ws)
+    if (w->stream == s) {
+      *out = w;
+      return FR_OK;
+    }
+  std::unique_ptr<Workspace> w(new Workspace());
+  w->stream = s;
+  const Geometry& g = p->geo;
+  int r;
+  if ((r = ws_alloc(&w->b1, (size_t)g.nx * g.Nv, w.get())) ||
+      (r = ws_alloc(&w->grid, (size_t)g.Nu * g.Nv, w.get())) ||
+      (r = ws_alloc(&w->vbuf, (size_t)std::max<int64_t>(p->lay.nsorted, 1), w.get()))) {
+    free_ws(w.release());
+    return r;
+  }
+  cudaError_t e = cudaMemsetAsync(w->grid, 0, (size_t)g.Nu * g.Nv * sizeof(float2), s);
+  if (e != cudaSuccess) {
+    set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+    free_ws(w.release());
+    return FR_ECUDA;
+  }
+  w->grid_zero = true;
+  if ((r = make_tmap(&w->tmap, w->grid, g.Nu, g.Nv, g.kern.W))) {
+    free_ws(w.release());
+    return r;
+  }
+  w->tmap_ok = true;
+  *out = w.get();
+  p->ws.push_back(w.release());
+  return FR_OK;
+}
+
+static int ws_reserve_h(Workspace* w, size_t n) {
+  if (w->h_bytes >= n * sizeof(float2)) return FR_OK;
+  cudaFree(w->h);
+  w->bytes -= w->h_bytes;
+  w->h = nullptr;
+  w->h_bytes = 0;
+  FR_TRY(ws_alloc(&w->h, n, w));
+  w->h_bytes = n * sizeof(float2);
+  return FR_OK;
+}
+
+static int ws_reserve_red(Workspace* w, size_t n) {
+  if (w->red_n >= n) return FR_OK;
+  cudaFree(w->red);
+  w->red = nullptr;
+  w->red_n = 0;
+  FR_TRY(ws_alloc(&w->red, n, w));
+  w->red_n = n;
+  return FR_OK;
+}
+
+static int ws_reserve_tmp(fr_plan* p, Workspace* w) {
+  if (!w->tmp_img) FR_TRY(ws_alloc(&w->tmp_img, (size_t)p->nsky * p->geo.nx * p->geo.ny, w));
+  if (!w->tmp_vis) FR_TRY(ws_alloc(&w->tmp_vis, (size_t)std::max<int64_t>(p->lay.nvis, 1), w));
+  return FR_OK;
+}
+
+// ------------------------------------------------------------------------ operators
+static PlaneArgs plane_args(const Geometry& geo, const VisLayout& lay, int g, int p) {
+  PlaneArgs a;
+  a.nx = geo.nx;
+  a.ny = geo.ny;
+  a.Nu = geo.Nu;
+  a.Nv = geo.Nv;
+  a.corr = geo.corr;
+  a.tq = geo.tq;
+  a.wterm = geo.wterm ? 1 : 0;
+  a.k64 = geo.wterm ? plane_k64(geo, plane_w(geo, lay, g, p)) : 0;
+  return a;
+}
+
+// R for all images of a layout
+static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Workspace* w,
+                      const float* sky, float2* vis, cudaStream_t s) {
+  if (lay.ndropped > 0)
+    FR_CUDA_TRY(cudaMemsetAsync(vis, 0, (size_t)lay.nvis * sizeof(float2), s));
+  const size_t img = (size_t)geo.nx * geo.ny;
+  for (int g = 0; g < lay.ngroups; ++g) {
+    const int P = geo.wterm ? lay.planes[g] : 1;
+    for (int p = 0; p < P; ++p) {
+      const int q = lay.plane_base[g] + p;
+      if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
+      PlaneArgs a = plane_args(geo, lay, g, p);
+      FR_TRY(degrid_prepass(a, sky + g * img, w->b1, w->grid, pl->tw[ilog2(geo.Nv)],
+                            pl->tw[ilog2(geo.Nu)], s));
+      w->grid_zero = false;
+      FR_TRY(degrid_plane(geo, lay, g, p, w->tmap, w->vbuf, vis, pl->status, s));
+    }
+  }
+  return FR_OK;
+}
+
+// R^dag (N^-1) for all images of a layout; vis == null grids ones (PSF)
+static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Workspace* w,
+                    const float2* vis, int apply_weights, float* dirty, float2* grid, float2* b1,
+                    float2* ybuf, cudaStream_t s, bool* grid_zero) {
+  FR_TRY(grid_prepare(geo, lay, vis, apply_weights, ybuf, s));
+  if (!*grid_zero) FR_CUDA_TRY(cudaMemsetAsync(grid, 0, (size_t)geo.Nu * geo.Nv * sizeof(float2), s));
+  *grid_zero = true;
+  const size_t img = (size_t)geo.nx * geo.ny;
+  for (int g = 0; g < lay.ngroups; ++g) {
+    const int P = geo.wterm ? lay.planes[g] : 1;
+    bool written = false;
+    for (int p = 0; p < P; ++p) {
+      const int q = lay.plane_base[g] + p;
+      if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
+      FR_TRY(grid_plane(geo, lay, g, p, ybuf, grid, s));
+      PlaneArgs a = plane_args(geo, lay, g, p);
+      FR_TRY(grid_postpass(a, grid, b1, dirty + g * img, written ? 1 : 0, pl->tw[ilog2(geo.Nu)],
+                           pl->tw[ilog2(geo.Nv)], s));
+      written = true;
+    }
+    if (!written) FR_CUDA_TRY(cudaMemsetAsync(dirty + g * img, 0, img * sizeof(float), s));
+  }
+  (void)w;
+  return FR_OK;
+}
+
+// ------------------------------------------------------------------------ plan creation
+static int choose_support(double eps) {
+  int W = (int)std::ceil(std::log10(1.0 / eps)) + 1;
+  return std::min(16, std::max(4, W));
+}
+
+static void set_kernel(Geometry* g, int W) {
+  g->kern.W = W;
+  g->beta = 0.97 * M_PI * W * (1.0 - 1.0 / (2.0 * 2.0));
+  g->kern.beta = (float)g->beta;
+  g->kern.inv_hw = 2.0f / (float)W;
+}
+
+static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const double* d_freqs,
+                     const float* d_weights, cudaStream_t s) {
+  Geometry pg;
+  pg.nx = 2 * p->geo.nx;
+  pg.ny = 2 * p->geo.ny;
+  pg.Nu = 2 * pg.nx;
+  pg.Nv = 2 * pg.ny;
+  pg.dl = p->geo.dl;
+  pg.dm = p->geo.dm;
+  set_kernel(&pg, p->geo.kern.W);
+  pg.wterm = false;
+  pg.nterm = false;
+  FR_TRY(ensure_twiddles(p, ilog2(pg.Nu), s));
+  FR_TRY(ensure_twiddles(p, ilog2(pg.Nv), s));
+  std::vector<double> iu, iv;
+  kernel_ft_tables(pg, iu, iv);
+  FR_TRY(make_tables(&pg, iu, iv, s));
+  VisLayout pl;
+  std::vector<double> wlo(p->nsky, 0.0);
+  std::vector<int> planes(p->nsky, 1);
+  int r = build_layout(pg, d_uvw, p->nrow, freqs, d_freqs, p->nchan, d_weights, p->nsky, wlo, planes,
+                       true, &pl, s);
+  float2 *grid = nullptr, *b1 = nullptr, *y = nullptr, *h = nullptr;
+  const size_t nimg2 = (size_t)pg.nx * pg.ny;
+  const int hp = p->geo.ny + 2;
+  if (r == FR_OK) {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&grid, (size_t)pg.Nu * pg.Nv * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&b1, (size_t)pg.nx * pg.Nv * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&y, (size_t)std::max<int64_t>(pl.nsorted, 1) * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&h, (size_t)p->nsky * pg.nx * hp * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->psf_img, (size_t)p->nsky * nimg2 * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMalloc(&p->transfer, (size_t)p->nsky * pg.nx * (p->geo.ny + 1) * sizeof(float));
+    if (e != cudaSuccess) {
+      set_error("PSF allocation failed: %s", cudaGetErrorString(e));
+      r = FR_ENOMEM;
+    }
+  }
+  if (r == FR_OK) {
+    bool zero = false;
+    r = run_grid(p, pg, pl, nullptr, nullptr, 1, p->psf_img, grid, b1, y, s, &zero);
+  }
+  if (r == FR_OK) r = zero_psf_edges(p->psf_img, p->nsky, pg.nx, pg.ny, s);
+  if (r == FR_OK)
+    r = build_transfer(p->geo.nx, p->geo.ny, p->nsky, p->psf_img, h, hp, p->transfer,
+                       p->tw[ilog2(pg.ny)], p->tw[ilog2(pg.nx)], s);
+  // psf_norm = sum of the kept weights per image (FP64)
+  double* d_norm = nullptr;
+  if (r == FR_OK) {
+    cudaError_t e = cudaMalloc(&d_norm, p->nsky * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_norm, 0, p->nsky * sizeof(double), s);
+    for (int g = 0; g < p->nsky && e == cudaSuccess; ++g) {
+      const int64_t b = pl.group_begin[g], en = pl.group_begin[g + 1];
+      if (en > b) sum_weights_kernel<<<nblocks(en - b), RED_T, 0, s>>>(pl.wgt, b, en, d_norm + g);
+      count_launch();
+      e = cudaGetLastError();
+    }
+    p->psf_norm.assign(p->nsky, 0.0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->psf_norm.data(), d_norm, p->nsky * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("PSF normalisation failed: %s", cudaGetErrorString(e));
+      r = FR_ECUDA;
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(d_norm);
+  cudaFree(grid);
+  cudaFree(b1);
+  cudaFree(y);
+  cudaFree(h);
+  cudaFree(pg.corr);
+  cudaFree(pg.tq);
+  free_layout(&pl);
+  if (r == FR_OK) {
+    p->has_psf = true;
+    p->resident += (size_t)p->nsky * nimg2 * sizeof(float) +
+                   (size_t)p->nsky * pg.nx * (p->geo.ny + 1) * sizeof(float);
+  }
+  return r;
+}
+
+static bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int32_t nchan,
+                       const float* weights, int32_t nx, int32_t ny, double dx, double dy,
+                       double eps, uint32_t flags, cudaStream_t s, fr_plan* p) {
+  if (!uvw || !freqs || nrow <= 0 || nchan <= 0) {
+    set_error("uvw/freqs must be non-null with nrow > 0 and nchan > 0");
+    return FR_EINVAL;
+  }
+  if (!pow2(nx) || !pow2(ny) || nx < 16 || ny < 16 || nx > 4096 || ny > 4096) {
+    set_error("nx, ny must be powers of two in [16, 4096] (got %d x %d)", nx, ny);
+    return FR_EUNSUPPORTED;
+  }
+  if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy)) {
+    set_error("pixel sizes must be finite and positive");
+    return FR_EINVAL;
+  }
+  if (!(eps >= 1e-6 && eps <= 1e-2)) {
+    set_error("eps must lie in [1e-6, 1e-2] (got %g)", eps);
+    return FR_EUNSUPPORTED;
+  }
+  if ((int64_t)nrow * nchan >= (1ll << 31)) {
+    set_error("at most 2^31 - 1 visibilities per plan");
+    return FR_EUNSUPPORTED;
+  }
+  for (int c = 0; c < nchan; ++c)
+    if (!(freqs[c] > 0) || !std::isfinite(freqs[c])) {
+      set_error("frequency %d is not finite and positive", c);
+      return FR_EINVAL;
+    }
+  double wabs_min = INFINITY, wabs_max = 0.0;
+  for (int64_t r = 0; r < nrow; ++r) {
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(uvw[3 * r + k])) {
+        set_error("uvw row %lld is not finite", (long long)r);
+        return FR_EINVAL;
+      }
+    const double a = std::fabs(uvw[3 * r + 2]);
+    wabs_min = std::min(wabs_min, a);
+    wabs_max = std::max(wabs_max, a);
+  }
+  if (weights) {
+    const int64_t M = nrow * nchan;
+    for (int64_t k = 0; k < M; ++k)
+      if (!(weights[k] >= 0.f) || !std::isfinite(weights[k])) {
+        set_error("weight %lld is negative or not finite", (long long)k);
+        return FR_EINVAL;
+      }
+  }
+  p->nrow = nrow;
+  p->nchan = nchan;
+  p->nsky = (flags & FR_MFS) ? 1 : nchan;
+  p->flags = flags;
+  p->eps = eps;
+  FR_CUDA_TRY(cudaMalloc(&p->status, sizeof(int)));
+  FR_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+
+  Geometry& g = p->geo;
+  g.nx = nx;
+  g.ny = ny;
+  g.Nu = 2 * nx;
+  g.Nv = 2 * ny;
+  g.dl = dx;
+  g.dm = dy;
+  set_kernel(&g, choose_support(eps));
+  g.nterm = (flags & FR_NTERM) != 0;
+  g.wterm = (flags & FR_WTERM) != 0;
+  // w-stacking extent: t = n - 1 in [t_min, 0]
+  const double lx = 0.5 * nx * dx, ly = 0.5 * ny * dy;
+  const double r2max = std::min(lx * lx + ly * ly, 1.0);
+  g.t_min = -r2max / (1.0 + std::sqrt(1.0 - r2max));
+  double fmax = 0.0, fmin = INFINITY;
+  for (int c = 0; c < nchan; ++c) {
+    fmax = std::max(fmax, freqs[c]);
+    fmin = std::min(fmin, freqs[c]);
+  }
+  const double CL = 299792458.0;
+  if (g.wterm && (wabs_max * fmax / CL) * (-g.t_min) < 1e-9) g.wterm = false;  // phase < 1e-9 turn
+  std::vector<double> w_lo(p->nsky, 0.0);
+  std::vector<int> planes(p->nsky, 1);
+  if (g.wterm) {
+    g.t_c = 0.5 * g.t_min;
+    g.t_half = -0.5 * g.t_min;
+    g.dw = 1.0 / (2.0 * -g.t_min);  // oversampling 2 along w
+    for (int k = 0; k < p->nsky; ++k) {
+      const double flo = p->nsky == 1 ? fmin : freqs[k], fhi = p->nsky == 1 ? fmax : freqs[k];
+      const double lo = wabs_min * flo / CL, hi = wabs_max * fhi / CL;
+      w_lo[k] = lo;
+      planes[k] = (int)std::floor((hi - lo) / g.dw) + 1 + g.kern.W;
+    }
+  }
+  for (int L : {g.Nu, g.Nv}) FR_TRY(ensure_twiddles(p, ilog2(L), s));
+
+  // device copies of the inputs (plan-time only)
+  double *d_uvw = nullptr, *d_freqs = nullptr;
+  float* d_w = nullptr;
+  struct Free {
+    void* a;
+    ~Free() { cudaFree(a); }
+  };
+  FR_CUDA_TRY(cudaMalloc(&d_uvw, (size_t)nrow * 3 * sizeof(double)));
+  Free f1{d_uvw};
+  FR_CUDA_TRY(cudaMalloc(&d_freqs, nchan * sizeof(double)));
+  Free f2{d_freqs};
+  FR_CUDA_TRY(cudaMemcpyAsync(d_uvw, uvw, (size_t)nrow * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_freqs, freqs, nchan * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (weights) {
+    FR_CUDA_TRY(cudaMalloc(&d_w, (size_t)nrow * nchan * sizeof(float)));
+    FR_CUDA_TRY(cudaMemcpyAsync(d_w, weights, (size_t)nrow * nchan * sizeof(float), cudaMemcpyHostToDevice, s));
+  }
+  Free f3{d_w};
+
+  std::vector<double> iu, iv;
+  kernel_ft_tables(g, iu, iv);
+  FR_TRY(make_tables(&g, iu, iv, s));
+  p->resident += (size_t)nx * ny * (sizeof(float) + (g.wterm ? sizeof(int32_t) : 0));
+  FR_TRY(build_layout(g, d_uvw, nrow, freqs, d_freqs, nchan, d_w, p->nsky, w_lo, planes,
+                      (flags & FR_DROP_OOB) != 0, &p->lay, s));
+  p->resident += p->lay.bytes;
+  if (!(flags & FR_NO_PSF)) FR_TRY(build_psf(p, d_uvw, freqs, d_freqs, d_w, s));
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+static void plan_free(fr_plan* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  for (Workspace* w : p->ws) free_ws(w);
+  free_layout(&p->lay);
+  cudaFree(p->geo.corr);
+  cudaFree(p->geo.tq);
+  cudaFree(p->psf_img);
+  cudaFree(p->transfer);
+  cudaFree(p->status);
+  for (float2*& t : p->tw) cudaFree(t);
+  delete p;
+}
+
+// ------------------------------------------------------------------------ host FFT check
+template <int R, int DIR>
+static void host_stage(const float2* in, float2* out, const float2* tw, int L, int Ns) {
+  for (int j = 0; j < L / R; ++j) stockham_task<R, DIR>(in, out, tw, L, Ns, j);
+}
+
+template <int DIR>
+static void host_fft(float2* buf, float2* tmp, const float2* tw, int log2l) {
+  const int L = 1 << log2l;
+  int Ns = 1;
+  float2* a = buf;
+  float2* b = tmp;
+  for (int st = 0; st < num_stages(log2l); ++st) {
+    const int R = 1 << stage_bits(log2l, st);
+    switch (R) {
+      case 2: host_stage<2, DIR>(a, b, tw, L, Ns); break;
+      case 4: host_stage<4, DIR>(a, b, tw, L, Ns); break;
+      case 8: host_stage<8, DIR>(a, b, tw, L, Ns); break;
+      default: host_stage<16, DIR>(a, b, tw, L, Ns); break;
+    }
+    Ns *= R;
+    std::swap(a, b);
+  }
+  if (a != buf) std::memcpy(buf, a, sizeof(float2) * spad_len(L));
+}
+
+}  // namespace fr
+
+using namespace fr;
+
+extern "C" {
+
+const char* fr_strerror(int code) {
+  switch (code) {
+    case FR_OK: return "success";
+    case FR_EINVAL: return "invalid argument";
+    case FR_ENOMEM: return "out of memory";
+    case FR_ECUDA: return "CUDA error";
+    case FR_EUNSUPPORTED: return "unsupported size or option";
+    case FR_ETIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char* fr_last_error(void) { return get_error(); }
+
+uint64_t fr_launch_count(int reset) {
+  uint64_t v = g_launches;
+  if (reset) g_launches = 0;
+  return v;
+}
+
+int fr_plan_create(const double* uvw, int64_t nrow, const double* freqs, int32_t nchan,
+                   const float* weights, int32_t nx, int32_t ny, double pixsize_x, double pixsize_y,
+                   double eps, uint32_t flags, void* stream, fr_plan_t* out) {
+  if (!out) {
+    set_error("out must not be NULL");
+    return FR_EINVAL;
+  }
+  *out = nullptr;
+  fr_plan* p = new (std::nothrow) fr_plan();
+  if (!p) return FR_ENOMEM;
+  int r = plan_create(uvw, nrow, freqs, nchan, weights, nx, ny, pixsize_x, pixsize_y, eps, flags,
+                      (cudaStream_t)stream, p);
+  if (r != FR_OK) {
+    std::string keep = get_error();
+    plan_free(p);
+    set_error("%s", keep.c_str());
+    return r;
+  }
+  *out = p;
+  return FR_OK;
+}
+
+void fr_plan_destroy(fr_plan_t p) { plan_free(p); }
+
+int fr_degrid(fr_plan_t p, const float* sky, fr_cf32* vis, void* stream) {
+  if (!p || !sky || !vis) {
+    set_error("plan, sky and vis must be non-null");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  return run_degrid(p, p->geo, p->lay, w, sky, (float2*)vis, s);
+}
+
+int fr_grid(fr_plan_t p, const fr_cf32* vis, int32_t apply_weights, float* dirty, void* stream) {
+  if (!p || !vis || !dirty) {
+    set_error("plan, vis and dirty must be non-null");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  return run_grid(p, p->geo, p->lay, w, (const float2*)vis, apply_weights ? 1 : 0, dirty, w->grid,
+                  w->b1, w->vbuf, s, &w->grid_zero);
+}
+
+int fr_dirty_psf(fr_plan_t p, const fr_cf32* vis, float* dirty, float* psf, double* psf_norm,
+                 void* stream) {
+  if (!p) {
+    set_error("plan must be non-null");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dirty) FR_TRY(fr_grid(p, vis, 1, dirty, stream));
+  if ((psf || psf_norm) && !p->has_psf) {
+    set_error("plan was created with FR_NO_PSF");
+    return FR_EINVAL;
+  }
+  if (psf)
+    FR_CUDA_TRY(cudaMemcpyAsync(psf, p->psf_img,
+                                (size_t)p->nsky * 4 * p->geo.nx * p->geo.ny * sizeof(float),
+                                cudaMemcpyDeviceToDevice, s));
+  if (psf_norm) std::memcpy(psf_norm, p->psf_norm.data(), p->nsky * sizeof(double));
+  return FR_OK;
+}
+
+static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, const float* dirty,
+                      double* value, cudaStream_t s) {
+  if (!p->has_psf) {
+    set_error("plan was created with FR_NO_PSF");
+    return FR_EINVAL;
+  }
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  const int nimg = batch * p->nsky;
+  const int hp = p->geo.ny + 2;
+  FR_TRY(ws_reserve_h(w, (size_t)nimg * p->geo.nx * hp));
+  PsfArgs a;
+  a.nx = p->geo.nx;
+  a.ny = p->geo.ny;
+  a.nimg = nimg;
+  a.nsky = p->nsky;
+  a.hp = hp;
+  a.transfer = p->transfer;
+  a.sky = sky;
+  a.out = out;
+  a.dirty = dirty;
+  a.value = nullptr;
+  if (dirty) {
+    FR_TRY(ws_reserve_red(w, (size_t)std::max(batch, 4)));
+    FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, batch * sizeof(double), s));
+    a.value = w->red;
+  }
+  FR_TRY(psf_apply_passes(a, w->h, p->tw[ilog2(2 * a.ny)], p->tw[ilog2(2 * a.nx)], s));
+  if (dirty && value) {
+    FR_CUDA_TRY(cudaMemcpyAsync(value, w->red, batch * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return FR_OK;
+}
+
+int fr_psf_apply(fr_plan_t p, const float* sky, int32_t batch, float* out, void* stream) {
+  if (!p || !sky || !out || batch < 1) {
+    set_error("plan, sky, out must be non-null and batch >= 1");
+    return FR_EINVAL;
+  }
+  return psf_common(p, sky, batch, out, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int fr_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, int32_t batch,
+                       int32_t exact, float* grad, double* value, void* stream) {
+  if (!p || !sky || !dirty || !grad || batch < 1) {
+    set_error("plan, sky, dirty, grad must be non-null and batch >= 1");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!exact) return psf_common(p, sky, batch, grad, dirty, value, s);
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  FR_TRY(ws_reserve_tmp(p, w));
+  FR_TRY(ws_reserve_red(w, (size_t)std::max(batch, 4)));
+  FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, batch * sizeof(double), s));
+  const size_t n = (size_t)p->nsky * p->geo.nx * p->geo.ny;
+  for (int b = 0; b < batch; ++b) {
+    const float* sb = sky + b * n;
+    float* gb = grad + b * n;
+    FR_TRY(run_degrid(p, p->geo, p->lay, w, sb, w->tmp_vis, s));
+    FR_TRY(run_grid(p, p->geo, p->lay, w, w->tmp_vis, 1, gb, w->grid, w->b1, w->vbuf, s, &w->grid_zero));
+    lik_kernel<<<nblocks(n), RED_T, 0, s>>>(sb, gb, dirty + b * n, n, w->red + b);
+    FR_LAUNCHED();
+  }
+  if (value) {
+    FR_CUDA_TRY(cudaMemcpyAsync(value, w->red, batch * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return FR_OK;
+}
+
+int fr_major_cycle(fr_plan_t p, const float* sky, const float* dirty, float* resid,
+                   double* resid_norm2, const fr_cf32* vis, double* vis_chi2, void* stream) {
+  if (!p || !sky) {
+    set_error("plan and sky must be non-null");
+    return FR_EINVAL;
+  }
+  if ((resid || resid_norm2) && !dirty) {
+    set_error("dirty is required for the image residual");
+    return FR_EINVAL;
+  }
+  if (vis_chi2 && !vis) {
+    set_error("vis is required for vis_chi2");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  FR_TRY(ws_reserve_tmp(p, w));
+  FR_TRY(ws_reserve_red(w, 4));
+  FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, 2 * sizeof(double), s));
+  FR_TRY(run_degrid(p, p->geo, p->lay, w, sky, w->tmp_vis, s));
+  if (vis_chi2 && p->lay.nsorted > 0) {
+    chi2_kernel<<<nblocks(p->lay.nsorted), RED_T, 0, s>>>((const float2*)vis, w->tmp_vis, p->lay.wgt,
+                                                          p->lay.perm, p->lay.nsorted, w->red + 1);
+    FR_LAUNCHED();
+  }
+  const size_t n = (size_t)p->nsky * p->geo.nx * p->geo.ny;
+  if (resid || resid_norm2) {
+    FR_TRY(run_grid(p, p->geo, p->lay, w, w->tmp_vis, 1, w->tmp_img, w->grid, w->b1, w->vbuf, s,
+                    &w->grid_zero));
+    float* r = resid ? resid : w->tmp_img;
+    FR_TRY(sub_images(dirty, w->tmp_img, r, n, s));
+    if (resid_norm2) FR_TRY(dot_images(r, nullptr, n, 1.0, w->red, s));
+  }
+  if (resid_norm2 || vis_chi2) {
+    double h[2];
+    FR_CUDA_TRY(cudaMemcpyAsync(h, w->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (resid_norm2) *resid_norm2 = h[0];
+    if (vis_chi2) *vis_chi2 = h[1];
+  }
+  return FR_OK;
+}
+
+int fr_plan_get_info(fr_plan_t p, fr_plan_info* info) {
+  if (!p || !info) {
+    set_error("plan and info must be non-null");
+    return FR_EINVAL;
+  }
+  std::memset(info, 0, sizeof *info);
+  info->nx = p->geo.nx;
+  info->ny = p->geo.ny;
+  info->nsky = p->nsky;
+  info->nchan = p->nchan;
+  info->nrow = p->nrow;
+  info->nvis = p->lay.nvis;
+  info->grid_nu = p->geo.Nu;
+  info->grid_nv = p->geo.Nv;
+  info->support = p->geo.kern.W;
+  info->beta = p->geo.beta;
+  int tot = 0, mx = 0;
+  for (int g = 0; g < p->lay.ngroups; ++g) {
+    const int P = p->geo.wterm ? p->lay.planes[g] : 1;
+    tot += P;
+    mx = std::max(mx, P);
+  }
+  info->wplanes_total = tot;
+  info->wplanes_max = mx;
+  info->dw = p->geo.wterm ? p->geo.dw : 0.0;
+  info->nvis_dropped = p->lay.ndropped;
+  info->work_items = p->lay.nitems;
+  info->flags = p->flags;
+  return FR_OK;
+}
+
+int fr_plan_footprint(fr_plan_t p, size_t* resident_bytes, size_t* workspace_bytes) {
+  if (!p) {
+    set_error("plan must be non-null");
+    return FR_EINVAL;
+  }
+  if (resident_bytes) *resident_bytes = p->resident;
+  if (workspace_bytes) {
+    std::lock_guard<std::mutex> lk(p->mu);
+    size_t m = 0;
+    for (Workspace* w : p->ws) m = std::max(m, w->bytes);
+    if (p->ws.empty()) {
+      const Geometry& g = p->geo;
+      m = ((size_t)g.nx * g.Nv + (size_t)g.Nu * g.Nv + (size_t)std::max<int64_t>(p->lay.nsorted, 1)) *
+          sizeof(float2);
+    }
+    *workspace_bytes = m;
+  }
+  return FR_OK;
+}
+
+int fr_plan_check(fr_plan_t p, void* stream) {
+  if (!p) {
+    set_error("plan must be non-null");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = 0;
+  FR_CUDA_TRY(cudaMemcpyAsync(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (st) {
+    FR_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+    set_error("a bounded device-side wait gave up (status %d)", st);
+    return FR_ETIMEOUT;
+  }
+  return FR_OK;
+}
+
+int fr_selftest_fft_host(float* data, int32_t log2l, int32_t batch, int32_t dir) {
+  if (!data || log2l < 1 || log2l > 14 || batch < 1 || (dir != 1 && dir != -1)) {
+    set_error("bad arguments to fr_selftest_fft_host");
+    return FR_EINVAL;
+  }
+  const int L = 1 << log2l;
+  std::vector<float2> tw(L), a(spad_len(L)), b(spad_len(L));
+  for (int m = 0; m < L; ++m) {
+    const double ang = -2.0 * M_PI * (double)m / (double)L;
+    tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  for (int q = 0; q < batch; ++q) {
+    float2* x = reinterpret_cast<float2*>(data) + (size_t)q * L;
+    for (int i = 0; i < L; ++i) a[spad(i)] = x[i];
+    if (dir < 0)
+      host_fft<-1>(a.data(), b.data(), tw.data(), log2l);
+    else
+      host_fft<1>(a.data(), b.data(), tw.data(), log2l);
+    for (int i = 0; i < L; ++i) x[i] = a[spad(i)];
+  }
+  return FR_OK;
+}
+
+}  // extern "C"

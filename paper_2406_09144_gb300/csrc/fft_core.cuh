@@ -1,0 +1,187 @@
+// Radix-2/4/8/16 Stockham FFT building blocks shared by every FFT pass kernel.
+//
+// The FFT passes implement the FFT[...] / FFT^-1[...] of the padded PSF convolution
+// (Sec. 3.3.2) and the oversampled-grid transforms of the measurement operator R (Eq. rime)
+// and its adjoint. Only power-of-two lengths are supported.
+//
+// A Stockham stage with radix R and current sub-transform size Ns maps, for each butterfly
+// task j in [0, L/R):
+//     k = j mod Ns
+//     v[r] = x[j + r L/R] * w^(r k),  w = exp(dir 2 pi i / (Ns R))
+//     v    = DFT_R(v)
+//     y[(j / Ns) Ns R + k + r Ns] = v[r]
+// which leaves the result in natural order after the last stage (no bit reversal).
+// Twiddles come from a per-length table tw[m] = exp(-2 pi i m / L) (conjugated for dir = +1).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#ifndef FR_HD
+#define FR_HD __host__ __device__ __forceinline__
+#endif
+
+namespace fr {
+
+FR_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+FR_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+FR_HD float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+FR_HD float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+FR_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+FR_HD float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by dir * i  (dir = -1: -i, dir = +1: +i)
+template <int DIR>
+FR_HD float2 mul_i(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// ---------------------------------------------------------------------------------------
+// In-register DFTs of size 2, 4, 8, 16 with exponent sign DIR (-1 forward, +1 inverse).
+// Input and output in natural order.
+// ---------------------------------------------------------------------------------------
+template <int DIR>
+FR_HD void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int DIR>
+FR_HD void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  // X[k] = sum_n x[n] w4^(nk),  w4 = exp(DIR 2 pi i / 4) = DIR * i
+  float2 s02 = cadd(x0, x2), d02 = csub(x0, x2);
+  float2 s13 = cadd(x1, x3), d13 = mul_i<DIR>(csub(x1, x3));
+  x0 = cadd(s02, s13);
+  x2 = csub(s02, s13);
+  x1 = cadd(d02, d13);
+  x3 = csub(d02, d13);
+}
+
+template <int DIR>
+FR_HD void dft8(float2* v) {
+  const float h = 0.70710678118654752440f;
+  // split into even / odd halves (decimation in time)
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<DIR>(e0, e1, e2, e3);
+  dft4<DIR>(o0, o1, o2, o3);
+  // twiddles w8^k, w8 = exp(DIR 2 pi i / 8)
+  // k=1: (h, DIR h); k=2: DIR i; k=3: (-h, DIR h)
+  float2 t1 = make_float2(h * (o1.x - DIR * o1.y), h * (o1.y + DIR * o1.x));
+  float2 t2 = mul_i<DIR>(o2);
+  float2 t3 = make_float2(-h * (o3.x + DIR * o3.y), h * (DIR * o3.x - o3.y));
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, t1);
+  v[5] = csub(e1, t1);
+  v[2] = cadd(e2, t2);
+  v[6] = csub(e2, t2);
+  v[3] = cadd(e3, t3);
+  v[7] = csub(e3, t3);
+}
+
+template <int DIR>
+FR_HD float2 tw16(float2 a, int k) {
+  // a * exp(DIR 2 pi i k / 16) for k in [0, 9], constants folded after unrolling
+  const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
+  const float h = 0.70710678118654752440f;
+  float c, s;
+  switch (k) {
+    case 0: return a;
+    case 1: c = c1; s = s1; break;
+    case 2: c = h; s = h; break;
+    case 3: c = s1; s = c1; break;
+    case 4: return mul_i<DIR>(a);
+    case 6: c = -h; s = h; break;
+    case 9: c = -c1; s = -s1; break;
+    default: c = 1.f; s = 0.f; break;
+  }
+  s = DIR * s;
+  return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+template <int DIR>
+FR_HD void dft16(float2* v) {
+  // 16 = 4 x 4: n = n1 + 4 n2, k = k2 + 4 k1
+  // step 1: for each n1, DFT4 over n2 -> index k2;  step 2: twiddle w16^(n1 k2);
+  // step 3: for each k2, DFT4 over n1 -> k1
+  float2 a[4][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    a[n1][0] = v[n1];
+    a[n1][1] = v[n1 + 4];
+    a[n1][2] = v[n1 + 8];
+    a[n1][3] = v[n1 + 12];
+    dft4<DIR>(a[n1][0], a[n1][1], a[n1][2], a[n1][3]);
+  }
+#pragma unroll
+  for (int n1 = 1; n1 < 4; ++n1)
+#pragma unroll
+    for (int k2 = 1; k2 < 4; ++k2) a[n1][k2] = tw16<DIR>(a[n1][k2], n1 * k2);
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 b0 = a[0][k2], b1 = a[1][k2], b2 = a[2][k2], b3 = a[3][k2];
+    dft4<DIR>(b0, b1, b2, b3);
+    v[k2] = b0;
+    v[k2 + 4] = b1;
+    v[k2 + 8] = b2;
+    v[k2 + 12] = b3;
+  }
+}
+
+template <int R, int DIR>
+FR_HD void dft_r(float2* v) {
+  if constexpr (R == 2) {
+    dft2<DIR>(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    dft4<DIR>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    dft8<DIR>(v);
+  } else {
+    static_assert(R == 16, "radix must be 2, 4, 8 or 16");
+    dft16<DIR>(v);
+  }
+}
+
+// Radix schedule: log2 bits per stage, each at most 4 (radix 16).
+// stage_bits(LOG2L, s) gives the bits of stage s (s = 0 first).
+constexpr int num_stages(int log2l) { return (log2l + 3) / 4; }
+constexpr int stage_bits(int log2l, int s) {
+  // spread bits as evenly as possible, larger radices first
+  return log2l / num_stages(log2l) + (s < (log2l % num_stages(log2l)) ? 1 : 0);
+}
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+// Shared-memory padding: one float2 of padding after every 16 elements breaks the
+// power-of-two strides of the Stockham scatter.
+FR_HD int spad(int i) { return i + (i >> 4); }
+constexpr int spad_len(int n) { return n + (n >> 4); }
+
+// One Stockham stage on a single task j, reading from `in` and writing to `out`
+// (both indexed through spad), used by the host emulation tests and as reference.
+template <int R, int DIR>
+FR_HD void stockham_task(const float2* in, float2* out, const float2* tw, int L, int Ns, int j) {
+  float2 v[R];
+  const int k = j % Ns;
+  const int stride = L / R;
+  const int tstep = L / (Ns * R);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float2 x = in[spad(j + r * stride)];
+    if (r > 0) {
+      float2 w = tw[(r * k * tstep) & (L - 1)];
+      if (DIR > 0) w.y = -w.y;
+      x = cmul(x, w);
+    }
+    v[r] = x;
+  }
+  dft_r<R, DIR>(v);
+  const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) out[spad(base + r * Ns)] = v[r];
+}
+
+}  // namespace fr

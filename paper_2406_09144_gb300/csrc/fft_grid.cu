@@ -1,0 +1,183 @@
+// FFT passes of the measurement operator R and its adjoint (Eq. rime, Eq. clean).
+//
+// Degridding pre-pass for one w-plane p (two passes, forward transforms):
+//   D1 (rows along v): image row jx -> pixel values I_j c_p(j) placed at v index (py mod Nv),
+//      c_p(j) = corr_j exp(-2 pi i w_p (t_j - t_c)), then FFT over v -> B1[jx][.]
+//   D2 (columns along u): B1 column v placed at u index (px mod Nu), FFT over u -> grid[.][v]
+// corr_j = (-1)^(px+py) / (n_j Phi_u Phi_v Phi_w) holds the grid correction (reciprocal of the
+// gridding kernel's Fourier transform) and the sign that centres zero frequency at (Nu/2, Nv/2).
+//
+// Gridding post-pass for one w-plane (two passes, inverse transforms, cropped early):
+//   G1 (columns along u): grid column -> inverse FFT -> keep the nx rows px in [-nx/2, nx/2)
+//      -> B1; the grid column is zeroed after loading (the grid stays zero between calls)
+//   G2 (rows along v): inverse FFT -> keep ny outputs -> Re(Z conj(c_p(j))) accumulated into
+//      the dirty image.
+#include "fft_engine.cuh"
+
+namespace fr {
+
+__device__ __forceinline__ void plane_phase(int32_t tq, long long k64, float* c, float* s) {
+  // frac(w_p (t - t_c)) from a wrapping 64-bit fixed-point product; the top 32 bits are the
+  // signed fraction of a cycle in [-1/2, 1/2).
+  unsigned long long prod = (unsigned long long)(long long)tq * (unsigned long long)k64;
+  int hi = (int)(unsigned)(prod >> 32);
+  float f = (float)hi * 2.3283064365386963e-10f;
+  sincospif(2.f * f, s, c);
+}
+
+struct D1Op {
+  const float* sky;
+  const float* corr;
+  const int32_t* tq;
+  long long k64;
+  int wterm;
+  float2* b1;
+  int nx, ny, Nv;
+  __host__ __device__ int nseq() const { return nx; }
+  __host__ __device__ int nout() const { return Nv; }
+  __device__ float2 load(int jx, int i) const {
+    const int hy = ny >> 1;
+    int jy;
+    if (i < hy)
+      jy = i + hy;
+    else if (i >= Nv - hy)
+      jy = i - Nv + hy;
+    else
+      return make_float2(0.f, 0.f);
+    const int pix = jx * ny + jy;
+    const float val = __ldg(&sky[pix]) * __ldg(&corr[pix]);
+    if (!wterm) return make_float2(val, 0.f);
+    float c, s;
+    plane_phase(__ldg(&tq[pix]), k64, &c, &s);
+    return make_float2(val * c, -val * s);
+  }
+  __device__ double store(int jx, int o, SeqView v) const {
+    b1[(size_t)jx * Nv + o] = v[o];
+    return 0.0;
+  }
+  __device__ void finish(int, double) const {}
+};
+
+struct D2Op {
+  const float2* b1;
+  float2* grid;
+  int nx, Nu, Nv;
+  __host__ __device__ int ncol() const { return Nv; }
+  __host__ __device__ int nout() const { return Nu; }
+  __device__ float2 load(int i, int v) const {
+    const int hx = nx >> 1;
+    int jx;
+    if (i < hx)
+      jx = i + hx;
+    else if (i >= Nu - hx)
+      jx = i - Nu + hx;
+    else
+      return make_float2(0.f, 0.f);
+    return b1[(size_t)jx * Nv + v];
+  }
+  template <int B, int NT, int L>
+  __device__ void after_load(int) const {}
+  template <int B, int NT, int L, int LP>
+  __device__ void mid(float2*, int) const {}
+  __device__ void store(int o, int v, SeqView s) const { grid[(size_t)o * Nv + v] = s[o]; }
+};
+
+struct G1Op {
+  float2* grid;
+  float2* b1;
+  int nx, Nu, Nv;
+  __host__ __device__ int ncol() const { return Nv; }
+  __host__ __device__ int nout() const { return nx; }
+  __device__ float2 load(int i, int v) const { return grid[(size_t)i * Nv + v]; }
+  template <int B, int NT, int L>
+  __device__ void after_load(int col0) const {
+    for (int idx = threadIdx.x; idx < B * L; idx += NT) {
+      const int i = idx / B, c = idx % B;
+      if (col0 + c < Nv) grid[(size_t)i * Nv + col0 + c] = make_float2(0.f, 0.f);
+    }
+  }
+  template <int B, int NT, int L, int LP>
+  __device__ void mid(float2*, int) const {}
+  __device__ void store(int o, int v, SeqView s) const {
+    const int i = (o - (nx >> 1) + Nu) & (Nu - 1);
+    b1[(size_t)o * Nv + v] = s[i];
+  }
+};
+
+struct G2Op {
+  const float2* b1;
+  float* dirty;
+  const float* corr;
+  const int32_t* tq;
+  long long k64;
+  int wterm, accumulate;
+  int nx, ny, Nv;
+  __host__ __device__ int nseq() const { return nx; }
+  __host__ __device__ int nout() const { return ny; }
+  __device__ float2 load(int jx, int i) const { return b1[(size_t)jx * Nv + i]; }
+  __device__ double store(int jx, int jy, SeqView s) const {
+    const int i = (jy - (ny >> 1) + Nv) & (Nv - 1);
+    const float2 z = s[i];
+    const int pix = jx * ny + jy;
+    float val;
+    if (wterm) {
+      float c, sn;
+      plane_phase(__ldg(&tq[pix]), k64, &c, &sn);
+      val = z.x * c - z.y * sn;  // Re(z exp(+2 pi i w_p (t - t_c)))
+    } else {
+      val = z.x;
+    }
+    val *= __ldg(&corr[pix]);
+    dirty[pix] = accumulate ? dirty[pix] + val : val;
+    return 0.0;
+  }
+  __device__ void finish(int, double) const {}
+};
+
+
+template <int LG>
+static int run_d1(const D1Op& op, const float2* tw, cudaStream_t s) {
+  return launch_rows<LG, -1>(op, tw, s);
+}
+template <int LG>
+static int run_d2(const D2Op& op, const float2* tw, cudaStream_t s) {
+  ColOp<LG, D2Op> c;
+  static_cast<D2Op&>(c) = op;
+  return launch_cols<LG, -1, -1, false>(c, 1, tw, s);
+}
+template <int LG>
+static int run_g1(const G1Op& op, const float2* tw, cudaStream_t s) {
+  ColOp<LG, G1Op> c;
+  static_cast<G1Op&>(c) = op;
+  return launch_cols<LG, 1, 1, false>(c, 1, tw, s);
+}
+template <int LG>
+static int run_g2(const G2Op& op, const float2* tw, cudaStream_t s) {
+  return launch_rows<LG, 1>(op, tw, s);
+}
+
+static int d1(int lg, const D1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1, op, tw, s); }
+static int d2(int lg, const D2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2, op, tw, s); }
+static int g1(int lg, const G1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1, op, tw, s); }
+static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2, op, tw, s); }
+
+int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
+                   const float2* twv, const float2* twu, cudaStream_t s) {
+  D1Op o1{sky, a.corr, a.tq, a.k64, a.wterm, b1, a.nx, a.ny, a.Nv};
+  FR_TRY(d1(ilog2(a.Nv), o1, twv, s));
+  D2Op o2{b1, grid, a.nx, a.Nu, a.Nv};
+  return d2(ilog2(a.Nu), o2, twu, s);
+}
+
+int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
+                  const float2* twu, const float2* twv, cudaStream_t s) {
+  G1Op o1{grid, b1, a.nx, a.Nu, a.Nv};
+  FR_TRY(g1(ilog2(a.Nu), o1, twu, s));
+  G2Op o2{b1, dirty, a.corr, a.tq, a.k64, a.wterm, accumulate, a.nx, a.ny, a.Nv};
+  return g2(ilog2(a.Nv), o2, twv, s);
+}
+
+int fft_max_log2() { return 14; }
+int fft_min_log2() { return 5; }
+
+}  // namespace fr

@@ -1,0 +1,219 @@
+// Internal declarations shared by the translation units of libfastresolve.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fastresolve.h"
+#include "fft_core.cuh"
+
+namespace fr {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+const char* get_error();
+void count_launch(int n = 1);
+
+#define FR_CUDA_TRY(expr)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ::fr::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,     \
+                      __LINE__);                                                           \
+      return e_ == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA;                       \
+    }                                                                                      \
+  } while (0)
+
+#define FR_TRY(expr)            \
+  do {                          \
+    int r_ = (expr);            \
+    if (r_ != FR_OK) return r_; \
+  } while (0)
+
+// launch check after a kernel launch
+#define FR_LAUNCHED()                                                                       \
+  do {                                                                                      \
+    ::fr::count_launch();                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                    \
+    if (e_ != cudaSuccess) {                                                                \
+      ::fr::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), __FILE__,  \
+                      __LINE__);                                                            \
+      return FR_ECUDA;                                                                      \
+    }                                                                                       \
+  } while (0)
+
+// device status word values (bitmask)
+enum : int { ST_TIMEOUT = 1 };
+
+// ------------------------------------------------------------------ kernel shape
+// Exponential-of-semicircle gridding kernel phi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)),
+// |x| <= W/2 in grid cells.
+struct EsKernel {
+  int W;         // support in cells
+  float beta;    // shape
+  float inv_hw;  // 2 / W
+};
+
+__device__ __forceinline__ float es_eval(const EsKernel& k, float x) {
+  float z = x * k.inv_hw;
+  float t = fmaxf(1.f - z * z, 0.f);
+  return __expf(k.beta * (sqrtf(t) - 1.f));
+}
+
+// ------------------------------------------------------------------ tiles and TMA
+constexpr int TILE = 32;       // grid cells per tile side (u and v)
+constexpr int MAXW = 16;       // largest kernel support
+constexpr int GRID_CHUNK = 512;  // visibilities per (tile, plane) work item at most
+
+// Padded tile box: rows BU = TILE + W - 1, columns BV = BU rounded up to even (16-byte rows).
+__host__ __device__ inline int box_u(int W) { return TILE + W - 1; }
+__host__ __device__ inline int box_v(int W) { return (TILE + W - 1 + 1) & ~1; }
+
+// ------------------------------------------------------------------ sorted visibility set
+// One imaging geometry: image nx x ny, oversampled grid Nu x Nv, kernel, w-stacking.
+struct Geometry {
+  int nx = 0, ny = 0, Nu = 0, Nv = 0;
+  double dl = 0, dm = 0;
+  EsKernel kern{};
+  double beta = 0;
+  bool wterm = false, nterm = false;
+  double t_min = 0, t_c = 0, t_half = 0;  // w-stacking image-side extent
+  double dw = 0;                           // plane spacing (wavelengths)
+  float* corr = nullptr;                   // [nx*ny] (-1)^(px+py) / (n Phi_u Phi_v Phi_w)
+  int32_t* tq = nullptr;                   // [nx*ny] (t - t_c) / t_half * 2^30  (wterm)
+};
+
+// Visibilities sorted by (image group, tile, first w-plane) for one geometry.
+struct VisLayout {
+  int ngroups = 0;
+  int ntu = 0, ntv = 0;                 // tiles per grid side
+  std::vector<int> planes;              // [ngroups]
+  std::vector<double> w_lo;             // [ngroups]
+  std::vector<int64_t> plane_items;     // [sum planes + 1] item ranges, (g, p) major
+  std::vector<int> plane_base;          // [ngroups] index of (g, 0) in plane_items
+  std::vector<int64_t> group_begin;     // [ngroups + 1] sorted index range of each group
+  int64_t nvis = 0;                     // visibilities in user order
+  int64_t nsorted = 0;                  // kept after dropping
+  int64_t ndropped = 0;
+  // device arrays in sorted order
+  uint32_t* cell = nullptr;  // iu0 << 18 | iv0 << 4 | (p_first & 15)
+  float* du = nullptr;
+  float* dv = nullptr;
+  float* dw = nullptr;       // y_w - p_first   (wterm)
+  uint32_t* ph = nullptr;    // frac(w t_c) as Q32 (wterm)
+  uint32_t* perm = nullptr;  // user index (row * nchan + chan) | conj flag << 31
+  float* wgt = nullptr;
+  int4* items = nullptr;     // {vis_begin, vis_count, tu << 16 | tv, 0}
+  int64_t nitems = 0;
+  size_t bytes = 0;
+};
+
+// Per-stream scratch.
+struct Workspace {
+  cudaStream_t stream = nullptr;
+  float2* b1 = nullptr;      // [nx][Nv] half-transformed plane
+  float2* grid = nullptr;    // [Nu][Nv] oversampled grid (kept zero between fr_grid calls)
+  bool grid_zero = false;
+  float2* vbuf = nullptr;    // [nsorted] sorted visibilities (accumulator / weighted input)
+  float2* h = nullptr;       // PSF-apply half spectra [nimg][nx][HP]
+  size_t h_bytes = 0;
+  float* tmp_img = nullptr;  // [nsky][nx][ny] scratch image (exact likelihood, major cycle)
+  float2* tmp_vis = nullptr; // [nvis] scratch visibilities (exact likelihood, major cycle)
+  double* red = nullptr;     // [max(batch, 4)] FP64 reduction targets
+  size_t red_n = 0;
+  CUtensorMap tmap;          // TMA descriptor of `grid`
+  bool tmap_ok = false;
+  size_t bytes = 0;
+};
+
+}  // namespace fr
+
+struct fr_plan {
+  fr::Geometry geo;
+  fr::VisLayout lay;
+  int64_t nrow = 0;
+  int nchan = 0, nsky = 0;
+  uint32_t flags = 0;
+  double eps = 0;
+  // PSF (Sec. 3.3.2)
+  bool has_psf = false;
+  std::vector<double> psf_norm;  // [nsky]
+  float* psf_img = nullptr;      // [nsky][2nx][2ny]
+  float* transfer = nullptr;     // [nsky][2nx][ny+1], includes 1 / (4 nx ny)
+  // twiddle tables by log2 length
+  float2* tw[16] = {nullptr};
+  int* status = nullptr;         // device status word
+  size_t resident = 0;
+  std::mutex mu;
+  std::vector<fr::Workspace*> ws;
+};
+
+namespace fr {
+
+// twiddle tables
+int ensure_twiddles(fr_plan* p, int log2l, cudaStream_t s);
+
+// -------- FFT passes (fft_*.cu) --------
+struct PlaneArgs {
+  // geometry
+  int nx, ny, Nu, Nv;
+  const float* corr;
+  const int32_t* tq;
+  long long k64;  // per-plane phase multiplier, Q64 cycles per tq unit (0 without w)
+  int wterm;
+};
+int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
+                   const float2* twv, const float2* twu, cudaStream_t s);
+int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
+                  const float2* twu, const float2* twv, cudaStream_t s);
+// PSF-apply passes over nimg images of nx x ny; image i uses transfer + (i % nsky) * tstride
+struct PsfArgs {
+  int nx, ny, nimg, nsky;
+  int hp;  // half-spectrum row pitch (complex)
+  const float* transfer;
+  const float* sky;
+  float* out;
+  const float* dirty;   // likelihood mode (grad = conv - dirty), else null
+  double* value;        // likelihood mode: [nimg / nsky] accumulators, else null
+};
+int psf_apply_passes(const PsfArgs& a, float2* h, const float2* tw_rows, const float2* tw_cols,
+                     cudaStream_t s);
+// transfer function from PSF images [nsky][2nx][2ny] -> transfer [nsky][2nx][ny+1]
+int build_transfer(int nx, int ny, int nsky, const float* psf, float2* h, int hp, float* transfer,
+                   const float2* tw_rows, const float2* tw_cols, cudaStream_t s);
+int fft_max_log2();
+int fft_min_log2();
+
+// -------- gridding kernels (gridder.cu) --------
+int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const double* h_freqs,
+                 const double* d_freqs, int nchan, const float* d_weights, int ngroups,
+                 const std::vector<double>& w_lo, const std::vector<int>& planes, bool drop_oob,
+                 VisLayout* lay, cudaStream_t s);
+void free_layout(VisLayout* lay);
+int make_tmap(CUtensorMap* m, float2* grid, int Nu, int Nv, int W);
+int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p,
+                 const CUtensorMap& tmap, float2* vacc, float2* vis_out, int* status,
+                 cudaStream_t s);
+int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const float2* ysorted,
+               float2* grid, cudaStream_t s);
+int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, int apply_weights,
+                 float2* ysorted, cudaStream_t s);
+int make_tables(Geometry* geo, const std::vector<double>& inv_phi_u,
+                const std::vector<double>& inv_phi_v, cudaStream_t s);
+void kernel_ft_tables(const Geometry& geo, std::vector<double>& inv_u, std::vector<double>& inv_v);
+long long plane_k64(const Geometry& geo, double w_plane);
+double plane_w(const Geometry& geo, const VisLayout& lay, int g, int p);
+
+// -------- small kernels (api.cu) --------
+int zero_psf_edges(float* psf, int nsky, int nx2, int ny2, cudaStream_t s);
+int sub_images(const float* a, const float* b, float* out, size_t n, cudaStream_t s);
+int dot_images(const float* a, const float* b, size_t n, double scale, double* acc,
+               cudaStream_t s);  // acc += scale * sum(a*b)
+int chi2_vis(const float2* v, const float2* m, const float* w, size_t n, double* acc,
+             cudaStream_t s);
+
+}  // namespace fr

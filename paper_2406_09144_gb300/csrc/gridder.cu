@@ -1,0 +1,1047 @@
+// Visibility-side kernels of R and R^dag N^-1 (Eq. rime, Eq. clean):
+//   * plan-time coordinate scaling k = uvw nu / c in FP64, w-plane assignment, tile keys and a
+//     counting sort into (image group, tile, first w-plane) order, plus the (tile, plane) work
+//     items (a1);
+//   * the degridder: per (tile, plane) work item one CTA stages the grid tile with a TMA bulk
+//     tensor copy into shared memory and each thread interpolates one visibility with the
+//     separable kernel phi(du) phi(dv) phi(dw) (a4);
+//   * the gridder: per work item one CTA accumulates its visibilities into a shared-memory
+//     sub-grid and flushes the non-zero cells to the global grid with vector atomics (a5);
+//   * per-pixel correction tables (grid correction, 1/n, w-plane phase coordinate).
+// The gridding kernel is the exponential of a semicircle; its Fourier transform corrects the
+// image side. The paper names the wgridder for this operator but does not describe it.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "fr_internal.cuh"
+
+namespace fr {
+
+static constexpr double C_LIGHT = 299792458.0;
+
+// ---------------------------------------------------------------------------------- scan
+// Exclusive prefix sum of int32 counts: out[0..n] with out[n] = total.
+static constexpr int SCAN_BLK = 1024, SCAN_PER = 4, SCAN_TILE = SCAN_BLK * SCAN_PER;
+
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+  __shared__ int ws[SCAN_BLK / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    ws[lane] = s;
+  }
+  __syncthreads();
+  const int before = (wid > 0 ? ws[wid - 1] : 0) + x - v;
+  *total = ws[SCAN_BLK / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(SCAN_BLK) scan_reduce(const int* in, int64_t n, int* bsum) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
+  int s = 0;
+  for (int k = 0; k < SCAN_PER; ++k)
+    if (base + k < n) s += in[base + k];
+  int tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_BLK) scan_blocks(int* bsum, int nb) {
+  int carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += SCAN_BLK) {
+    int i = b0 + threadIdx.x;
+    int v = i < nb ? bsum[i] : 0;
+    int tot;
+    int ex = block_excl_scan(v, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_BLK) scan_final(const int* in, int64_t n, const int* bsum,
+                                                       int* out) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
+  int v[SCAN_PER];
+  int s = 0;
+  for (int k = 0; k < SCAN_PER; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  int tot;
+  int ex = block_excl_scan(s, &tot) + bsum[blockIdx.x];
+  for (int k = 0; k < SCAN_PER; ++k) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = bsum[gridDim.x];
+}
+
+static int exclusive_scan(const int* in, int* out, int64_t n, cudaStream_t s) {
+  const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (n == 0) {
+    FR_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int), s));
+    return FR_OK;
+  }
+  int* bsum = nullptr;
+  FR_CUDA_TRY(cudaMallocAsync(&bsum, (nb + 1) * sizeof(int), s));
+  scan_reduce<<<(unsigned)nb, SCAN_BLK, 0, s>>>(in, n, bsum);
+  FR_LAUNCHED();
+  scan_blocks<<<1, SCAN_BLK, 0, s>>>(bsum, (int)nb);
+  FR_LAUNCHED();
+  scan_final<<<(unsigned)nb, SCAN_BLK, 0, s>>>(in, n, bsum, out);
+  FR_LAUNCHED();
+  FR_CUDA_TRY(cudaFreeAsync(bsum, s));
+  return FR_OK;
+}
+
+// ------------------------------------------------------------------------ coordinates
+struct PrepArgs {
+  const double* uvw;
+  const double* freqs;
+  const float* weights;
+  int64_t nrow;
+  int nchan, ngroups;
+  int Nu, Nv, W;
+  double dl, dm;
+  int wterm;
+  double t_c, dw;
+  const double* w_lo;    // [ngroups]
+  const int* planes;     // [ngroups]
+  const int* keybase;    // [ngroups]
+  int ntu, ntv;
+  int drop;
+  // outputs in user order
+  int* key;              // -1 = dropped
+  uint32_t* cell;
+  float* du;
+  float* dv;
+  float* dw_out;
+  uint32_t* ph;
+  float* wgt;
+  int* err;              // bit 1: footprint outside the grid, bit 2: bad coordinate
+  unsigned long long* ndrop;
+};
+
+__global__ void vis_prepare(PrepArgs a) {
+  const int64_t M = a.nrow * a.nchan;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = k / a.nchan;
+    const int c = (int)(k - row * a.nchan);
+    const int g = a.ngroups == 1 ? 0 : c;
+    const double f = a.freqs[c] / C_LIGHT;
+    double u = a.uvw[3 * row] * f, v = a.uvw[3 * row + 1] * f, w = a.uvw[3 * row + 2] * f;
+    if (a.wterm && w < 0.0) {  // V(-u,-v,-w) = conj V(u,v,w) for a real sky
+      u = -u;
+      v = -v;
+      w = -w;
+    }
+    const double gu = u * a.Nu * a.dl + 0.5 * a.Nu;
+    const double gv = v * a.Nv * a.dm + 0.5 * a.Nv;
+    const double hw = 0.5 * a.W;
+    bool ok = isfinite(gu) && isfinite(gv) && isfinite(w);
+    double iu0 = 0, iv0 = 0;
+    if (ok) {
+      iu0 = ceil(gu - hw);
+      iv0 = ceil(gv - hw);
+      ok = iu0 >= 0.0 && iu0 + a.W - 1 <= a.Nu - 1 && iv0 >= 0.0 && iv0 + a.W - 1 <= a.Nv - 1;
+    }
+    int pf = 0;
+    double dwv = 0.0;
+    if (ok && a.wterm) {
+      const double y = (w - a.w_lo[g]) / a.dw + hw;
+      pf = (int)ceil(y - hw);
+      if (pf < 0) pf = 0;
+      if (pf > a.planes[g] - a.W) pf = a.planes[g] - a.W;
+      dwv = y - pf;
+    }
+    if (!ok) {
+      a.key[k] = -1;
+      if (a.drop)
+        atomicAdd(a.ndrop, 1ull);
+      else
+        atomicOr(a.err, 1);
+      continue;
+    }
+    const int ju = (int)iu0, jv = (int)iv0;
+    const int tu = ju / TILE, tv = jv / TILE;
+    const int P = a.wterm ? a.planes[g] : 1;
+    a.key[k] = a.keybase[g] + (tu * a.ntv + tv) * P + pf;
+    a.cell[k] = ((uint32_t)ju << 18) | ((uint32_t)jv << 4) | (uint32_t)(pf & 15);
+    a.du[k] = (float)(gu - iu0);
+    a.dv[k] = (float)(gv - iv0);
+    if (a.wterm) {
+      a.dw_out[k] = (float)dwv;
+      const double x = w * a.t_c;
+      const double fr = x - rint(x);
+      a.ph[k] = (uint32_t)(long long)llrint(fr * 4294967296.0);
+    }
+    a.wgt[k] = a.weights ? a.weights[k] : 1.f;
+  }
+}
+
+__global__ void count_keys(const int* key, int64_t M, int* count) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int kk = key[k];
+    if (kk >= 0) atomicAdd(&count[kk], 1);
+  }
+}
+
+struct ScatterArgs {
+  const int* key;
+  int64_t M;
+  int nchan;
+  int* cursor;
+  int wterm;
+  const double* uvw;
+  const double* freqs;
+  const uint32_t* cell_in;
+  const float* du_in;
+  const float* dv_in;
+  const float* dw_in;
+  const uint32_t* ph_in;
+  const float* wgt_in;
+  uint32_t* cell;
+  float* du;
+  float* dv;
+  float* dw;
+  uint32_t* ph;
+  float* wgt;
+  uint32_t* perm;
+};
+
+__global__ void scatter_sorted(ScatterArgs a) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.M;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int kk = a.key[k];
+    if (kk < 0) continue;
+    const int pos = atomicAdd(&a.cursor[kk], 1);
+    a.cell[pos] = a.cell_in[k];
+    a.du[pos] = a.du_in[k];
+    a.dv[pos] = a.dv_in[k];
+    a.wgt[pos] = a.wgt_in[k];
+    uint32_t flip = 0;
+    if (a.wterm) {
+      a.dw[pos] = a.dw_in[k];
+      a.ph[pos] = a.ph_in[k];
+      const int64_t row = k / a.nchan;
+      flip = a.uvw[3 * row + 2] < 0.0 ? 1u : 0u;
+    }
+    a.perm[pos] = (uint32_t)k | (flip << 31);
+  }
+}
+
+// number of work-item chunks of every (group, plane, tile)
+struct ItemArgs {
+  const int* off;        // key offsets [K + 1]
+  const int* keybase;    // [ngroups]
+  const int* planes;     // [ngroups] (1 without w)
+  const int64_t* ebase;  // [ngroups + 1] (group, plane, tile) enumeration base
+  int ngroups, ntiles, ntv, W, wterm;
+  int* chunks;           // [E]
+  const int* item_off;   // [E + 1] (emit pass)
+  int4* items;
+};
+
+__device__ __forceinline__ void item_range(const ItemArgs& a, int64_t e, int* begin, int* count,
+                                           int* tile) {
+  int g = 0;
+  while (g + 1 < a.ngroups && e >= a.ebase[g + 1]) ++g;
+  const int64_t r = e - a.ebase[g];
+  const int P = a.planes[g];
+  const int p = (int)(r / a.ntiles);
+  const int t = (int)(r - (int64_t)p * a.ntiles);
+  *tile = t;
+  int lo, hi;
+  if (a.wterm) {
+    lo = max(p - a.W + 1, 0);
+    hi = min(p, P - a.W);
+  } else {
+    lo = 0;
+    hi = 0;
+  }
+  if (hi < lo) {
+    *begin = 0;
+    *count = 0;
+    return;
+  }
+  const int64_t kb = (int64_t)a.keybase[g] + (int64_t)t * P;
+  *begin = a.off[kb + lo];
+  *count = a.off[kb + hi + 1] - *begin;
+}
+
+__global__ void count_items(ItemArgs a, int64_t E) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int b, c, t;
+    item_range(a, e, &b, &c, &t);
+    a.chunks[e] = (c + GRID_CHUNK - 1) / GRID_CHUNK;
+  }
+}
+
+__global__ void emit_items(ItemArgs a, int64_t E) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int b, c, t;
+    item_range(a, e, &b, &c, &t);
+    if (c == 0) continue;
+    const int tu = t / a.ntv, tv = t - (t / a.ntv) * a.ntv;
+    int o = a.item_off[e];
+    for (int s = 0; s < c; s += GRID_CHUNK, ++o)
+      a.items[o] = make_int4(b + s, min(GRID_CHUNK, c - s), (tu << 16) | tv, 0);
+  }
+}
+
+__global__ void gather_plane_items(const int* item_off, const int64_t* qpos, int nq, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nq) out[i] = item_off[qpos[i]];
+}
+
+static unsigned grid1d(int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+template <class T>
+static int dalloc(T** p, size_t n, size_t* acc) {
+  *p = nullptr;
+  if (n == 0) return FR_OK;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+    *p = nullptr;
+    return FR_ENOMEM;
+  }
+  if (acc) *acc += n * sizeof(T);
+  return FR_OK;
+}
+
+void free_layout(VisLayout* lay) {
+  cudaFree(lay->cell);
+  cudaFree(lay->du);
+  cudaFree(lay->dv);
+  cudaFree(lay->dw);
+  cudaFree(lay->ph);
+  cudaFree(lay->perm);
+  cudaFree(lay->wgt);
+  cudaFree(lay->items);
+  lay->cell = nullptr;
+  lay->du = lay->dv = lay->dw = lay->wgt = nullptr;
+  lay->ph = lay->perm = nullptr;
+  lay->items = nullptr;
+}
+
+namespace {
+// RAII holder of temporary device buffers
+struct Temps {
+  std::vector<void*> p;
+  ~Temps() {
+    for (void* q : p) cudaFree(q);
+  }
+  template <class T>
+  int alloc(T** out, size_t n) {
+    int r = dalloc(out, n, nullptr);
+    if (r == FR_OK && *out) p.push_back(*out);
+    return r;
+  }
+};
+}  // namespace
+
+int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const double* h_freqs,
+                 const double* d_freqs, int nchan, const float* d_weights, int ngroups,
+                 const std::vector<double>& w_lo, const std::vector<int>& planes, bool drop_oob,
+                 VisLayout* lay, cudaStream_t s) {
+  (void)h_freqs;
+  const int64_t M = nrow * (int64_t)nchan;
+  lay->ngroups = ngroups;
+  lay->ntu = (geo.Nu + TILE - 1) / TILE;
+  lay->ntv = (geo.Nv + TILE - 1) / TILE;
+  lay->planes = planes;
+  lay->w_lo = w_lo;
+  lay->nvis = M;
+  const int ntiles = lay->ntu * lay->ntv;
+  const bool wterm = geo.wterm;
+
+  // keys: (group, tile, first plane)
+  std::vector<int> keybase(ngroups);
+  int64_t K = 0;
+  std::vector<int64_t> ebase(ngroups + 1);
+  int64_t E = 0;
+  for (int g = 0; g < ngroups; ++g) {
+    const int P = wterm ? planes[g] : 1;
+    keybase[g] = (int)K;
+    K += (int64_t)ntiles * P;
+    ebase[g] = E;
+    E += (int64_t)ntiles * P;
+  }
+  ebase[ngroups] = E;
+  if (K >= (1ll << 31) || M >= (1ll << 31)) {
+    set_error("problem too large: %lld keys, %lld visibilities", (long long)K, (long long)M);
+    return FR_EUNSUPPORTED;
+  }
+
+  Temps t;
+  int *d_key, *d_count, *d_off, *d_keybase, *d_planes, *d_err;
+  double* d_wlo;
+  int64_t* d_ebase;
+  unsigned long long* d_ndrop;
+  uint32_t *cell_u, *ph_u = nullptr;
+  float *du_u, *dv_u, *dw_u = nullptr, *wgt_u;
+  FR_TRY(t.alloc(&d_key, M));
+  FR_TRY(t.alloc(&d_count, K));
+  FR_TRY(t.alloc(&d_off, K + 1));
+  FR_TRY(t.alloc(&d_keybase, ngroups));
+  FR_TRY(t.alloc(&d_planes, ngroups));
+  FR_TRY(t.alloc(&d_wlo, ngroups));
+  FR_TRY(t.alloc(&d_ebase, ngroups + 1));
+  FR_TRY(t.alloc(&d_err, 1));
+  FR_TRY(t.alloc(&d_ndrop, 1));
+  FR_TRY(t.alloc(&cell_u, M));
+  FR_TRY(t.alloc(&du_u, M));
+  FR_TRY(t.alloc(&dv_u, M));
+  FR_TRY(t.alloc(&wgt_u, M));
+  if (wterm) {
+    FR_TRY(t.alloc(&dw_u, M));
+    FR_TRY(t.alloc(&ph_u, M));
+  }
+  std::vector<int> pl(ngroups);
+  for (int g = 0; g < ngroups; ++g) pl[g] = wterm ? planes[g] : 1;
+  FR_CUDA_TRY(cudaMemcpyAsync(d_keybase, keybase.data(), ngroups * sizeof(int), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_planes, pl.data(), ngroups * sizeof(int), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_wlo, w_lo.data(), ngroups * sizeof(double), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_ebase, ebase.data(), (ngroups + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  FR_CUDA_TRY(cudaMemsetAsync(d_ndrop, 0, sizeof(unsigned long long), s));
+  FR_CUDA_TRY(cudaMemsetAsync(d_count, 0, K * sizeof(int), s));
+
+  PrepArgs pa;
+  pa.uvw = d_uvw;
+  pa.freqs = d_freqs;
+  pa.weights = d_weights;
+  pa.nrow = nrow;
+  pa.nchan = nchan;
+  pa.ngroups = ngroups;
+  pa.Nu = geo.Nu;
+  pa.Nv = geo.Nv;
+  pa.W = geo.kern.W;
+  pa.dl = geo.dl;
+  pa.dm = geo.dm;
+  pa.wterm = wterm;
+  pa.t_c = geo.t_c;
+  pa.dw = geo.dw;
+  pa.w_lo = d_wlo;
+  pa.planes = d_planes;
+  pa.keybase = d_keybase;
+  pa.ntu = lay->ntu;
+  pa.ntv = lay->ntv;
+  pa.drop = drop_oob;
+  pa.key = d_key;
+  pa.cell = cell_u;
+  pa.du = du_u;
+  pa.dv = dv_u;
+  pa.dw_out = dw_u;
+  pa.ph = ph_u;
+  pa.wgt = wgt_u;
+  pa.err = d_err;
+  pa.ndrop = d_ndrop;
+  vis_prepare<<<grid1d(M), 256, 0, s>>>(pa);
+  FR_LAUNCHED();
+  count_keys<<<grid1d(M), 256, 0, s>>>(d_key, M, d_count);
+  FR_LAUNCHED();
+  FR_TRY(exclusive_scan(d_count, d_off, K, s));
+
+  int h_err = 0;
+  unsigned long long h_ndrop = 0;
+  int h_total = 0;
+  FR_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(&h_ndrop, d_ndrop, sizeof(h_ndrop), cudaMemcpyDeviceToHost, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(&h_total, d_off + K, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h_err) {
+    set_error("visibility coordinates outside the oversampled grid or not finite "
+              "(|u| must stay below about (1 - (W+2)/Nu) / (2 pixsize)); use FR_DROP_OOB to drop them");
+    return FR_EINVAL;
+  }
+  lay->ndropped = (int64_t)h_ndrop;
+  lay->nsorted = h_total;
+  {
+    std::vector<int> gb(ngroups + 1);
+    for (int g = 0; g < ngroups; ++g)
+      FR_CUDA_TRY(cudaMemcpyAsync(&gb[g], d_off + keybase[g], sizeof(int), cudaMemcpyDeviceToHost, s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+    gb[ngroups] = h_total;
+    lay->group_begin.assign(gb.begin(), gb.end());
+  }
+  const int64_t N = h_total;
+
+  size_t acc = 0;
+  FR_TRY(dalloc(&lay->cell, N, &acc));
+  FR_TRY(dalloc(&lay->du, N, &acc));
+  FR_TRY(dalloc(&lay->dv, N, &acc));
+  FR_TRY(dalloc(&lay->wgt, N, &acc));
+  FR_TRY(dalloc(&lay->perm, N, &acc));
+  if (wterm) {
+    FR_TRY(dalloc(&lay->dw, N, &acc));
+    FR_TRY(dalloc(&lay->ph, N, &acc));
+  }
+  // cursor = offsets (reuse the count buffer)
+  FR_CUDA_TRY(cudaMemcpyAsync(d_count, d_off, K * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  ScatterArgs sa;
+  sa.key = d_key;
+  sa.M = M;
+  sa.nchan = nchan;
+  sa.cursor = d_count;
+  sa.wterm = wterm;
+  sa.uvw = d_uvw;
+  sa.freqs = d_freqs;
+  sa.cell_in = cell_u;
+  sa.du_in = du_u;
+  sa.dv_in = dv_u;
+  sa.dw_in = dw_u;
+  sa.ph_in = ph_u;
+  sa.wgt_in = wgt_u;
+  sa.cell = lay->cell;
+  sa.du = lay->du;
+  sa.dv = lay->dv;
+  sa.dw = lay->dw;
+  sa.ph = lay->ph;
+  sa.wgt = lay->wgt;
+  sa.perm = lay->perm;
+  scatter_sorted<<<grid1d(M), 256, 0, s>>>(sa);
+  FR_LAUNCHED();
+
+  // work items per (group, plane, tile)
+  int *d_chunks, *d_item_off;
+  FR_TRY(t.alloc(&d_chunks, E));
+  FR_TRY(t.alloc(&d_item_off, E + 1));
+  ItemArgs ia;
+  ia.off = d_off;
+  ia.keybase = d_keybase;
+  ia.planes = d_planes;
+  ia.ebase = d_ebase;
+  ia.ngroups = ngroups;
+  ia.ntiles = ntiles;
+  ia.ntv = lay->ntv;
+  ia.W = geo.kern.W;
+  ia.wterm = wterm;
+  ia.chunks = d_chunks;
+  ia.item_off = d_item_off;
+  ia.items = nullptr;
+  count_items<<<grid1d(E), 256, 0, s>>>(ia, E);
+  FR_LAUNCHED();
+  FR_TRY(exclusive_scan(d_chunks, d_item_off, E, s));
+  // plane boundaries (g, p) -> item index
+  std::vector<int64_t> qpos;
+  lay->plane_base.assign(ngroups, 0);
+  for (int g = 0; g < ngroups; ++g) {
+    lay->plane_base[g] = (int)qpos.size();
+    for (int p = 0; p < pl[g]; ++p) qpos.push_back(ebase[g] + (int64_t)p * ntiles);
+  }
+  qpos.push_back(E);
+  const int nq = (int)qpos.size();
+  int64_t* d_qpos;
+  int* d_pitems;
+  FR_TRY(t.alloc(&d_qpos, nq));
+  FR_TRY(t.alloc(&d_pitems, nq));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_qpos, qpos.data(), nq * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  gather_plane_items<<<(nq + 255) / 256, 256, 0, s>>>(d_item_off, d_qpos, nq, d_pitems);
+  FR_LAUNCHED();
+  std::vector<int> pitems(nq);
+  FR_CUDA_TRY(cudaMemcpyAsync(pitems.data(), d_pitems, nq * sizeof(int), cudaMemcpyDeviceToHost, s));
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  lay->plane_items.assign(pitems.begin(), pitems.end());
+  lay->nitems = pitems[nq - 1];
+  FR_TRY(dalloc(&lay->items, lay->nitems, &acc));
+  ia.items = lay->items;
+  if (lay->nitems > 0) {
+    emit_items<<<grid1d(E), 256, 0, s>>>(ia, E);
+    FR_LAUNCHED();
+  }
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  lay->bytes = acc;
+  return FR_OK;
+}
+
+// --------------------------------------------------------------------------- tables
+struct TableArgs {
+  int nx, ny;
+  double dl, dm;
+  int wterm, nterm;
+  double t_c, t_half, dw;
+  const double* inv_phi_u;  // [nx] 1 / Phi_u(px / Nu)
+  const double* inv_phi_v;  // [ny]
+  const double* gl_x;       // quadrature nodes on [-1, 1]
+  const double* gl_w;
+  int nq;
+  double beta, hw;          // kernel shape, half width W/2
+  float* corr;
+  int32_t* tq;
+};
+
+__global__ void make_tables_kernel(TableArgs a) {
+  const int64_t n = (int64_t)a.nx * a.ny;
+  for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < n;
+       pix += (int64_t)gridDim.x * blockDim.x) {
+    const int jx = (int)(pix / a.ny), jy = (int)(pix - (int64_t)jx * a.ny);
+    const int px = jx - a.nx / 2, py = jy - a.ny / 2;
+    const double l = px * a.dl, m = py * a.dm;
+    const double r2 = l * l + m * m;
+    if (r2 >= 1.0) {
+      a.corr[pix] = 0.f;
+      if (a.tq) a.tq[pix] = 0;
+      continue;
+    }
+    const double nn = sqrt(1.0 - r2);
+    double c = a.inv_phi_u[jx] * a.inv_phi_v[jy];
+    if (a.nterm) c /= nn;
+    if (a.wterm) {
+      const double t = -r2 / (1.0 + nn);  // n - 1 without cancellation
+      const double tp = t - a.t_c;
+      a.tq[pix] = (int32_t)llrint(tp / a.t_half * 1073741824.0);
+      // Phi_w(dw * tp) = (W/2) int_{-1}^{1} exp(beta (sqrt(1 - z^2) - 1)) cos(pi k W z) dz
+      const double k = a.dw * tp;
+      double phi = 0.0;
+      for (int q = 0; q < a.nq; ++q) {
+        const double z = a.gl_x[q];
+        phi += a.gl_w[q] * exp(a.beta * (sqrt(1.0 - z * z) - 1.0)) * cos(M_PI * k * 2.0 * a.hw * z);
+      }
+      phi *= a.hw;
+      c /= phi;
+    }
+    if ((px + py) & 1) c = -c;
+    a.corr[pix] = (float)c;
+  }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n)
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) {
+        // recompute derivative at the converged node
+        p0 = 1.0;
+        p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        break;
+      }
+      x[i] = z;
+      w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+}
+
+// Fourier transform of the kernel at k cycles per cell (host, FP64)
+double es_ft(double beta, int W, double k, const std::vector<double>& x,
+             const std::vector<double>& w) {
+  const double hw = 0.5 * W;
+  double s = 0.0;
+  for (size_t q = 0; q < x.size(); ++q)
+    s += w[q] * std::exp(beta * (std::sqrt(1.0 - x[q] * x[q]) - 1.0)) * std::cos(M_PI * k * 2.0 * hw * x[q]);
+  return s * hw;
+}
+
+int make_tables(Geometry* geo, const std::vector<double>& inv_phi_u,
+                const std::vector<double>& inv_phi_v, cudaStream_t s) {
+  const int64_t n = (int64_t)geo->nx * geo->ny;
+  std::vector<double> gx, gw;
+  gauss_legendre(4 * geo->kern.W + 32, gx, gw);
+  Temps t;
+  double *d_pu, *d_pv, *d_gx, *d_gw;
+  FR_TRY(t.alloc(&d_pu, geo->nx));
+  FR_TRY(t.alloc(&d_pv, geo->ny));
+  FR_TRY(t.alloc(&d_gx, gx.size()));
+  FR_TRY(t.alloc(&d_gw, gw.size()));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_pu, inv_phi_u.data(), geo->nx * sizeof(double), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_pv, inv_phi_v.data(), geo->ny * sizeof(double), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_gx, gx.data(), gx.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(d_gw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  FR_TRY(dalloc(&geo->corr, n, nullptr));
+  if (geo->wterm) FR_TRY(dalloc(&geo->tq, n, nullptr));
+  TableArgs a;
+  a.nx = geo->nx;
+  a.ny = geo->ny;
+  a.dl = geo->dl;
+  a.dm = geo->dm;
+  a.wterm = geo->wterm;
+  a.nterm = geo->nterm;
+  a.t_c = geo->t_c;
+  a.t_half = geo->t_half;
+  a.dw = geo->dw;
+  a.inv_phi_u = d_pu;
+  a.inv_phi_v = d_pv;
+  a.gl_x = d_gx;
+  a.gl_w = d_gw;
+  a.nq = (int)gx.size();
+  a.beta = geo->beta;
+  a.hw = 0.5 * geo->kern.W;
+  a.corr = geo->corr;
+  a.tq = geo->tq;
+  make_tables_kernel<<<grid1d(n), 256, 0, s>>>(a);
+  FR_LAUNCHED();
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+void kernel_ft_tables(const Geometry& geo, std::vector<double>& inv_u, std::vector<double>& inv_v) {
+  std::vector<double> gx, gw;
+  gauss_legendre(4 * geo.kern.W + 32, gx, gw);
+  inv_u.resize(geo.nx);
+  inv_v.resize(geo.ny);
+  for (int j = 0; j < geo.nx; ++j)
+    inv_u[j] = 1.0 / es_ft(geo.beta, geo.kern.W, (double)(j - geo.nx / 2) / geo.Nu, gx, gw);
+  for (int j = 0; j < geo.ny; ++j)
+    inv_v[j] = 1.0 / es_ft(geo.beta, geo.kern.W, (double)(j - geo.ny / 2) / geo.Nv, gx, gw);
+}
+
+double plane_w(const Geometry& geo, const VisLayout& lay, int g, int p) {
+  return lay.w_lo[g] + (p - 0.5 * geo.kern.W) * geo.dw;
+}
+
+long long plane_k64(const Geometry& geo, double w_plane) {
+  // phase(pix) = w_p (t - t_c) = tq * K with K = w_p t_half 2^-30 cycles; Q64: K * 2^64
+  return (long long)llround(w_plane * geo.t_half * 17179869184.0);
+}
+
+// ------------------------------------------------------------------------------- TMA
+int make_tmap(CUtensorMap* m, float2* grid, int Nu, int Nv, int W) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      set_error("cuTensorMapEncodeTiled unavailable");
+      return FR_ECUDA;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)2 * Nv, (cuuint64_t)Nu};
+  cuuint64_t strides[1] = {(cuuint64_t)Nv * sizeof(float2)};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * box_v(W)), (cuuint32_t)box_u(W)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)grid, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FR_ECUDA;
+  }
+  return FR_OK;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: gives up after ~2^20 polls with back-off (well above a microsecond copy)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    if (mbar_try_wait(bar, phase)) return true;
+    if (it > 64) __nanosleep(256);
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------- degrid
+struct MetaPtrs {
+  const uint32_t* cell;
+  const float* du;
+  const float* dv;
+  const float* dw;
+  const uint32_t* ph;
+  const uint32_t* perm;
+};
+
+template <int W>
+__device__ __forceinline__ void kernel_weights(const EsKernel& k, float d, float* out) {
+#pragma unroll
+  for (int a = 0; a < W; ++a) out[a] = es_eval(k, d - (float)a);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                     const int4* __restrict__ items, MetaPtrs m,
+                                                     EsKernel kern, int p, int wterm,
+                                                     float2* __restrict__ vacc,
+                                                     float2* __restrict__ vis_out, int* status) {
+  constexpr int BU = TILE + W - 1;
+  constexpr int BV = (TILE + W - 1 + 1) & ~1;
+  __shared__ __align__(128) float2 tile[BU * BV];
+  __shared__ __align__(8) uint64_t mbar;
+  const int4 it = items[blockIdx.x];
+  const int tu = it.z >> 16, tv = it.z & 0xffff;
+  const uint32_t bar = smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)(BU * BV * sizeof(float2)))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tile)),
+        "l"((uint64_t)&tmap), "r"(2 * TILE * tv), "r"(TILE * tu), "r"(bar)
+        : "memory");
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0)) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, ST_TIMEOUT);
+      mbar_wait_bounded(bar, 0);  // let the copy in flight land before the CTA exits
+    }
+    return;
+  }
+  const int end = it.x + it.y;
+  for (int i = it.x + threadIdx.x; i < end; i += blockDim.x) {
+    const uint32_t cell = m.cell[i];
+    const int ru = (int)(cell >> 18) - tu * TILE;
+    const int rv = (int)((cell >> 4) & 0x3fff) - tv * TILE;
+    float ku[W], kv[W];
+    kernel_weights<W>(kern, m.du[i], ku);
+    kernel_weights<W>(kern, m.dv[i], kv);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      const float2* row = tile + (ru + a) * BV + rv;
+      float2 ra = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
+        const float2 g = row[b];
+        ra.x = fmaf(kv[b], g.x, ra.x);
+        ra.y = fmaf(kv[b], g.y, ra.y);
+      }
+      acc.x = fmaf(ku[a], ra.x, acc.x);
+      acc.y = fmaf(ku[a], ra.y, acc.y);
+    }
+    int rel = 0;
+    if (wterm) {
+      rel = (p - (int)(cell & 15)) & 15;
+      const float kw = es_eval(kern, m.dw[i] - (float)rel);
+      acc.x *= kw;
+      acc.y *= kw;
+      if (rel > 0) {
+        const float2 prev = vacc[i];
+        acc.x += prev.x;
+        acc.y += prev.y;
+      }
+    }
+    if (!wterm || rel == W - 1) {
+      if (wterm) {
+        // exp(-2 pi i w t_c)
+        const float f = (float)(int)m.ph[i] * 2.3283064365386963e-10f;
+        float s, c;
+        sincospif(2.f * f, &s, &c);
+        acc = make_float2(acc.x * c + acc.y * s, acc.y * c - acc.x * s);
+      }
+      const uint32_t pm = m.perm[i];
+      if (pm >> 31) acc.y = -acc.y;
+      vis_out[pm & 0x7fffffffu] = acc;
+    } else {
+      vacc[i] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ grid
+template <int W>
+__global__ void __launch_bounds__(256) grid_kernel(const int4* __restrict__ items, MetaPtrs m,
+                                                   EsKernel kern, int p, int wterm,
+                                                   const float2* __restrict__ y,
+                                                   float2* __restrict__ grid, int Nu, int Nv) {
+  constexpr int BU = TILE + W - 1;
+  constexpr int BV = (TILE + W - 1 + 1) & ~1;
+  __shared__ float sre[BU * BV], sim[BU * BV];
+  for (int i = threadIdx.x; i < BU * BV; i += blockDim.x) {
+    sre[i] = 0.f;
+    sim[i] = 0.f;
+  }
+  __syncthreads();
+  const int4 it = items[blockIdx.x];
+  const int tu = it.z >> 16, tv = it.z & 0xffff;
+  const int end = it.x + it.y;
+  for (int i = it.x + threadIdx.x; i < end; i += blockDim.x) {
+    const uint32_t cell = m.cell[i];
+    const int ru = (int)(cell >> 18) - tu * TILE;
+    const int rv = (int)((cell >> 4) & 0x3fff) - tv * TILE;
+    float ku[W], kv[W];
+    kernel_weights<W>(kern, m.du[i], ku);
+    kernel_weights<W>(kern, m.dv[i], kv);
+    float2 val = y[i];
+    if (wterm) {
+      const int rel = (p - (int)(cell & 15)) & 15;
+      const float kw = es_eval(kern, m.dw[i] - (float)rel);
+      val.x *= kw;
+      val.y *= kw;
+    }
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      const float vr = val.x * ku[a], vi = val.y * ku[a];
+      const int base = (ru + a) * BV + rv;
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
+        atomicAdd(&sre[base + b], vr * kv[b]);
+        atomicAdd(&sim[base + b], vi * kv[b]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < BU * BV; idx += blockDim.x) {
+    const int r = idx / BV, c = idx - (idx / BV) * BV;
+    if (c >= BU) continue;
+    const float re = sre[idx], im = sim[idx];
+    if (re == 0.f && im == 0.f) continue;
+    const int gu = tu * TILE + r, gv = tv * TILE + c;
+    if (gu < Nu && gv < Nv) atomicAdd(&grid[(size_t)gu * Nv + gv], make_float2(re, im));
+  }
+}
+
+struct GridPrepArgs {
+  const uint32_t* perm;
+  const float* wgt;
+  const uint32_t* ph;
+  const float2* vis;  // user order, null = ones (PSF)
+  int apply_weights, wterm;
+  int64_t n;
+  float2* y;
+};
+
+__global__ void grid_prepare_kernel(GridPrepArgs a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t pm = a.perm[i];
+    float2 v = a.vis ? a.vis[pm & 0x7fffffffu] : make_float2(1.f, 0.f);
+    if (pm >> 31) v.y = -v.y;
+    if (a.apply_weights) {
+      const float w = a.wgt[i];
+      v.x *= w;
+      v.y *= w;
+    }
+    if (a.wterm) {
+      // exp(+2 pi i w t_c)
+      const float f = (float)(int)a.ph[i] * 2.3283064365386963e-10f;
+      float s, c;
+      sincospif(2.f * f, &s, &c);
+      v = make_float2(v.x * c - v.y * s, v.x * s + v.y * c);
+    }
+    a.y[i] = v;
+  }
+}
+
+int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, int apply_weights,
+                 float2* ysorted, cudaStream_t s) {
+  if (lay.nsorted == 0) return FR_OK;
+  GridPrepArgs a{lay.perm, lay.wgt, lay.ph, vis, apply_weights, geo.wterm ? 1 : 0, lay.nsorted,
+                 ysorted};
+  grid_prepare_kernel<<<grid1d(lay.nsorted), 256, 0, s>>>(a);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+#define FR_W_DISPATCH(W, F, ...)                           \
+  switch (W) {                                             \
+    case 4: return F<4>(__VA_ARGS__);                      \
+    case 5: return F<5>(__VA_ARGS__);                      \
+    case 6: return F<6>(__VA_ARGS__);                      \
+    case 7: return F<7>(__VA_ARGS__);                      \
+    case 8: return F<8>(__VA_ARGS__);                      \
+    case 9: return F<9>(__VA_ARGS__);                      \
+    case 10: return F<10>(__VA_ARGS__);                    \
+    case 11: return F<11>(__VA_ARGS__);                    \
+    case 12: return F<12>(__VA_ARGS__);                    \
+    case 13: return F<13>(__VA_ARGS__);                    \
+    case 14: return F<14>(__VA_ARGS__);                    \
+    case 15: return F<15>(__VA_ARGS__);                    \
+    case 16: return F<16>(__VA_ARGS__);                    \
+    default:                                               \
+      ::fr::set_error("kernel support %d unsupported", W); \
+      return FR_EUNSUPPORTED;                              \
+  }
+
+template <int W>
+static int launch_degrid(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n, int p,
+                         const CUtensorMap& tmap, float2* vacc, float2* vis_out, int* status,
+                         cudaStream_t s) {
+  MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
+  degrid_kernel<W><<<(unsigned)n, 256, 0, s>>>(tmap, lay.items + i0, m, geo.kern, p,
+                                               geo.wterm ? 1 : 0, vacc, vis_out, status);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+template <int W>
+static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n, int p,
+                       const float2* y, float2* grid, cudaStream_t s) {
+  MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
+  grid_kernel<W><<<(unsigned)n, 256, 0, s>>>(lay.items + i0, m, geo.kern, p, geo.wterm ? 1 : 0, y,
+                                             grid, geo.Nu, geo.Nv);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const CUtensorMap& tmap,
+                 float2* vacc, float2* vis_out, int* status, cudaStream_t s) {
+  const int q = lay.plane_base[g] + p;
+  const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
+  if (i1 <= i0) return FR_OK;
+  FR_W_DISPATCH(geo.kern.W, launch_degrid, geo, lay, i0, i1 - i0, p, tmap, vacc, vis_out, status, s);
+}
+
+int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const float2* ysorted,
+               float2* grid, cudaStream_t s) {
+  const int q = lay.plane_base[g] + p;
+  const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
+  if (i1 <= i0) return FR_OK;
+  FR_W_DISPATCH(geo.kern.W, launch_grid, geo, lay, i0, i1 - i0, p, ysorted, grid, s);
+}
+
+}  // namespace fr

@@ -1,0 +1,72 @@
+"""CPU-only checks of the native library: it loads, exports every declared symbol, and its FFT
+stage arithmetic (run on the host with the same code the kernels use) matches numpy.fft."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2406_09144_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2406_09144_gb300 import build
+    build.build()
+    return binding.load()
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"\b(fr_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_symbols()
+    assert "fr_plan_create" in names and "fr_psf_apply" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(binding.EXPORTS) <= names
+
+
+def test_error_strings(lib):
+    assert lib.fr_strerror(0) == b"success"
+    assert lib.fr_strerror(-1) == b"invalid argument"
+
+
+def test_plan_create_rejects_bad_sizes_without_gpu(lib):
+    # argument validation happens before any device work
+    h = ctypes.c_void_p()
+    uvw = np.zeros((4, 3))
+    f = np.array([1e9])
+    r = lib.fr_plan_create(uvw.ctypes.data, 4, f.ctypes.data, 1, None, 100, 64, 1e-5, 1e-5, 1e-5,
+                           0, None, ctypes.byref(h))
+    assert r == -4 and not h.value
+    r = lib.fr_plan_create(uvw.ctypes.data, 4, f.ctypes.data, 1, None, 64, 64, 1e-5, 1e-5, 1e-9,
+                           0, None, ctypes.byref(h))
+    assert r == -4
+    bad = uvw.copy()
+    bad[1, 0] = np.nan
+    r = lib.fr_plan_create(bad.ctypes.data, 4, f.ctypes.data, 1, None, 64, 64, 1e-5, 1e-5, 1e-5,
+                           0, None, ctypes.byref(h))
+    assert r == -1 and b"not finite" in lib.fr_last_error()
+
+
+@pytest.mark.parametrize("lg", list(range(1, 15)))
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_host_fft_stages_match_numpy(lib, lg, direction):
+    rng = np.random.default_rng(lg)
+    n = 1 << lg
+    x = (rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))).astype(np.complex64)
+    got = binding.selftest_fft_host(x, direction)
+    ref = np.fft.fft(x.astype(np.complex128), axis=1) if direction < 0 else \
+        np.fft.ifft(x.astype(np.complex128), axis=1) * n
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 2e-6 * max(1, lg / 4), err
