@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the fast-resolve measurement-operator hot path on synthetic data.
+
+One step = one major cycle plus one minor-cycle likelihood evaluation on the VLA-like
+single-channel workload (1024^2 sky at 0.1", 27 antennas, 8 h at 2 s = 5,054,400 visibilities,
+w-terms, natural weights, eps = 1e-5):
+    R      (degrid the sky to model visibilities)
+    R^dag N^-1 (grid the data visibilities to a residual/dirty image)
+    likelihood + gradient with the PSF convolution on the 2048^2 padded grid.
+Inputs are resident in HBM before timing; L2 is flushed (512 MB write) between timed steps,
+outside the timed events. value = grid+degrid Mvis/s = N_vis / (t_degrid + t_grid), summed
+over all ranks (weak scaling: every rank runs its own copy of the workload, no collective).
+
+--impl reference times the FP64 CPU oracle (direct sums) on the host cores on a bounded
+sample of the same workload and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid+degrid Mvis/s"
+UNIT = "Mvis/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fastresolve", choices=["fastresolve", "reference"])
+    ap.add_argument("--workload", default="vla", choices=["vla", "small", "meerkat"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_desc(obs, name):
+    return {
+        "workload": {
+            "vla": "VLA-like single channel: 1024^2 sky at 0.1 arcsec, 27 antennas (351 baselines), "
+                   "8 h at 2 s, 5,054,400 complex64 visibilities with w-terms, natural weights, "
+                   "FP32 NUFFT eps 1e-5; PSF convolution on the 2048^2 padded grid",
+            "small": "plain method, small: 128^2 sky, 1 channel at 1.4 GHz, 27 antennas, 4 h at 10 s "
+                     "(505,440 visibilities), w = 0; PSF on the 256^2 padded grid",
+            "meerkat": "MeerKAT-like multi-channel: 4096^2 sky per channel at 2 arcsec, 64 antennas, "
+                       "8 channels 856-1712 MHz, 8 h at 8 s (58,060,800 visibilities), w-terms; "
+                       "PSF convolution on 8192^2 padded grids",
+        }[name],
+        "nx": obs.nx, "ny": obs.ny, "nchan": obs.nchan, "nrow": obs.nrow, "nvis": obs.nvis,
+        "pixsize_rad": obs.pixsize, "eps": 1e-5,
+        "step": "R (degrid) + R^dag N^-1 (grid) + PSF likelihood/gradient",
+        "l2": "flushed between timed steps (512 MB write, outside the timed events)",
+    }
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_rate(obs, sky, seconds, seed=0):
+    """Time the FP64 direct-sum oracle on a bounded sample; return (Mvis/s, sample text, cores).
+
+    Degridding one visibility costs one O(N_pix) sum; gridding one pixel costs one O(N_vis)
+    sum. The whole-job rate is N_vis / (N_vis * tau_vis + N_pix * tau_pix)."""
+    from oracle import cdft
+    cdft.build()
+    rng = np.random.default_rng(seed)
+    npix = obs.nx * obs.ny
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    from paper_2406_09144_gb300 import synth
+    vis = synth.complex_gaussian((obs.nrow, obs.nchan), seed=1)
+    w32 = obs.weights.astype(np.float32)
+
+    def measure(nv, npx):
+        rows = rng.integers(0, obs.nrow, nv)
+        chans = rng.integers(0, obs.nchan, nv)
+        t0 = time.perf_counter()
+        cdft.degrid_at(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, rows, chans,
+                       wterm=obs.wterm)
+        tv = time.perf_counter() - t0
+        pix = rng.integers(0, npix, npx)
+        imgs = rng.integers(0, obs.nsky, npx)
+        t0 = time.perf_counter()
+        cdft.grid_at(vis, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, obs.nx, obs.ny, imgs, pix,
+                     weights=w32, nsky=obs.nsky, wterm=obs.wterm)
+        tp = time.perf_counter() - t0
+        return tv / nv, tp / npx
+
+    # a small pilot sizes the sample to about `seconds` of CPU work, split between directions
+    tau_v, tau_p = measure(16, 2)
+    nv = max(16, int(0.5 * seconds / max(tau_v, 1e-9)))
+    npx = max(2, int(0.5 * seconds / max(tau_p, 1e-9)))
+    tau_v, tau_p = measure(nv, npx)
+    total = obs.nvis * tau_v + npix * tau_p
+    rate = obs.nvis / total / 1e6
+    sample = (f"{nv} visibilities (each a {npix}-pixel FP64 direct sum) and {npx} pixels (each a "
+              f"{obs.nvis}-visibility sum) of the workload; rate = N_vis / (N_vis t_vis + N_pix t_pix)")
+    return rate, sample, cores
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2406_09144_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(category, workload):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(category)
+    if not e or e.get("source") != source_digest():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_2406_09144_gb300 import synth
+    obs = synth.observation(args.workload)
+    sky = synth.random_skies(obs.nsky, obs.nx, obs.ny, seed=0)
+    rates = []
+    per = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup):
+        oracle_rate(obs, sky, per, seed=100 + i)
+    t0 = time.perf_counter()
+    sample = cores = None
+    for i in range(args.steps):
+        r, sample, cores = oracle_rate(obs, sky, per, seed=i)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = float(statistics.median(rates))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_desc(obs, args.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"per step: {sample}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2406_09144_gb300 import build, synth
+    from paper_2406_09144_gb300 import binding as B
+    build.build()
+    B.load()
+
+    obs = synth.observation(args.workload)
+    w32 = obs.weights.astype(np.float32)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plan = B.Plan(obs.uvw, obs.freqs, obs.nx, obs.ny, obs.pixsize, weights=w32, eps=1e-5,
+                  wterm=obs.wterm, nterm=True, mfs=not obs.per_channel_sky)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+
+    sky_h = synth.random_skies(obs.nsky, obs.nx, obs.ny, seed=0).astype(np.float32)
+    vis_h = synth.complex_gaussian((obs.nrow, obs.nchan), seed=1).astype(np.complex64)
+    sky = torch.from_numpy(sky_h).to(dev)
+    vis = torch.from_numpy(vis_h).to(dev)
+    model = torch.empty(plan.vis_shape, dtype=torch.complex64, device=dev)
+    dirty = plan.grid(vis)
+    grad = torch.empty_like(dirty)
+    resid = torch.empty_like(dirty)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step(evs):
+        evs[0].record(stream)
+        plan.degrid(sky, out=model)
+        evs[1].record(stream)
+        plan.grid(vis, out=resid)
+        evs[2].record(stream)
+        plan.likelihood_grad(sky, dirty, grad=grad, want_value=False)
+        evs[3].record(stream)
+
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(mk())
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    B.profile_enable(True)
+    B.launch_count(reset=True)
+    events = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e = mk()
+        step(e)
+        events.append(e)
+    torch.cuda.synchronize()
+    launches = B.launch_count()
+    if ws > 1:
+        dist.barrier()
+    cats = B.profile_read()
+    B.profile_enable(False)
+    clk = clocks.stop()
+
+    t_deg = sum(e[0].elapsed_time(e[1]) for e in events)
+    t_grd = sum(e[1].elapsed_time(e[2]) for e in events)
+    t_psf = sum(e[2].elapsed_time(e[3]) for e in events)
+    t_step = sum(e[0].elapsed_time(e[3]) for e in events)
+    times = torch.tensor([t_deg + t_grd, t_psf, t_step], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    t_dg, t_psf, t_step = (float(x) for x in times.cpu())
+    value = ws * obs.nvis * args.steps / (t_dg * 1e-3) / 1e6
+    psf_mpix = ws * obs.nsky * obs.nx * obs.ny * args.steps / (t_psf * 1e-3) / 1e6
+
+    # roofline of the dominant kernel class
+    dom = max(cats, key=lambda k: cats[k][0])
+    dms, dby, dn = cats[dom]
+    peak, peak_kind = measured_peaks()
+    achieved = (dby / dn) / (dms / dn * 1e-3) / 1e9 if dn else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(dom, args.workload),
+                "algorithmic_bytes_per_launch": dby / max(dn, 1),
+                "avg_launch_ms": dms / max(dn, 1), "launches": int(dn),
+                "share_of_step": dms / max(t_step, 1e-9)}
+    kernels = {k: {"ms": v[0] / args.steps, "launches": int(v[2]) // args.steps,
+                   "GBps": (v[1] / (v[0] * 1e-3) / 1e9) if v[0] > 0 else None}
+               for k, v in cats.items() if v[2]}
+
+    # end to end through the C ABI with host buffers: H2D sky + vis, R and R^dag, D2H results
+    e2e = None
+    if True:
+        sky_p = torch.from_numpy(sky_h).pin_memory()
+        vis_p = torch.from_numpy(vis_h).pin_memory()
+        model_p = torch.empty(plan.vis_shape, dtype=torch.complex64).pin_memory()
+        dirty_p = torch.empty(plan.sky_shape, dtype=torch.float32).pin_memory()
+        sky_d = torch.empty_like(sky)
+        vis_d = torch.empty_like(vis)
+        out_d = torch.empty_like(dirty)
+
+        def e2e_step():
+            sky_d.copy_(sky_p, non_blocking=True)
+            vis_d.copy_(vis_p, non_blocking=True)
+            plan.degrid(sky_d, out=model)
+            model_p.copy_(model, non_blocking=True)
+            plan.grid(vis_d, out=out_d)
+            dirty_p.copy_(out_d, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        tt = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            b.synchronize()
+            tt += a.elapsed_time(b)
+        tt_t = torch.tensor([tt], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(tt_t, op=dist.ReduceOp.MAX)
+        tt = float(tt_t.item())
+        e2e = {"value": ws * obs.nvis * args.steps / (tt * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(sky_h.nbytes + vis_h.nbytes),
+               "d2h_bytes_per_step": int(model.numel() * 8 + dirty.numel() * 4),
+               "path": "pinned host sky + visibilities -> fr_degrid, fr_grid -> pinned host model "
+                       "visibilities + dirty image"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, sample, cores = oracle_rate(obs, sky_h.astype(np.float64), args.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded VLA-like array, Earth-rotation tracks, point+blob sky, "
+                    "Gaussian visibilities)",
+            "config": workload_desc(obs, args.workload),
+            "psf_apply_mpix_s": psf_mpix,
+            "degrid_ms": t_deg / args.steps if ws == 1 else None,
+            "grid_ms": t_grd / args.steps if ws == 1 else None,
+            "psf_likelihood_ms": t_psf / args.steps,
+            "plan_s": plan_s,
+            "plan": {k: info[k] for k in ("support", "wplanes_total", "work_items", "grid_nu")},
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -156,6 +156,18 @@ const char *fr_last_error(void);
  * (for launch accounting in benchmarks). */
 uint64_t fr_launch_count(int reset);
 
+/* Per-kernel-class launch timing for roofline reports (not part of the method). When enabled,
+ * every kernel launch of the library is bracketed by CUDA events on its launching stream and
+ * tagged with its algorithmic byte count (the bytes the operation must move at the API dtypes).
+ * fr_profile_enable(1) clears the accumulators; fr_profile_read synchronises on the recorded
+ * events and writes, for categories 0 .. ncat-1, the summed milliseconds, algorithmic bytes and
+ * launch counts (any output may be NULL); it returns the number of categories. Categories:
+ * 0 fft_rows, 1 fft_cols, 2 degrid, 3 grid, 4 psf_rows, 5 psf_cols, 6 vis_prep, 7 reduce;
+ * fr_profile_category(c) gives the name. */
+void fr_profile_enable(int on);
+int fr_profile_read(double *ms, double *bytes, uint64_t *launches, int32_t ncat);
+const char *fr_profile_category(int32_t cat);
+
 /* Host-only check of the FFT passes' Stockham index and butterfly arithmetic: transforms
  * `batch` sequences of 2^log2l complex values in place (interleaved float32 re, im) on the CPU
  * with the same stage code the kernels use. dir = -1 forward, +1 inverse (unnormalised).

@@ -74,6 +74,13 @@ def load(path: str = LIB_PATH):
     lib.fr_launch_count.argtypes = [ctypes.c_int]
     lib.fr_launch_count.restype = ctypes.c_uint64
     lib.fr_selftest_fft_host.argtypes = [P, I32, I32, I32]
+    lib.fr_profile_enable.argtypes = [ctypes.c_int]
+    lib.fr_profile_enable.restype = None
+    lib.fr_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_uint64), I32]
+    lib.fr_profile_read.restype = ctypes.c_int
+    lib.fr_profile_category.argtypes = [I32]
+    lib.fr_profile_category.restype = ctypes.c_char_p
     for name in ("fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
                  "fr_likelihood_grad", "fr_major_cycle", "fr_plan_get_info", "fr_plan_footprint",
                  "fr_plan_check", "fr_selftest_fft_host"):
@@ -89,6 +96,25 @@ def check(code: int):
 
 def launch_count(reset: bool = False) -> int:
     return int(load().fr_launch_count(1 if reset else 0))
+
+
+PROFILE_CATEGORIES = 8
+
+
+def profile_enable(on: bool = True):
+    """Bracket every library launch with CUDA events (per kernel class) until disabled."""
+    load().fr_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """{category: (milliseconds, algorithmic bytes, launches)} since profile_enable(True)."""
+    lib = load()
+    n = PROFILE_CATEGORIES
+    ms = (ctypes.c_double * n)()
+    by = (ctypes.c_double * n)()
+    nl = (ctypes.c_uint64 * n)()
+    lib.fr_profile_read(ms, by, nl, n)
+    return {lib.fr_profile_category(c).decode(): (ms[c], by[c], int(nl[c])) for c in range(n)}
 
 
 def selftest_fft_host(x: np.ndarray, direction: int) -> np.ndarray:

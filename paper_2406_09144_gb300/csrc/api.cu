@@ -27,6 +27,65 @@ void set_error(const char* fmt, ...) {
 const char* get_error() { return g_err.c_str(); }
 void count_launch(int n) { g_launches += (uint64_t)n; }
 
+// ------------------------------------------------------------------------ launch profiling
+namespace {
+struct ProfRec {
+  int cat;
+  double bytes;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_ev_pool;
+double g_prof_ms[PC_N], g_prof_bytes[PC_N];
+uint64_t g_prof_n[PC_N];
+
+cudaEvent_t take_event() {
+  if (!g_ev_pool.empty()) {
+    cudaEvent_t e = g_ev_pool.back();
+    g_ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void prof_drain_locked() {
+  for (ProfRec& r : g_prof) {
+    float ms = 0.f;
+    if (r.a && r.b && cudaEventSynchronize(r.b) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      g_prof_ms[r.cat] += ms;
+      g_prof_bytes[r.cat] += r.bytes;
+      g_prof_n[r.cat] += 1;
+    }
+    if (r.a) g_ev_pool.push_back(r.a);
+    if (r.b) g_ev_pool.push_back(r.b);
+  }
+  g_prof.clear();
+}
+}  // namespace
+
+ProfScope::ProfScope(int cat, cudaStream_t s, double bytes) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  if (g_prof.size() >= 8192) prof_drain_locked();
+  ProfRec r{cat, bytes, take_event(), take_event()};
+  if (!r.a || !r.b) return;
+  cudaEventRecord(r.a, s);
+  stream = s;
+  slot = (int)g_prof.size();
+  g_prof.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot < (int)g_prof.size()) cudaEventRecord(g_prof[slot].b, stream);
+}
+
 // ------------------------------------------------------------------------ reductions
 static constexpr int RED_T = 256;
 
@@ -61,6 +120,7 @@ __global__ void __launch_bounds__(RED_T) dot_kernel(const float* a, const float*
 int dot_images(const float* a, const float* b, size_t n, double scale, double* acc,
                cudaStream_t s) {
   if (n == 0) return FR_OK;
+  ProfScope ps(PC_REDUCE, s, (double)n * (b ? 8.0 : 4.0));
   dot_kernel<<<nblocks(n), RED_T, 0, s>>>(a, b, n, scale, acc);
   FR_LAUNCHED();
   return FR_OK;
@@ -74,6 +134,7 @@ __global__ void __launch_bounds__(RED_T) sub_kernel(const float* a, const float*
 
 int sub_images(const float* a, const float* b, float* out, size_t n, cudaStream_t s) {
   if (n == 0) return FR_OK;
+  ProfScope ps(PC_REDUCE, s, (double)n * 12.0);
   sub_kernel<<<nblocks(n), RED_T, 0, s>>>(a, b, out, n);
   FR_LAUNCHED();
   return FR_OK;
@@ -309,7 +370,9 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
 
 // ------------------------------------------------------------------------ plan creation
 static int choose_support(double eps) {
-  int W = (int)std::ceil(std::log10(1.0 / eps)) + 1;
+  // measured against the FP64 oracle: W = ceil(log10(1/eps)) + 1 left the relative L2 error of
+  // R at about 1.2 eps for eps = 1e-5; one more cell of support restores a margin
+  int W = (int)std::ceil(std::log10(1.0 / eps)) + 2;
   return std::min(16, std::max(4, W));
 }
 
@@ -594,6 +657,36 @@ uint64_t fr_launch_count(int reset) {
   return v;
 }
 
+void fr_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain_locked();
+  if (on) {
+    for (int c = 0; c < PC_N; ++c) {
+      g_prof_ms[c] = 0.0;
+      g_prof_bytes[c] = 0.0;
+      g_prof_n[c] = 0;
+    }
+  }
+  g_prof_on = on != 0;
+}
+
+int fr_profile_read(double* ms, double* bytes, uint64_t* launches, int32_t ncat) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain_locked();
+  for (int c = 0; c < ncat && c < PC_N; ++c) {
+    if (ms) ms[c] = g_prof_ms[c];
+    if (bytes) bytes[c] = g_prof_bytes[c];
+    if (launches) launches[c] = g_prof_n[c];
+  }
+  return PC_N;
+}
+
+const char* fr_profile_category(int32_t cat) {
+  static const char* names[PC_N] = {"fft_rows", "fft_cols", "degrid", "grid",
+                                    "psf_rows", "psf_cols", "vis_prep", "reduce"};
+  return (cat >= 0 && cat < PC_N) ? names[cat] : "unknown";
+}
+
 int fr_plan_create(const double* uvw, int64_t nrow, const double* freqs, int32_t nchan,
                    const float* weights, int32_t nx, int32_t ny, double pixsize_x, double pixsize_y,
                    double eps, uint32_t flags, void* stream, fr_plan_t* out) {
@@ -723,7 +816,10 @@ int fr_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, int32_
     float* gb = grad + b * n;
     FR_TRY(run_degrid(p, p->geo, p->lay, w, sb, w->tmp_vis, s));
     FR_TRY(run_grid(p, p->geo, p->lay, w, w->tmp_vis, 1, gb, w->grid, w->b1, w->vbuf, s, &w->grid_zero));
-    lik_kernel<<<nblocks(n), RED_T, 0, s>>>(sb, gb, dirty + b * n, n, w->red + b);
+    {
+      ProfScope ps(PC_REDUCE, s, (double)n * 16.0);
+      lik_kernel<<<nblocks(n), RED_T, 0, s>>>(sb, gb, dirty + b * n, n, w->red + b);
+    }
     FR_LAUNCHED();
   }
   if (value) {
@@ -755,6 +851,7 @@ int fr_major_cycle(fr_plan_t p, const float* sky, const float* dirty, float* res
   FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, 2 * sizeof(double), s));
   FR_TRY(run_degrid(p, p->geo, p->lay, w, sky, w->tmp_vis, s));
   if (vis_chi2 && p->lay.nsorted > 0) {
+    ProfScope ps(PC_REDUCE, s, (double)p->lay.nsorted * 24.0);
     chi2_kernel<<<nblocks(p->lay.nsorted), RED_T, 0, s>>>((const float2*)vis, w->tmp_vis, p->lay.wgt,
                                                           p->lay.perm, p->lay.nsorted, w->red + 1);
     FR_LAUNCHED();

@@ -163,17 +163,30 @@ static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG
 
 int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
                    const float2* twv, const float2* twu, cudaStream_t s) {
+  const double img = (double)a.nx * a.ny, half = (double)a.nx * a.Nv, full = (double)a.Nu * a.Nv;
   D1Op o1{sky, a.corr, a.tq, a.k64, a.wterm, b1, a.nx, a.ny, a.Nv};
-  FR_TRY(d1(ilog2(a.Nv), o1, twv, s));
+  {
+    // sky + corr (+ tq) in, half-transformed plane out
+    ProfScope ps(PC_FFT_ROWS, s, img * (8.0 + (a.wterm ? 4.0 : 0.0)) + half * 8.0);
+    FR_TRY(d1(ilog2(a.Nv), o1, twv, s));
+  }
   D2Op o2{b1, grid, a.nx, a.Nu, a.Nv};
+  ProfScope ps(PC_FFT_COLS, s, half * 8.0 + full * 8.0);
   return d2(ilog2(a.Nu), o2, twu, s);
 }
 
 int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
                   const float2* twu, const float2* twv, cudaStream_t s) {
+  const double img = (double)a.nx * a.ny, half = (double)a.nx * a.Nv, full = (double)a.Nu * a.Nv;
   G1Op o1{grid, b1, a.nx, a.Nu, a.Nv};
-  FR_TRY(g1(ilog2(a.Nu), o1, twu, s));
+  {
+    // grid in, grid zeroed, cropped plane out
+    ProfScope ps(PC_FFT_COLS, s, full * 16.0 + half * 8.0);
+    FR_TRY(g1(ilog2(a.Nu), o1, twu, s));
+  }
   G2Op o2{b1, dirty, a.corr, a.tq, a.k64, a.wterm, accumulate, a.nx, a.ny, a.Nv};
+  ProfScope ps(PC_FFT_ROWS, s,
+               half * 8.0 + img * (4.0 + (a.wterm ? 4.0 : 0.0) + (accumulate ? 8.0 : 4.0)));
   return g2(ilog2(a.Nv), o2, twv, s);
 }
 

@@ -188,11 +188,20 @@ static int pt(int lg, const TOp& op, int n, const float2* tw, cudaStream_t s) { 
 int psf_apply_passes(const PsfArgs& a, float2* h, const float2* tw_rows, const float2* tw_cols,
                      cudaStream_t s) {
   const int nrows = a.nimg * a.nx;
+  const double px = (double)nrows * a.ny, hs = (double)nrows * (a.ny + 1);
   P1Op o1{a.sky, a.ny, a.ny, h, a.hp, nrows, a.ny};
-  FR_TRY(p1(ilog2(2 * a.ny), o1, tw_rows, s));
+  {
+    ProfScope ps(PC_PSF_ROWS, s, px * 4.0 + hs * 8.0);
+    FR_TRY(p1(ilog2(2 * a.ny), o1, tw_rows, s));
+  }
   P2Op o2{h, a.hp, a.nx, a.ny, a.nsky, a.transfer};
-  FR_TRY(p2(ilog2(2 * a.nx), o2, a.nimg, tw_cols, s));
+  {
+    // half spectra in and out, transfer function (2nx x (ny+1) floats) once per image
+    ProfScope ps(PC_PSF_COLS, s, hs * 16.0 + (double)a.nimg * 2 * a.nx * (a.ny + 1) * 4.0);
+    FR_TRY(p2(ilog2(2 * a.nx), o2, a.nimg, tw_cols, s));
+  }
   P3Op o3{h, a.hp, a.ny, nrows, a.out, a.sky, a.dirty, a.value, a.nx, a.nsky, 1};
+  ProfScope ps(PC_PSF_ROWS, s, hs * 8.0 + px * (a.dirty ? 12.0 : 4.0));
   return p3(ilog2(2 * a.ny), o3, tw_rows, s);
 }
 

@@ -49,6 +49,27 @@ void count_launch(int n = 1);
 // device status word values (bitmask)
 enum : int { ST_TIMEOUT = 1 };
 
+// ------------------------------------------------------------------ launch profiling
+// Kernel classes timed with CUDA events on the launching stream when profiling is enabled
+// (fr_profile_enable); each launch also records its algorithmic bytes.
+enum ProfCat : int {
+  PC_FFT_ROWS = 0,  // grid FFT row passes (D1, G2)
+  PC_FFT_COLS,      // grid FFT column passes (D2, G1)
+  PC_DEGRID,        // degridder
+  PC_GRID,          // gridder
+  PC_PSF_ROWS,      // PSF-convolution row passes (P1, P3)
+  PC_PSF_COLS,      // PSF-convolution column pass (P2)
+  PC_PREP,          // visibility gather / weighting before gridding
+  PC_REDUCE,        // FP64 reductions and small elementwise kernels
+  PC_N
+};
+struct ProfScope {
+  int slot = -1;
+  cudaStream_t stream = nullptr;
+  ProfScope(int cat, cudaStream_t s, double bytes);
+  ~ProfScope();
+};
+
 // ------------------------------------------------------------------ kernel shape
 // Exponential-of-semicircle gridding kernel phi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)),
 // |x| <= W/2 in grid cells.
@@ -96,6 +117,7 @@ struct VisLayout {
   std::vector<int64_t> plane_items;     // [sum planes + 1] item ranges, (g, p) major
   std::vector<int> plane_base;          // [ngroups] index of (g, 0) in plane_items
   std::vector<int64_t> group_begin;     // [ngroups + 1] sorted index range of each group
+  std::vector<int64_t> plane_visits;    // [sum planes] visibilities processed per (g, p)
   int64_t nvis = 0;                     // visibilities in user order
   int64_t nsorted = 0;                  // kept after dropping
   int64_t ndropped = 0;

@@ -308,6 +308,20 @@ __global__ void emit_items(ItemArgs a, int64_t E) {
   }
 }
 
+__global__ void plane_visits_kernel(const int4* items, const int* pitems, long long* out) {
+  const int q = blockIdx.x;
+  long long s = 0;
+  for (int i = pitems[q] + threadIdx.x; i < pitems[q + 1]; i += blockDim.x) s += items[i].y;
+  __shared__ long long sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[q] = sh[0];
+}
+
 __global__ void gather_plane_items(const int* item_off, const int64_t* qpos, int nq, int* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nq) out[i] = item_off[qpos[i]];
@@ -574,6 +588,18 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   if (lay->nitems > 0) {
     emit_items<<<grid1d(E), 256, 0, s>>>(ia, E);
     FR_LAUNCHED();
+  }
+  // visibility visits per (group, plane), for launch accounting
+  lay->plane_visits.assign(nq - 1, 0);
+  if (nq > 1 && lay->nitems > 0) {
+    long long* d_visits;
+    FR_TRY(t.alloc(&d_visits, nq - 1));
+    plane_visits_kernel<<<nq - 1, 256, 0, s>>>(lay->items, d_pitems, d_visits);
+    FR_LAUNCHED();
+    std::vector<long long> hv(nq - 1);
+    FR_CUDA_TRY(cudaMemcpyAsync(hv.data(), d_visits, (nq - 1) * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < nq - 1; ++i) lay->plane_visits[i] = hv[i];
   }
   FR_CUDA_TRY(cudaStreamSynchronize(s));
   lay->bytes = acc;
@@ -982,6 +1008,8 @@ int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, i
   if (lay.nsorted == 0) return FR_OK;
   GridPrepArgs a{lay.perm, lay.wgt, lay.ph, vis, apply_weights, geo.wterm ? 1 : 0, lay.nsorted,
                  ysorted};
+  ProfScope ps(PC_PREP, s, (double)lay.nsorted * (4.0 + 8.0 + 8.0 + (apply_weights ? 4.0 : 0.0) +
+                                                  (geo.wterm ? 4.0 : 0.0)));
   grid_prepare_kernel<<<grid1d(lay.nsorted), 256, 0, s>>>(a);
   FR_LAUNCHED();
   return FR_OK;
@@ -1028,11 +1056,17 @@ static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, in
   return FR_OK;
 }
 
+// algorithmic bytes per visibility visit: cell, du, dv (, dw) in; accumulator / output traffic
+static double meta_bytes(const Geometry& geo) { return 12.0 + (geo.wterm ? 4.0 : 0.0); }
+
 int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const CUtensorMap& tmap,
                  float2* vacc, float2* vis_out, int* status, cudaStream_t s) {
   const int q = lay.plane_base[g] + p;
   const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
   if (i1 <= i0) return FR_OK;
+  // each grid cell read once, per visit: metadata + accumulator read/write (or output + perm)
+  ProfScope ps(PC_DEGRID, s,
+               (double)geo.Nu * geo.Nv * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 16.0));
   FR_W_DISPATCH(geo.kern.W, launch_degrid, geo, lay, i0, i1 - i0, p, tmap, vacc, vis_out, status, s);
 }
 
@@ -1041,6 +1075,9 @@ int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const fl
   const int q = lay.plane_base[g] + p;
   const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
   if (i1 <= i0) return FR_OK;
+  // each grid cell written once, per visit: metadata + weighted visibility
+  ProfScope ps(PC_GRID, s,
+               (double)geo.Nu * geo.Nv * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 8.0));
   FR_W_DISPATCH(geo.kern.W, launch_grid, geo, lay, i0, i1 - i0, p, ysorted, grid, s);
 }
 

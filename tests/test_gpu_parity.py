@@ -130,7 +130,8 @@ def test_dirty_image_matches_grid():
 
 @pytest.mark.parametrize("nx,ny,batch", [(32, 32, 1), (32, 64, 3), (64, 16, 2), (128, 128, 2)])
 def test_psf_apply_matches_direct_convolution(nx, ny, batch):
-    obs = synth.random_observation(1000, 1, nx, ny, 2e-3, seed=37)
+    # a 16-pixel axis has a 32-cell grid, so the kernel footprint limits |v| to ~0.3 / pixsize
+    obs = synth.random_observation(1000, 1, nx, ny, 2e-3, seed=37, umax_frac=0.3)
     plan = make_plan(obs)
     _, psf, _ = plan.dirty_psf(want_dirty=False)
     P = psf.cpu().numpy().astype(np.float64)
