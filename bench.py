@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fastresolve", choices=["fastresolve", "reference"])
-    ap.add_argument("--workload", default="vla", choices=["vla", "small", "meerkat"])
+    ap.add_argument("--workload", default="vla", choices=["vla", "small", "meerkat", "meerkat1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -66,6 +66,9 @@ def workload_desc(obs, name):
             "meerkat": "MeerKAT-like multi-channel: 4096^2 sky per channel at 2 arcsec, 64 antennas, "
                        "8 channels 856-1712 MHz, 8 h at 8 s (58,060,800 visibilities), w-terms; "
                        "PSF convolution on 8192^2 padded grids",
+            "meerkat1": "MeerKAT-like top channel alone: 4096^2 sky at 2 arcsec, 64 antennas, "
+                        "1658.5 MHz, 8 h at 8 s (7,257,600 visibilities), w-terms; PSF convolution "
+                        "on the 8192^2 padded grid",
         }[name],
         "nx": obs.nx, "ny": obs.ny, "nchan": obs.nchan, "nrow": obs.nrow, "nvis": obs.nvis,
         "pixsize_rad": obs.pixsize, "eps": 1e-5,

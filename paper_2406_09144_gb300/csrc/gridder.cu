@@ -919,55 +919,103 @@ __global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUt
 }
 
 // ------------------------------------------------------------------------------ grid
+// Gridder: one warp spreads one visibility at a time, lane l owning footprint cells
+// l, l + 32, ... (row a = idx / W, column b = idx % W), into the warp's private shared-memory
+// sub-grid, so no two threads ever update the same cell concurrently and no shared atomics are
+// needed. Lanes 0..W-1 evaluate phi(du - a), lanes W..2W-1 phi(dv - b); every lane fetches its
+// two factors by shuffle. The warps' sub-grids are summed at the end and the non-zero cells
+// added to the global grid with one vector atomic each.
+constexpr int GRID_WARPS = 8;
+
 template <int W>
-__global__ void __launch_bounds__(256) grid_kernel(const int4* __restrict__ items, MetaPtrs m,
-                                                   EsKernel kern, int p, int wterm,
-                                                   const float2* __restrict__ y,
-                                                   float2* __restrict__ grid, int Nu, int Nv) {
+constexpr size_t grid_smem_bytes() {
+  return (size_t)GRID_WARPS * (TILE + W - 1) * ((TILE + W) & ~1) * sizeof(float2);
+}
+
+template <int W>
+__global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __restrict__ items,
+                                                               MetaPtrs m, EsKernel kern, int p,
+                                                               int wterm,
+                                                               const float2* __restrict__ y,
+                                                               float2* __restrict__ grid, int Nu,
+                                                               int Nv) {
   constexpr int BU = TILE + W - 1;
   constexpr int BV = (TILE + W - 1 + 1) & ~1;
-  __shared__ float sre[BU * BV], sim[BU * BV];
-  for (int i = threadIdx.x; i < BU * BV; i += blockDim.x) {
-    sre[i] = 0.f;
-    sim[i] = 0.f;
-  }
-  __syncthreads();
+  constexpr int SUB = BU * BV;
+  constexpr int CELLS = W * W;
+  constexpr int NIT = (CELLS + 31) / 32;
+  extern __shared__ float2 sub[];  // [GRID_WARPS][SUB]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int4 it = items[blockIdx.x];
   const int tu = it.z >> 16, tv = it.z & 0xffff;
   const int end = it.x + it.y;
-  for (int i = it.x + threadIdx.x; i < end; i += blockDim.x) {
-    const uint32_t cell = m.cell[i];
-    const int ru = (int)(cell >> 18) - tu * TILE;
-    const int rv = (int)((cell >> 4) & 0x3fff) - tv * TILE;
-    float ku[W], kv[W];
-    kernel_weights<W>(kern, m.du[i], ku);
-    kernel_weights<W>(kern, m.dv[i], kv);
-    float2 val = y[i];
-    if (wterm) {
-      const int rel = (p - (int)(cell & 15)) & 15;
-      const float kw = es_eval(kern, m.dw[i] - (float)rel);
-      val.x *= kw;
-      val.y *= kw;
+  const int nused = min(GRID_WARPS, (it.y + 31) / 32);
+  for (int i = threadIdx.x; i < nused * SUB; i += blockDim.x) sub[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  float2* mysub = sub + warp * SUB;
+  int ca[NIT], cb[NIT];
+#pragma unroll
+  for (int k = 0; k < NIT; ++k) {
+    const int idx = lane + 32 * k;
+    ca[k] = idx / W;
+    cb[k] = idx % W;
+  }
+  for (int base = it.x + warp * 32; base < end; base += GRID_WARPS * 32) {
+    const int i = base + lane;
+    uint32_t cell = 0;
+    float du = 0.f, dv = 0.f;
+    float2 val = make_float2(0.f, 0.f);
+    if (i < end) {
+      cell = m.cell[i];
+      du = m.du[i];
+      dv = m.dv[i];
+      val = y[i];
+      if (wterm) {
+        const int rel = (p - (int)(cell & 15)) & 15;
+        const float kw = es_eval(kern, m.dw[i] - (float)rel);
+        val.x *= kw;
+        val.y *= kw;
+      }
     }
+    const int nb = min(32, end - base);
+    for (int j = 0; j < nb; ++j) {
+      const uint32_t cj = __shfl_sync(0xffffffffu, cell, j);
+      const float duj = __shfl_sync(0xffffffffu, du, j);
+      const float dvj = __shfl_sync(0xffffffffu, dv, j);
+      const float vr = __shfl_sync(0xffffffffu, val.x, j);
+      const float vi = __shfl_sync(0xffffffffu, val.y, j);
+      const int ru = (int)(cj >> 18) - tu * TILE;
+      const int rv = (int)((cj >> 4) & 0x3fff) - tv * TILE;
+      float kval = 0.f;
+      if (lane < 2 * W) kval = es_eval(kern, lane < W ? duj - (float)lane : dvj - (float)(lane - W));
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-      const float vr = val.x * ku[a], vi = val.y * ku[a];
-      const int base = (ru + a) * BV + rv;
-#pragma unroll
-      for (int b = 0; b < W; ++b) {
-        atomicAdd(&sre[base + b], vr * kv[b]);
-        atomicAdd(&sim[base + b], vi * kv[b]);
+      for (int k = 0; k < NIT; ++k) {
+        const float ku = __shfl_sync(0xffffffffu, kval, ca[k] & 31);
+        const float kv = __shfl_sync(0xffffffffu, kval, W + cb[k]);
+        if (lane + 32 * k < CELLS) {
+          float2* c = mysub + (ru + ca[k]) * BV + rv + cb[k];
+          const float wgt = ku * kv;
+          float2 g = *c;
+          g.x = fmaf(wgt, vr, g.x);
+          g.y = fmaf(wgt, vi, g.y);
+          *c = g;
+        }
       }
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < BU * BV; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < SUB; idx += blockDim.x) {
     const int r = idx / BV, c = idx - (idx / BV) * BV;
     if (c >= BU) continue;
-    const float re = sre[idx], im = sim[idx];
-    if (re == 0.f && im == 0.f) continue;
+    float2 acc = sub[idx];
+    for (int w = 1; w < nused; ++w) {
+      const float2 o = sub[w * SUB + idx];
+      acc.x += o.x;
+      acc.y += o.y;
+    }
+    if (acc.x == 0.f && acc.y == 0.f) continue;
     const int gu = tu * TILE + r, gv = tv * TILE + c;
-    if (gu < Nu && gv < Nv) atomicAdd(&grid[(size_t)gu * Nv + gv], make_float2(re, im));
+    if (gu < Nu && gv < Nv) atomicAdd(&grid[(size_t)gu * Nv + gv], acc);
   }
 }
 
@@ -1050,8 +1098,16 @@ template <int W>
 static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n, int p,
                        const float2* y, float2* grid, cudaStream_t s) {
   MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
-  grid_kernel<W><<<(unsigned)n, 256, 0, s>>>(lay.items + i0, m, geo.kern, p, geo.wterm ? 1 : 0, y,
-                                             grid, geo.Nu, geo.Nv);
+  constexpr size_t smem = grid_smem_bytes<W>();
+  static bool attr = false;
+  if (!attr) {
+    FR_CUDA_TRY(cudaFuncSetAttribute(grid_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    attr = true;
+  }
+  grid_kernel<W><<<(unsigned)n, GRID_WARPS * 32, smem, s>>>(lay.items + i0, m, geo.kern, p,
+                                                            geo.wterm ? 1 : 0, y, grid, geo.Nu,
+                                                            geo.Nv);
   FR_LAUNCHED();
   return FR_OK;
 }

@@ -37,8 +37,9 @@ def vla_like_enu(seed: int = 1, n_per_arm: int = 9, arm_km: float = 21.0) -> np.
 
 
 def meerkat_like_enu(seed: int = 1, nant: int = 64, core_frac: float = 0.7,
-                     core_km: float = 1.0, outer_km: float = 8.0) -> np.ndarray:
-    """Dense core (70% of dishes within 1 km) plus a sparse ring out to 8 km. ENU metres [nant, 3]."""
+                     core_km: float = 1.0, outer_km: float = 4.0) -> np.ndarray:
+    """Dense core (70% of dishes within 1 km) plus outer dishes out to 4 km radius (baselines up
+    to about 8 km, as for MeerKAT). ENU metres [nant, 3]."""
     rng = np.random.default_rng(seed)
     ncore = int(round(core_frac * nant))
     r_core = core_km * 1e3 * np.sqrt(rng.uniform(0.0, 1.0, ncore))
@@ -189,10 +190,12 @@ def observation(name: str, seed_array: int = 1, seed_noise: int = 2, hours=None,
         sig = baseline_sigmas(uvw.shape[0], nbl, 1e-2, seed_noise)[:, None]
         wterm = True
         per_chan = False
-    elif name == "meerkat":
+    elif name in ("meerkat", "meerkat1"):
         enu = meerkat_like_enu(seed_array)
         uvw = earth_rotation_uvw(enu, -30.7, -60.5, hours or 8.0, step_s or 8.0)
         freqs = 909.5e6 + 107e6 * np.arange(8)
+        if name == "meerkat1":  # the top channel alone (7,257,600 visibilities)
+            freqs = freqs[-1:]
         nx = ny = 4096
         pix = 2.0 * ARCSEC
         nbl = len(enu) * (len(enu) - 1) // 2
@@ -208,7 +211,7 @@ def observation(name: str, seed_array: int = 1, seed_noise: int = 2, hours=None,
 
 
 def random_observation(nrow: int, nchan: int, nx: int, ny: int, pixsize: float, seed: int,
-                       umax_frac: float = 0.45, wmax_cycles: float = 0.0, f0: float = 1.0e9,
+                       umax_frac: float = 0.35, wmax_cycles: float = 0.0, f0: float = 1.0e9,
                        per_channel_sky: bool = False, weights: bool = True) -> Observation:
     """Uniformly scattered uvw for small parity cases.
 
