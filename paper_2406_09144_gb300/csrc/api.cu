@@ -428,7 +428,7 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
   }
   if (r == FR_OK) r = zero_psf_edges(p->psf_img, p->nsky, pg.nx, pg.ny, s);
   if (r == FR_OK)
-    r = build_transfer(p->geo.nx, p->geo.ny, p->nsky, p->psf_img, h, hp, p->transfer,
+    r = build_transfer(p->geo.nx, p->geo.ny, p->nsky, p->psf_img, h, p->transfer,
                        p->tw[ilog2(pg.ny)], p->tw[ilog2(pg.nx)], s);
   // psf_norm = sum of the kept weights per image (FP64)
   double* d_norm = nullptr;
@@ -764,7 +764,8 @@ static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, 
   FR_TRY(get_ws(p, s, &w));
   const int nimg = batch * p->nsky;
   const int hp = p->geo.ny + 2;
-  FR_TRY(ws_reserve_h(w, (size_t)nimg * p->geo.nx * hp));
+  const size_t hsize = (size_t)nimg * p->geo.nx * hp;  // H, then HT ([nimg][ny+1][nx])
+  FR_TRY(ws_reserve_h(w, hsize + (size_t)nimg * (p->geo.ny + 1) * p->geo.nx));
   PsfArgs a;
   a.nx = p->geo.nx;
   a.ny = p->geo.ny;
@@ -781,7 +782,8 @@ static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, 
     FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, batch * sizeof(double), s));
     a.value = w->red;
   }
-  FR_TRY(psf_apply_passes(a, w->h, p->tw[ilog2(2 * a.ny)], p->tw[ilog2(2 * a.nx)], s));
+  FR_TRY(psf_apply_passes(a, w->h, w->h + hsize, p->tw[ilog2(2 * a.ny)], p->tw[ilog2(2 * a.nx)],
+                          s));
   if (dirty && value) {
     FR_CUDA_TRY(cudaMemcpyAsync(value, w->red, batch * sizeof(double), cudaMemcpyDeviceToHost, s));
     FR_CUDA_TRY(cudaStreamSynchronize(s));

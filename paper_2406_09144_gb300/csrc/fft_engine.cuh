@@ -1,10 +1,13 @@
-// Shared-memory FFT engine and the generic row / column pass kernels.
+// Shared-memory FFT engine and the generic FFT pass kernel.
 //
-// A CTA holds B sequences of length L = 2^LOG2L in shared memory (sequence b at b * LP,
-// element i at spad(i)), 16 complex points per thread, and runs the Stockham stages of
-// fft_core.cuh with register-held butterflies. Row passes read rows that are contiguous in
-// global memory; column passes read B adjacent columns (coalesced across the B columns of each
-// row) and transpose them into the same shared layout.
+// Every pass reads the sequences it transforms from contiguous memory: a CTA loads B
+// sequences of length L = 2^LOG2L (register-staged, 16 complex values per thread, all loads in
+// flight before the first shared-memory store), runs the Stockham stages of fft_core.cuh
+// on them in shared memory (sequence b at b * LP, element i at spad(i)), and hands them to the
+// pass's store, which writes either along the sequence (row-major) or across the B sequences
+// (transposed: consecutive threads write consecutive sequences of one output index). The
+// transposed store is how a pass produces the layout the next pass reads contiguously, so no
+// pass ever reads a column.
 #pragma once
 #include "fr_internal.cuh"
 
@@ -13,10 +16,12 @@ namespace fr {
 template <int LOG2L>
 struct FftCfg {
   static constexpr int L = 1 << LOG2L;
-  static constexpr int B = (L >= 4096) ? 1 : 4096 / L;   // sequences per CTA
-  static constexpr int NT = (B * L) / 16;                 // threads: 16 points each
-  static constexpr int LP = spad_len(L) + 1;              // odd stride between sequences
+  // two sequences per CTA for the long transforms keep transposed stores 16 bytes wide
+  static constexpr int B = (L >= 16384) ? 1 : (L >= 4096 ? 2 : 4096 / L);
+  static constexpr int NT = (B * L) / 16;     // threads: 16 points each
+  static constexpr int LP = spad_len(L) + 1;  // odd stride between sequences
   static constexpr size_t SMEM = size_t(B) * LP * sizeof(float2);
+  static constexpr int MINB = NT >= 1024 ? 1 : 2;
 };
 
 constexpr int ns_before(int log2l, int st) {
@@ -80,113 +85,87 @@ struct SeqView {
   __device__ __forceinline__ float2 operator[](int i) const { return p[spad(i)]; }
 };
 
-// Row pass: sequences are rows. Op provides
-//   float2 load(int seq, int i)                      for i in [0, L)
-//   int nout() const; double store(int seq, int o, SeqView v)   for o in [0, nout)
-//   int nseq() const; void finish(int seq0, double acc)  (per-thread sum of store results)
-template <int LOG2L, int DIR, class Op>
-__global__ void __launch_bounds__(FftCfg<LOG2L>::NT) fft_rows_kernel(Op op,
-                                                                      const float2* __restrict__ tw) {
+// Generic pass. blockIdx.x selects B consecutive sequences, blockIdx.y an image (ops that batch
+// images use it). Op provides:
+//   static constexpr bool TRANSPOSED   store mapping (see above)
+//   static constexpr bool TWO          second transform (DIR2) after mid()
+//   int nseq() const, int nout() const      (host and device)
+//   float2 load(int seq, int i)        element i of the sequence (zero padding costs no load)
+//   void after_load(int seq0, int nb)  after every thread's loads have landed
+//   void mid(float2* s, int seq0)      between the transforms (TWO)
+//   double store(int seq, int o, SeqView v)   o < nout(); per-thread results are summed
+//   void finish(int seq0, double acc)
+template <int LOG2L, int DIR, int DIR2, class Op>
+__global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB)
+    fft_pass_kernel(Op op, const float2* __restrict__ tw) {
   using C = FftCfg<LOG2L>;
   constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
+  constexpr int PER = B * L / NT;
   extern __shared__ float2 smem[];
   const int nseq = op.nseq();
   const int seq0 = blockIdx.x * B;
-  for (int idx = threadIdx.x; idx < B * L; idx += NT) {
+  float2 r[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + k * NT;
     const int b = idx / L, i = idx % L;
-    const int sq = seq0 + b;
-    smem[b * LP + spad(i)] = (sq < nseq) ? op.load(sq, i) : make_float2(0.f, 0.f);
+    r[k] = (seq0 + b < nseq) ? op.load(seq0 + b, i) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + k * NT;
+    smem[(idx / L) * LP + spad(idx % L)] = r[k];
   }
   __syncthreads();
+  op.after_load(seq0, min(B, nseq - seq0));
   fft_stages<LOG2L, 0, DIR>(smem, tw);
-  const int nout = op.nout();
-  double acc = 0.0;
-  for (int idx = threadIdx.x; idx < B * nout; idx += NT) {
-    const int b = idx / nout, o = idx % nout;
-    const int sq = seq0 + b;
-    if (sq < nseq) acc += op.store(sq, o, SeqView{smem + b * LP});
-  }
-  op.finish(seq0, acc);
-}
-
-// Column pass: sequences are columns; blockIdx.y selects an image for ops that batch images.
-// Op provides
-//   float2 load(int i, int col)   i in [0, L)
-//   void after_load(int col0)     (e.g. zero the source once every CTA thread has loaded)
-//   void mid(float2* s, int col0) (between the two transforms when TWO is set)
-//   int nout() const; void store(int o, int col, SeqView v)
-//   int ncol() const
-template <int LOG2L, int DIR, int DIR2, bool TWO, class Op>
-__global__ void __launch_bounds__(FftCfg<LOG2L>::NT) fft_cols_kernel(Op op,
-                                                                      const float2* __restrict__ tw) {
-  using C = FftCfg<LOG2L>;
-  constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
-  extern __shared__ float2 smem[];
-  const int ncol = op.ncol();
-  const int col0 = blockIdx.x * B;
-  for (int idx = threadIdx.x; idx < B * L; idx += NT) {
-    const int i = idx / B, c = idx % B;
-    const int col = col0 + c;
-    smem[c * LP + spad(i)] = (col < ncol) ? op.load(i, col) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  op.after_load(col0);
-  fft_stages<LOG2L, 0, DIR>(smem, tw);
-  if constexpr (TWO) {
-    op.mid(smem, col0);
+  if constexpr (Op::TWO) {
+    op.template mid<B, NT, L, LP>(smem, seq0);
     __syncthreads();
     fft_stages<LOG2L, 0, DIR2>(smem, tw);
   }
   const int nout = op.nout();
-  for (int idx = threadIdx.x; idx < B * nout; idx += NT) {
-    const int o = idx / B, c = idx % B;
-    const int col = col0 + c;
-    if (col < ncol) op.store(o, col, SeqView{smem + c * LP});
+  double acc = 0.0;
+  if constexpr (Op::TRANSPOSED) {
+    for (int idx = threadIdx.x; idx < B * nout; idx += NT) {
+      const int o = idx / B, b = idx % B;
+      if (seq0 + b < nseq) acc += op.store(seq0 + b, o, SeqView{smem + b * LP});
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < B * nout; idx += NT) {
+      const int b = idx / nout, o = idx % nout;
+      if (seq0 + b < nseq) acc += op.store(seq0 + b, o, SeqView{smem + b * LP});
+    }
   }
+  op.finish(seq0, acc);
 }
 
-// The column kernel calls op.after_load(col0) and op.mid(smem, col0); ops implement them as
-// templates on the CTA shape, which this wrapper fixes.
-template <int LOG2L, class Op>
-struct ColOp : Op {
-  using C = FftCfg<LOG2L>;
-  __device__ void after_load(int col0) const { Op::template after_load<C::B, C::NT, C::L>(col0); }
-  __device__ void mid(float2* s, int col0) const {
-    Op::template mid<C::B, C::NT, C::L, C::LP>(s, col0);
-  }
-};
-
-template <int LOG2L, int DIR, class Op>
-int launch_rows(const Op& op, const float2* tw, cudaStream_t s) {
+template <int LOG2L, int DIR, int DIR2, class Op>
+int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
   using C = FftCfg<LOG2L>;
   const int nblk = (op.nseq() + C::B - 1) / C::B;
-  if (nblk == 0) return FR_OK;
-  auto kern = fft_rows_kernel<LOG2L, DIR, Op>;
-  static bool attr = false;
-  if (!attr) {
-    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
-    attr = true;
-  }
-  kern<<<nblk, C::NT, C::SMEM, s>>>(op, tw);
-  FR_LAUNCHED();
-  return FR_OK;
-}
-
-template <int LOG2L, int DIR, int DIR2, bool TWO, class Op>
-int launch_cols(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
-  using C = FftCfg<LOG2L>;
-  const int nblk = (op.ncol() + C::B - 1) / C::B;
   if (nblk == 0 || nimg == 0) return FR_OK;
-  auto kern = fft_cols_kernel<LOG2L, DIR, DIR2, TWO, Op>;
+  auto kern = fft_pass_kernel<LOG2L, DIR, DIR2, Op>;
   static bool attr = false;
   if (!attr) {
     FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr = true;
   }
   kern<<<dim3(nblk, nimg), C::NT, C::SMEM, s>>>(op, tw);
   FR_LAUNCHED();
   return FR_OK;
 }
+
+// Defaults for the optional parts of an op.
+struct OpBase {
+  static constexpr bool TRANSPOSED = false;
+  static constexpr bool TWO = false;
+  __device__ void after_load(int, int) const {}
+  template <int B, int NT, int L, int LP>
+  __device__ void mid(float2*, int) const {}
+  __device__ void finish(int, double) const {}
+};
 
 // Dispatch a templated functor on a runtime log2 length in [5, 14].
 #define FR_LOG2_DISPATCH(log2l, F, ...)                      \

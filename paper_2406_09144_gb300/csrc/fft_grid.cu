@@ -1,17 +1,22 @@
 // FFT passes of the measurement operator R and its adjoint (Eq. rime, Eq. clean).
 //
-// Degridding pre-pass for one w-plane p (two passes, forward transforms):
-//   D1 (rows along v): image row jx -> pixel values I_j c_p(j) placed at v index (py mod Nv),
-//      c_p(j) = corr_j exp(-2 pi i w_p (t_j - t_c)), then FFT over v -> B1[jx][.]
-//   D2 (columns along u): B1 column v placed at u index (px mod Nu), FFT over u -> grid[.][v]
-// corr_j = (-1)^(px+py) / (n_j Phi_u Phi_v Phi_w) holds the grid correction (reciprocal of the
-// gridding kernel's Fourier transform) and the sign that centres zero frequency at (Nu/2, Nv/2).
+// Layouts: sky and dirty images [jx][jy]; the oversampled grid of one w-plane G[v][u] (u
+// fastest, zero frequency at (Nu/2, Nv/2)); the half-transformed plane B1T[v][jx] on the way
+// in and B1[jx][v] on the way out. Each pass reads contiguous sequences; the transposed stores
+// produce the next pass's contiguous input.
 //
-// Gridding post-pass for one w-plane (two passes, inverse transforms, cropped early):
-//   G1 (columns along u): grid column -> inverse FFT -> keep the nx rows px in [-nx/2, nx/2)
-//      -> B1; the grid column is zeroed after loading (the grid stays zero between calls)
-//   G2 (rows along v): inverse FFT -> keep ny outputs -> Re(Z conj(c_p(j))) accumulated into
-//      the dirty image.
+// Degridding pre-pass for one w-plane p (forward transforms):
+//   D1 (image rows, along v): I_j c_p(j) placed at v index (py mod Nv), FFT -> B1T[.][jx]
+//      with c_p(j) = corr_j exp(-2 pi i w_p (t_j - t_c));
+//   D2 (B1T rows, along u): row v placed at u index (px mod Nu), FFT -> G[v][.].
+// corr_j = (-1)^(px+py) / (n_j Phi_u Phi_v Phi_w) holds the grid correction (reciprocal of the
+// gridding kernel's Fourier transform) and the sign that centres zero frequency.
+//
+// Gridding post-pass for one w-plane (inverse transforms, cropped as early as possible):
+//   G1 (grid rows, along u): inverse FFT, keep px in [-nx/2, nx/2) -> B1[.][v]; the grid row is
+//      zeroed once loaded (the grid stays zero between calls);
+//   G2 (B1 rows, along v): inverse FFT, keep ny outputs, Re(Z conj(c_p(j))) accumulated into the
+//      dirty image.
 #include "fft_engine.cuh"
 
 namespace fr {
@@ -25,13 +30,14 @@ __device__ __forceinline__ void plane_phase(int32_t tq, long long k64, float* c,
   sincospif(2.f * f, s, c);
 }
 
-struct D1Op {
+struct D1Op : OpBase {
+  static constexpr bool TRANSPOSED = true;
   const float* sky;
   const float* corr;
   const int32_t* tq;
   long long k64;
   int wterm;
-  float2* b1;
+  float2* b1t;  // [Nv][nx]
   int nx, ny, Nv;
   __host__ __device__ int nseq() const { return nx; }
   __host__ __device__ int nout() const { return Nv; }
@@ -51,20 +57,19 @@ struct D1Op {
     plane_phase(__ldg(&tq[pix]), k64, &c, &s);
     return make_float2(val * c, -val * s);
   }
-  __device__ double store(int jx, int o, SeqView v) const {
-    b1[(size_t)jx * Nv + o] = v[o];
+  __device__ double store(int jx, int v, SeqView s) const {
+    b1t[(size_t)v * nx + jx] = s[v];
     return 0.0;
   }
-  __device__ void finish(int, double) const {}
 };
 
-struct D2Op {
-  const float2* b1;
-  float2* grid;
+struct D2Op : OpBase {
+  const float2* b1t;
+  float2* grid;  // [Nv][Nu]
   int nx, Nu, Nv;
-  __host__ __device__ int ncol() const { return Nv; }
+  __host__ __device__ int nseq() const { return Nv; }
   __host__ __device__ int nout() const { return Nu; }
-  __device__ float2 load(int i, int v) const {
+  __device__ float2 load(int v, int i) const {
     const int hx = nx >> 1;
     int jx;
     if (i < hx)
@@ -73,38 +78,35 @@ struct D2Op {
       jx = i - Nu + hx;
     else
       return make_float2(0.f, 0.f);
-    return b1[(size_t)jx * Nv + v];
+    return b1t[(size_t)v * nx + jx];
   }
-  template <int B, int NT, int L>
-  __device__ void after_load(int) const {}
-  template <int B, int NT, int L, int LP>
-  __device__ void mid(float2*, int) const {}
-  __device__ void store(int o, int v, SeqView s) const { grid[(size_t)o * Nv + v] = s[o]; }
+  __device__ double store(int v, int u, SeqView s) const {
+    grid[(size_t)v * Nu + u] = s[u];
+    return 0.0;
+  }
 };
 
-struct G1Op {
-  float2* grid;
-  float2* b1;
+struct G1Op : OpBase {
+  static constexpr bool TRANSPOSED = true;
+  float2* grid;  // [Nv][Nu]
+  float2* b1;    // [nx][Nv]
   int nx, Nu, Nv;
-  __host__ __device__ int ncol() const { return Nv; }
+  __host__ __device__ int nseq() const { return Nv; }
   __host__ __device__ int nout() const { return nx; }
-  __device__ float2 load(int i, int v) const { return grid[(size_t)i * Nv + v]; }
-  template <int B, int NT, int L>
-  __device__ void after_load(int col0) const {
-    for (int idx = threadIdx.x; idx < B * L; idx += NT) {
-      const int i = idx / B, c = idx % B;
-      if (col0 + c < Nv) grid[(size_t)i * Nv + col0 + c] = make_float2(0.f, 0.f);
-    }
+  __device__ float2 load(int v, int i) const { return grid[(size_t)v * Nu + i]; }
+  __device__ void after_load(int seq0, int nb) const {
+    float4* p = reinterpret_cast<float4*>(grid + (size_t)seq0 * Nu);
+    const int n = nb * Nu / 2;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  template <int B, int NT, int L, int LP>
-  __device__ void mid(float2*, int) const {}
-  __device__ void store(int o, int v, SeqView s) const {
+  __device__ double store(int v, int o, SeqView s) const {
     const int i = (o - (nx >> 1) + Nu) & (Nu - 1);
     b1[(size_t)o * Nv + v] = s[i];
+    return 0.0;
   }
 };
 
-struct G2Op {
+struct G2Op : OpBase {
   const float2* b1;
   float* dirty;
   const float* corr;
@@ -131,30 +133,16 @@ struct G2Op {
     dirty[pix] = accumulate ? dirty[pix] + val : val;
     return 0.0;
   }
-  __device__ void finish(int, double) const {}
 };
 
-
 template <int LG>
-static int run_d1(const D1Op& op, const float2* tw, cudaStream_t s) {
-  return launch_rows<LG, -1>(op, tw, s);
-}
+static int run_d1(const D1Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, 1, tw, s); }
 template <int LG>
-static int run_d2(const D2Op& op, const float2* tw, cudaStream_t s) {
-  ColOp<LG, D2Op> c;
-  static_cast<D2Op&>(c) = op;
-  return launch_cols<LG, -1, -1, false>(c, 1, tw, s);
-}
+static int run_d2(const D2Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, 1, tw, s); }
 template <int LG>
-static int run_g1(const G1Op& op, const float2* tw, cudaStream_t s) {
-  ColOp<LG, G1Op> c;
-  static_cast<G1Op&>(c) = op;
-  return launch_cols<LG, 1, 1, false>(c, 1, tw, s);
-}
+static int run_g1(const G1Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, 1, tw, s); }
 template <int LG>
-static int run_g2(const G2Op& op, const float2* tw, cudaStream_t s) {
-  return launch_rows<LG, 1>(op, tw, s);
-}
+static int run_g2(const G2Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, 1, tw, s); }
 
 static int d1(int lg, const D1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1, op, tw, s); }
 static int d2(int lg, const D2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2, op, tw, s); }
@@ -164,13 +152,27 @@ static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG
 int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
                    const float2* twv, const float2* twu, cudaStream_t s) {
   const double img = (double)a.nx * a.ny, half = (double)a.nx * a.Nv, full = (double)a.Nu * a.Nv;
-  D1Op o1{sky, a.corr, a.tq, a.k64, a.wterm, b1, a.nx, a.ny, a.Nv};
+  D1Op o1;
+  o1.sky = sky;
+  o1.corr = a.corr;
+  o1.tq = a.tq;
+  o1.k64 = a.k64;
+  o1.wterm = a.wterm;
+  o1.b1t = b1;
+  o1.nx = a.nx;
+  o1.ny = a.ny;
+  o1.Nv = a.Nv;
   {
     // sky + corr (+ tq) in, half-transformed plane out
     ProfScope ps(PC_FFT_ROWS, s, img * (8.0 + (a.wterm ? 4.0 : 0.0)) + half * 8.0);
     FR_TRY(d1(ilog2(a.Nv), o1, twv, s));
   }
-  D2Op o2{b1, grid, a.nx, a.Nu, a.Nv};
+  D2Op o2;
+  o2.b1t = b1;
+  o2.grid = grid;
+  o2.nx = a.nx;
+  o2.Nu = a.Nu;
+  o2.Nv = a.Nv;
   ProfScope ps(PC_FFT_COLS, s, half * 8.0 + full * 8.0);
   return d2(ilog2(a.Nu), o2, twu, s);
 }
@@ -178,13 +180,28 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
 int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
                   const float2* twu, const float2* twv, cudaStream_t s) {
   const double img = (double)a.nx * a.ny, half = (double)a.nx * a.Nv, full = (double)a.Nu * a.Nv;
-  G1Op o1{grid, b1, a.nx, a.Nu, a.Nv};
+  G1Op o1;
+  o1.grid = grid;
+  o1.b1 = b1;
+  o1.nx = a.nx;
+  o1.Nu = a.Nu;
+  o1.Nv = a.Nv;
   {
     // grid in, grid zeroed, cropped plane out
     ProfScope ps(PC_FFT_COLS, s, full * 16.0 + half * 8.0);
     FR_TRY(g1(ilog2(a.Nu), o1, twu, s));
   }
-  G2Op o2{b1, dirty, a.corr, a.tq, a.k64, a.wterm, accumulate, a.nx, a.ny, a.Nv};
+  G2Op o2;
+  o2.b1 = b1;
+  o2.dirty = dirty;
+  o2.corr = a.corr;
+  o2.tq = a.tq;
+  o2.k64 = a.k64;
+  o2.wterm = a.wterm;
+  o2.accumulate = accumulate;
+  o2.nx = a.nx;
+  o2.ny = a.ny;
+  o2.Nv = a.Nv;
   ProfScope ps(PC_FFT_ROWS, s,
                half * 8.0 + img * (4.0 + (a.wterm ? 4.0 : 0.0) + (accumulate ? 8.0 : 4.0)));
   return g2(ilog2(a.Nv), o2, twv, s);

@@ -202,10 +202,12 @@ struct PsfArgs {
   const float* dirty;   // likelihood mode (grad = conv - dirty), else null
   double* value;        // likelihood mode: [nimg / nsky] accumulators, else null
 };
-int psf_apply_passes(const PsfArgs& a, float2* h, const float2* tw_rows, const float2* tw_cols,
-                     cudaStream_t s);
-// transfer function from PSF images [nsky][2nx][2ny] -> transfer [nsky][2nx][ny+1]
-int build_transfer(int nx, int ny, int nsky, const float* psf, float2* h, int hp, float* transfer,
+// h: [nimg][nx][hp] half spectra, ht: [nimg][ny+1][nx] transposed half spectra
+int psf_apply_passes(const PsfArgs& a, float2* h, float2* ht, const float2* tw_rows,
+                     const float2* tw_cols, cudaStream_t s);
+// transfer function from PSF images [nsky][2nx][2ny] -> transfer TT [nsky][ny+1][2nx]
+// (ht: [nsky][ny+1][2nx] scratch)
+int build_transfer(int nx, int ny, int nsky, const float* psf, float2* ht, float* transfer,
                    const float2* tw_rows, const float2* tw_cols, cudaStream_t s);
 int fft_max_log2();
 int fft_min_log2();

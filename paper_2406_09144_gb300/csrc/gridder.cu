@@ -779,8 +779,9 @@ int make_tmap(CUtensorMap* m, float2* grid, int Nu, int Nv, int W) {
     }
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  cuuint64_t dims[2] = {(cuuint64_t)2 * Nv, (cuuint64_t)Nu};
-  cuuint64_t strides[1] = {(cuuint64_t)Nv * sizeof(float2)};
+  // grid G[v][u]: x = u (2 floats per cell), y = v
+  cuuint64_t dims[2] = {(cuuint64_t)2 * Nu, (cuuint64_t)Nv};
+  cuuint64_t strides[1] = {(cuuint64_t)Nu * sizeof(float2)};
   cuuint32_t box[2] = {(cuuint32_t)(2 * box_v(W)), (cuuint32_t)box_u(W)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)grid, dims, strides, box, estr,
@@ -856,7 +857,7 @@ __global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUt
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
         "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tile)),
-        "l"((uint64_t)&tmap), "r"(2 * TILE * tv), "r"(TILE * tu), "r"(bar)
+        "l"((uint64_t)&tmap), "r"(2 * TILE * tu), "r"(TILE * tv), "r"(bar)
         : "memory");
   }
   __syncthreads();
@@ -877,17 +878,17 @@ __global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUt
     kernel_weights<W>(kern, m.dv[i], kv);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-      const float2* row = tile + (ru + a) * BV + rv;
+    for (int b = 0; b < W; ++b) {  // tile rows are v, columns u
+      const float2* row = tile + (rv + b) * BV + ru;
       float2 ra = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int b = 0; b < W; ++b) {
-        const float2 g = row[b];
-        ra.x = fmaf(kv[b], g.x, ra.x);
-        ra.y = fmaf(kv[b], g.y, ra.y);
+      for (int a = 0; a < W; ++a) {
+        const float2 g = row[a];
+        ra.x = fmaf(ku[a], g.x, ra.x);
+        ra.y = fmaf(ku[a], g.y, ra.y);
       }
-      acc.x = fmaf(ku[a], ra.x, acc.x);
-      acc.y = fmaf(ku[a], ra.y, acc.y);
+      acc.x = fmaf(kv[b], ra.x, acc.x);
+      acc.y = fmaf(kv[b], ra.y, acc.y);
     }
     int rel = 0;
     if (wterm) {
@@ -990,10 +991,11 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
       if (lane < 2 * W) kval = es_eval(kern, lane < W ? duj - (float)lane : dvj - (float)(lane - W));
 #pragma unroll
       for (int k = 0; k < NIT; ++k) {
-        const float ku = __shfl_sync(0xffffffffu, kval, ca[k] & 31);
-        const float kv = __shfl_sync(0xffffffffu, kval, W + cb[k]);
+        // cell (v offset ca, u offset cb); the sub-grid rows are v, columns u
+        const float ku = __shfl_sync(0xffffffffu, kval, cb[k]);
+        const float kv = __shfl_sync(0xffffffffu, kval, (W + ca[k]) & 31);
         if (lane + 32 * k < CELLS) {
-          float2* c = mysub + (ru + ca[k]) * BV + rv + cb[k];
+          float2* c = mysub + (rv + ca[k]) * BV + ru + cb[k];
           const float wgt = ku * kv;
           float2 g = *c;
           g.x = fmaf(wgt, vr, g.x);
@@ -1014,8 +1016,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
       acc.y += o.y;
     }
     if (acc.x == 0.f && acc.y == 0.f) continue;
-    const int gu = tu * TILE + r, gv = tv * TILE + c;
-    if (gu < Nu && gv < Nv) atomicAdd(&grid[(size_t)gu * Nv + gv], acc);
+    const int gv = tv * TILE + r, gu = tu * TILE + c;
+    if (gu < Nu && gv < Nv) atomicAdd(&grid[(size_t)gv * Nu + gu], acc);
   }
 }
 
