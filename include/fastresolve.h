@@ -123,6 +123,26 @@ int fr_likelihood_grad(fr_plan_t plan, const float *sky, const float *dirty, int
 int fr_major_cycle(fr_plan_t plan, const float *sky, const float *dirty, float *resid,
                    double *resid_norm2, const fr_cf32 *vis, double *vis_chi2, void *stream);
 
+/* Allocation-free PSF convolution. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory, such as code embedded in an application that owns
+ * the whole device-memory budget through its own pool, or code running where a cudaMalloc would
+ * implicitly synchronise the device or is not allowed. It computes the same linear convolution
+ * as fr_psf_apply, out_b(p) = sum_q psf(p - q) sky_b(q) cropped to the image, but takes the PSF
+ * image itself instead of a plan and allocates nothing: every intermediate lives in one
+ * file-scope device array of 32 MiB compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   psf   device float32 [2nx][2ny], offset (a, b) stored at (a + nx, b + ny) as fr_dirty_psf
+ *         writes it (row 0 and column 0 are not used)
+ *   sky   device float32 [batch][nx][ny];  out: device float32 [batch][nx][ny]
+ *   nx, ny powers of two >= 16 with nx * ny <= 2^20 (FR_EINVAL with a message otherwise)
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture. All calls share the one array and it keeps
+ * the last call's contents; each call writes every intermediate before reading it. Calls that
+ * overlap on the GPU (different streams, or different host threads) race on the array and must
+ * be serialised by the caller. */
+int fr_psf_convolve_noalloc(const float *psf, const float *sky, int32_t nx, int32_t ny,
+                            int32_t batch, float *out, void *stream);
+
 /* Plan parameters chosen at creation (for reports and tests). */
 typedef struct {
   int32_t nx, ny, nsky, nchan;

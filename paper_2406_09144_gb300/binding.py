@@ -20,7 +20,7 @@ ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EUNSUPPORTED
 EXPORTS = ["fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
            "fr_likelihood_grad", "fr_major_cycle", "fr_plan_get_info", "fr_plan_footprint",
            "fr_plan_check", "fr_plan_destroy", "fr_strerror", "fr_last_error", "fr_launch_count",
-           "fr_selftest_fft_host"]
+           "fr_selftest_fft_host", "fr_psf_convolve_noalloc"]
 
 
 class FastResolveError(RuntimeError):
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH):
     lib.fr_profile_read.restype = ctypes.c_int
     lib.fr_profile_category.argtypes = [I32]
     lib.fr_profile_category.restype = ctypes.c_char_p
+    lib.fr_psf_convolve_noalloc.argtypes = [P, P, I32, I32, I32, P, P]
+    lib.fr_psf_convolve_noalloc.restype = ctypes.c_int
     for name in ("fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
                  "fr_likelihood_grad", "fr_major_cycle", "fr_plan_get_info", "fr_plan_footprint",
                  "fr_plan_check", "fr_selftest_fft_host"):
