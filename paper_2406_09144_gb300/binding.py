@@ -169,6 +169,7 @@ class Plan:
             weights = np.ascontiguousarray(np.broadcast_to(weights, (self.nrow, self.nchan)),
                                            dtype=np.float32)
             wptr = weights.ctypes.data
+        self._weights_host = weights  # kept for the adjoint of the weighted gridder
         flags = ((FR_WTERM if wterm else 0) | (FR_NTERM if nterm else 0) | (FR_MFS if mfs else 0)
                  | (FR_DROP_OOB if drop_oob else 0) | (FR_NO_PSF if no_psf else 0))
         self.nx, self.ny = int(nx), int(ny)

@@ -933,6 +933,10 @@ constexpr size_t grid_smem_bytes() {
   return (size_t)GRID_WARPS * (TILE + W - 1) * ((TILE + W) & ~1) * sizeof(float2);
 }
 
+// Within a work item the visibilities are first ordered by their footprint origin with a
+// shared-memory counting sort, so each warp walks runs of visibilities that share an origin;
+// a run is accumulated in registers and added to the warp's sub-grid once, when the origin
+// changes.
 template <int W>
 __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __restrict__ items,
                                                                MetaPtrs m, EsKernel kern, int p,
@@ -945,28 +949,84 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   constexpr int SUB = BU * BV;
   constexpr int CELLS = W * W;
   constexpr int NIT = (CELLS + 31) / 32;
+  constexpr int NT = GRID_WARPS * 32;
+  constexpr int NKEY = TILE * TILE;
   extern __shared__ float2 sub[];  // [GRID_WARPS][SUB]
+  __shared__ int hist[NKEY];
+  __shared__ short order[GRID_CHUNK];
+  __shared__ int wsum[GRID_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int4 it = items[blockIdx.x];
   const int tu = it.z >> 16, tv = it.z & 0xffff;
-  const int end = it.x + it.y;
-  const int nused = min(GRID_WARPS, (it.y + 31) / 32);
-  for (int i = threadIdx.x; i < nused * SUB; i += blockDim.x) sub[i] = make_float2(0.f, 0.f);
+  const int n = it.y;
+  // each warp takes a contiguous segment of the sorted order, a multiple of 32 long
+  const int seg = (((n + GRID_WARPS - 1) / GRID_WARPS) + 31) & ~31;
+  const int nused = n > 0 ? (n + seg - 1) / seg : 0;
+  for (int i = threadIdx.x; i < nused * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < NKEY; i += NT) hist[i] = 0;
   __syncthreads();
+  // counting sort of the item's visibilities by footprint origin (rv * TILE + ru)
+  int mykey[GRID_CHUNK / NT];
+#pragma unroll
+  for (int r = 0; r < GRID_CHUNK / NT; ++r) {
+    const int t = threadIdx.x + r * NT;
+    mykey[r] = -1;
+    if (t < n) {
+      const uint32_t c = m.cell[it.x + t];
+      mykey[r] = ((int)((c >> 4) & 0x3fff) - tv * TILE) * TILE + (int)(c >> 18) - tu * TILE;
+      atomicAdd(&hist[mykey[r]], 1);
+    }
+  }
+  __syncthreads();
+  {
+    constexpr int PER = NKEY / NT;
+    int v[PER], s = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      v[r] = hist[threadIdx.x * PER + r];
+      s += v[r];
+    }
+    int x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int yv = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += yv;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int before = x - s;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      hist[threadIdx.x * PER + r] = before;
+      before += v[r];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < GRID_CHUNK / NT; ++r)
+    if (mykey[r] >= 0) order[atomicAdd(&hist[mykey[r]], 1)] = (short)(threadIdx.x + r * NT);
+  __syncthreads();
+
   float2* mysub = sub + warp * SUB;
-  int ca[NIT], cb[NIT];
+  int off[NIT], cu[NIT], cv[NIT];
 #pragma unroll
   for (int k = 0; k < NIT; ++k) {
     const int idx = lane + 32 * k;
-    ca[k] = idx / W;
-    cb[k] = idx % W;
+    cv[k] = idx / W;  // v offset (sub-grid row)
+    cu[k] = idx % W;  // u offset (sub-grid column)
+    off[k] = cv[k] * BV + cu[k];
   }
-  for (int base = it.x + warp * 32; base < end; base += GRID_WARPS * 32) {
-    const int i = base + lane;
+  const int s0 = min(n, warp * seg), s1 = min(n, s0 + seg);
+  int cur = -1;  // current origin offset rv * BV + ru, uniform across the warp
+  float2 acc[NIT];
+#pragma unroll
+  for (int k = 0; k < NIT; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int base = s0; base < s1; base += 32) {
     uint32_t cell = 0;
     float du = 0.f, dv = 0.f;
     float2 val = make_float2(0.f, 0.f);
-    if (i < end) {
+    if (base + lane < s1) {
+      const int i = it.x + order[base + lane];
       cell = m.cell[i];
       du = m.du[i];
       dv = m.dv[i];
@@ -978,32 +1038,51 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
         val.y *= kw;
       }
     }
-    const int nb = min(32, end - base);
+    const int nb = min(32, s1 - base);
     for (int j = 0; j < nb; ++j) {
       const uint32_t cj = __shfl_sync(0xffffffffu, cell, j);
       const float duj = __shfl_sync(0xffffffffu, du, j);
       const float dvj = __shfl_sync(0xffffffffu, dv, j);
       const float vr = __shfl_sync(0xffffffffu, val.x, j);
       const float vi = __shfl_sync(0xffffffffu, val.y, j);
-      const int ru = (int)(cj >> 18) - tu * TILE;
-      const int rv = (int)((cj >> 4) & 0x3fff) - tv * TILE;
+      const int org = ((int)((cj >> 4) & 0x3fff) - tv * TILE) * BV + (int)(cj >> 18) - tu * TILE;
+      if (org != cur) {
+        if (cur >= 0) {
+#pragma unroll
+          for (int k = 0; k < NIT; ++k)
+            if (lane + 32 * k < CELLS) {
+              float2* c = mysub + cur + off[k];
+              float2 g = *c;
+              g.x += acc[k].x;
+              g.y += acc[k].y;
+              *c = g;
+              acc[k] = make_float2(0.f, 0.f);
+            }
+        }
+        cur = org;
+      }
       float kval = 0.f;
       if (lane < 2 * W) kval = es_eval(kern, lane < W ? duj - (float)lane : dvj - (float)(lane - W));
 #pragma unroll
       for (int k = 0; k < NIT; ++k) {
-        // cell (v offset ca, u offset cb); the sub-grid rows are v, columns u
-        const float ku = __shfl_sync(0xffffffffu, kval, cb[k]);
-        const float kv = __shfl_sync(0xffffffffu, kval, (W + ca[k]) & 31);
-        if (lane + 32 * k < CELLS) {
-          float2* c = mysub + (rv + ca[k]) * BV + ru + cb[k];
-          const float wgt = ku * kv;
-          float2 g = *c;
-          g.x = fmaf(wgt, vr, g.x);
-          g.y = fmaf(wgt, vi, g.y);
-          *c = g;
-        }
+        const float ku = __shfl_sync(0xffffffffu, kval, cu[k]);
+        const float kv = __shfl_sync(0xffffffffu, kval, (W + cv[k]) & 31);
+        const float wgt = ku * kv;
+        acc[k].x = fmaf(wgt, vr, acc[k].x);
+        acc[k].y = fmaf(wgt, vi, acc[k].y);
       }
     }
+  }
+  if (cur >= 0) {
+#pragma unroll
+    for (int k = 0; k < NIT; ++k)
+      if (lane + 32 * k < CELLS) {
+        float2* c = mysub + cur + off[k];
+        float2 g = *c;
+        g.x += acc[k].x;
+        g.y += acc[k].y;
+        *c = g;
+      }
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < SUB; idx += blockDim.x) {

@@ -1,0 +1,381 @@
+"""Continuous-batching imaging server on one GPU.
+
+Requests are imaging jobs of different image sizes, visibility counts and channel counts, of two
+kinds, matching the two operator calls of the fast-resolve scheme (Algorithm 1):
+  * "psf":   minor-cycle work, the PSF convolution of a batch of skies (Sec. 3.3.2);
+  * "major": major-cycle work, R^dagger N^-1 R of a sky (Eq. clean), degridding then gridding.
+Each job makes `ncalls` operator applications.
+
+Scheduler (host logic, `Scheduler`):
+  * arrivals join a FIFO wait queue;
+  * a job is admitted as soon as an execution slot is free and its estimated HBM footprint fits
+    the remaining budget (admission by footprint); jobs that arrive while others run are
+    admitted as slots and memory free up (continuous batching, not a queue in front of a
+    single worker);
+  * admitted jobs run concurrently, one CUDA stream per slot, so their work overlaps on the
+    device; a finished job releases its slot and memory immediately.
+
+GPU executor (`GpuExecutor`): at admission it builds the job's plan (sorted visibilities, PSF
+transfer function; resident until the job retires), uploads the inputs, makes one eager call
+(which also sizes the per-stream workspace) and captures the job's operator call into a CUDA
+graph; every later call is one graph launch. `run_sequential` is the baseline: one job at a
+time, plain per-call launches, one stream.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Callable, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    kind: str                      # "psf" or "major"
+    uvw: np.ndarray                # [nrow, 3] metres
+    freqs: np.ndarray              # [nchan] Hz
+    weights: Optional[np.ndarray]  # [nrow, nchan] or None
+    nx: int
+    ny: int
+    pixsize: float
+    sky: np.ndarray                # psf: [batch, nsky, nx, ny]; major: [nsky, nx, ny]
+    mfs: bool = False
+    ncalls: int = 1
+    arrival: float = 0.0           # seconds after the start of the run
+    # filled in by the scheduler
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    result: Optional[np.ndarray] = None
+
+    @property
+    def nvis(self) -> int:
+        return self.uvw.shape[0] * len(self.freqs)
+
+    @property
+    def nsky(self) -> int:
+        return 1 if self.mfs else len(self.freqs)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+
+def estimate_bytes(req: Request) -> int:
+    """HBM footprint of a job while it is admitted: plan-resident data, the per-stream workspace,
+    the inputs and outputs, and the PSF-build transients during plan creation."""
+    n = req.nx * req.ny
+    m = req.nvis
+    plan = m * 28 + n * 8 + req.nsky * (4 * n * 4 + 2 * n * 4)     # sorted vis, tables, PSF, T
+    work = n * 4 * 8 + n * 2 * 8 + m * 8                           # grid, half plane, vis buffer
+    build = 16 * n * 8 + 8 * n * 8 + m * 32                        # PSF-build grid and sort temps
+    io = req.sky.size * 4 * 2 + (m * 8 * 2 if req.kind == "major" else 0)
+    if req.kind == "psf":
+        work += req.sky.shape[0] * req.nsky * n * 8 * 2            # half spectra
+    return int(plan + work + max(build, 0) + io)
+
+
+class Scheduler:
+    """FIFO admission by HBM footprint into a fixed number of concurrent slots.
+
+    The executor provides admit(req) -> handle, issue(handle) -> None (launch the next call),
+    ready(handle) -> bool (previous work finished), finish(handle) -> None (collect the result
+    and release device memory). `clock` is a monotonic time source in seconds.
+    """
+
+    def __init__(self, executor, budget_bytes: int, max_active: int = 8,
+                 clock: Callable[[], float] = time.perf_counter, realtime: bool = True):
+        self.ex = executor
+        self.budget = int(budget_bytes)
+        self.max_active = int(max_active)
+        self.clock = clock
+        self.realtime = realtime
+        self.peak_bytes = 0
+        self.peak_active = 0
+        self.log = []
+
+    def run(self, requests):
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        for r in reqs:
+            if estimate_bytes(r) > self.budget:
+                raise ValueError(f"request {r.rid} needs {estimate_bytes(r)} bytes, budget is {self.budget}")
+        pending = collections.deque(reqs)
+        waiting = collections.deque()
+        active = {}
+        used = 0
+        t0 = self.clock()
+        while pending or waiting or active:
+            now = self.clock() - t0
+            if not self.realtime and not waiting and not active and pending:
+                now = max(now, pending[0].arrival)
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.popleft())
+            progressed = False
+            # admission: FIFO, while a slot is free and the footprint fits
+            while waiting and len(active) < self.max_active and \
+                    used + estimate_bytes(waiting[0]) <= self.budget:
+                r = waiting.popleft()
+                r.t_admit = self.clock() - t0
+                h = self.ex.admit(r)
+                est = estimate_bytes(r)
+                active[r.rid] = [r, h, 0, est]
+                used += est
+                self.peak_bytes = max(self.peak_bytes, used)
+                self.peak_active = max(self.peak_active, len(active))
+                self.log.append(("admit", r.rid, r.t_admit, used))
+                progressed = True
+            # issue the next call of every job whose previous call finished
+            for rid in list(active):
+                r, h, done, est = active[rid]
+                if not self.ex.ready(h):
+                    continue
+                if done < r.ncalls:
+                    self.ex.issue(h)
+                    active[rid][2] = done + 1
+                    progressed = True
+                else:
+                    self.ex.finish(h)
+                    r.t_done = self.clock() - t0
+                    used -= est
+                    del active[rid]
+                    self.log.append(("done", rid, r.t_done, used))
+                    progressed = True
+            if not progressed:
+                if self.realtime and not active and not waiting and pending:
+                    time.sleep(max(0.0, min(0.002, pending[0].arrival - (self.clock() - t0))))
+                else:
+                    time.sleep(0.0002 if self.realtime else 0.0)
+        return reqs
+
+
+def summarize(reqs, wall_s: float) -> dict:
+    lat = np.array([r.latency for r in reqs]) * 1e3
+    nvis = sum(r.nvis * r.ncalls for r in reqs if r.kind == "major")
+    npix = sum(r.sky.size * r.ncalls for r in reqs if r.kind == "psf")
+    return {"requests": len(reqs), "wall_s": wall_s, "req_per_s": len(reqs) / wall_s,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "major_mvis_s": nvis / wall_s / 1e6,
+            "psf_mpix_s": npix / wall_s / 1e6}
+
+
+# ------------------------------------------------------------------------------ GPU executor
+class GpuExecutor:
+    """Runs admitted jobs on their own CUDA streams; one captured CUDA graph per job call."""
+
+    def __init__(self, device="cuda", graphs: bool = True, eps: float = 1e-5):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.graphs = graphs
+        self.eps = eps
+        self.streams = []
+
+    def _stream(self):
+        return self.streams.pop() if self.streams else self.torch.cuda.Stream(device=self.device)
+
+    def admit(self, r: Request):
+        torch = self.torch
+        from .binding import Plan
+        s = self._stream()
+        h = {"req": r, "stream": s, "event": None, "graph": None}
+        with torch.cuda.stream(s):
+            plan = Plan(r.uvw, r.freqs, r.nx, r.ny, r.pixsize, weights=r.weights, eps=self.eps,
+                        mfs=r.mfs, stream=s)
+            sky = torch.as_tensor(np.ascontiguousarray(r.sky), dtype=torch.float32).to(self.device,
+                                                                                      non_blocking=True)
+            if r.kind == "psf":
+                out = torch.empty_like(sky)
+
+                def call():
+                    plan.psf_apply(sky, out=out, stream=s)
+            else:
+                vis = torch.empty(plan.vis_shape, dtype=torch.complex64, device=self.device)
+                out = torch.empty(plan.sky_shape, dtype=torch.float32, device=self.device)
+
+                def call():
+                    plan.degrid(sky, out=vis, stream=s)
+                    plan.grid(vis, out=out, stream=s)
+            call()  # eager: sizes the per-stream workspace before any capture
+            if self.graphs:
+                g = torch.cuda.CUDAGraph()
+                g.capture_begin()
+                call()
+                g.capture_end()
+                h["graph"] = g
+        h.update(plan=plan, sky=sky, out=out, call=call)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        h["event"] = ev
+        return h
+
+    def ready(self, h) -> bool:
+        return h["event"] is None or h["event"].query()
+
+    def issue(self, h):
+        torch = self.torch
+        s = h["stream"]
+        with torch.cuda.stream(s):
+            if h["graph"] is not None:
+                h["graph"].replay()
+            else:
+                h["call"]()
+            ev = torch.cuda.Event()
+            ev.record(s)
+            h["event"] = ev
+
+    def finish(self, h):
+        h["event"].synchronize()
+        h["req"].result = h["out"].cpu().numpy()
+        h["plan"].close()
+        for k in ("graph", "plan", "sky", "out", "call"):
+            h[k] = None
+        self.streams.append(h["stream"])
+
+
+def run_sequential(requests, device="cuda", eps=1e-5):
+    """Baseline: each job alone, in arrival order, plain launches on one stream."""
+    import torch
+    from .binding import Plan
+    reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+    t0 = time.perf_counter()
+    for r in reqs:
+        now = time.perf_counter() - t0
+        if now < r.arrival:
+            time.sleep(r.arrival - now)
+        r.t_admit = time.perf_counter() - t0
+        plan = Plan(r.uvw, r.freqs, r.nx, r.ny, r.pixsize, weights=r.weights, eps=eps, mfs=r.mfs)
+        sky = torch.as_tensor(np.ascontiguousarray(r.sky), dtype=torch.float32).to(device)
+        for _ in range(r.ncalls):
+            if r.kind == "psf":
+                out = plan.psf_apply(sky)
+            else:
+                out = plan.grid(plan.degrid(sky))
+        r.result = out.cpu().numpy()
+        plan.close()
+        r.t_done = time.perf_counter() - t0
+    return reqs
+
+
+# ------------------------------------------------------------------------------ workload
+def make_requests(n: int, seed: int = 100, sizes=(256, 512, 1024, 2048, 4096),
+                  nvis_range=(1e4, 2e7), nchan_max: int = 8, ncalls: int = 4,
+                  psf_batch: int = 2) -> list:
+    """Serving workload: image sizes uniform over `sizes`, visibility counts log-uniform over
+    `nvis_range`, 1..nchan_max channels, half PSF-convolution and half major-cycle jobs, arrays
+    and tracks as the VLA-like and MeerKAT-like observations (seeded per request: 100 + i)."""
+    from . import synth
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed + i)
+        nx = int(rng.choice(sizes))
+        nvis = float(np.exp(rng.uniform(math.log(nvis_range[0]), math.log(nvis_range[1]))))
+        nchan = int(rng.integers(1, nchan_max + 1))
+        meerkat = bool(rng.integers(0, 2))
+        enu = synth.meerkat_like_enu(seed + i) if meerkat else synth.vla_like_enu(seed + i)
+        nbl = len(enu) * (len(enu) - 1) // 2
+        ntime = max(1, int(round(nvis / nchan / nbl)))
+        hours = 8.0
+        uvw = synth.earth_rotation_uvw(enu, -30.7 if meerkat else 34.08,
+                                       -60.5 if meerkat else 40.7, hours, hours * 3600.0 / ntime)
+        f0 = 0.9e9 if meerkat else 1.4e9
+        freqs = f0 * (1.0 + 0.1 * np.arange(nchan))
+        umax = float(np.max(np.abs(uvw[:, :2]))) * freqs.max() / synth.C_LIGHT
+        pix = 1.0 / (2.6 * umax)
+        kind = "psf" if rng.integers(0, 2) == 0 else "major"
+        mfs = bool(rng.integers(0, 2))
+        nsky = 1 if mfs else nchan
+        if kind == "psf":
+            sky = synth.random_skies(psf_batch * nsky, nx, nx, seed=seed + i).reshape(psf_batch, nsky, nx, nx)
+        else:
+            sky = synth.random_skies(nsky, nx, nx, seed=seed + i)
+        wt = rng.uniform(0.5, 2.0, (uvw.shape[0], nchan)).astype(np.float32)
+        out.append(Request(rid=i, kind=kind, uvw=uvw, freqs=freqs, weights=wt, nx=nx, ny=nx,
+                           pixsize=pix, sky=sky.astype(np.float32), mfs=mfs, ncalls=ncalls))
+    return out
+
+
+def poisson_arrivals(reqs, rate_per_s: float, seed: int = 7):
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    for r in reqs:
+        t += rng.exponential(1.0 / rate_per_s)
+        r.arrival = t
+    return reqs
+
+
+# ------------------------------------------------------------------------------ benchmark
+def _copy_requests(reqs):
+    return [dataclasses.replace(r, result=None, t_admit=math.nan, t_done=math.nan) for r in reqs]
+
+
+def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float = 0.8,
+          seed: int = 100, **kw) -> dict:
+    """Serving benchmark: (1) plain per-request launches, one job at a time, all jobs present
+    at t = 0 -> capacity; (2) the continuous-batching server on the same jobs at t = 0 ->
+    throughput; (3) the server under Poisson arrivals at `load` x the sequential capacity ->
+    p50 / p99 latency. Returns one dict."""
+    import torch
+    from .binding import load as load_lib
+    load_lib()
+    base = make_requests(n, seed=seed, **kw)
+    budget = int(budget_gb * 2 ** 30)
+    # warm-up: one small job of each kind through both paths (module load, kernel attributes)
+    warm = make_requests(2, seed=seed + 10 ** 6, sizes=(64,), nvis_range=(1e3, 2e3), nchan_max=1)
+    run_sequential(_copy_requests(warm))
+    Scheduler(GpuExecutor(), budget, max_active).run(_copy_requests(warm))
+    torch.cuda.synchronize()
+
+    seq = _copy_requests(base)
+    t0 = time.perf_counter()
+    run_sequential(seq)
+    torch.cuda.synchronize()
+    seq_wall = time.perf_counter() - t0
+    srv = _copy_requests(base)
+    sch = Scheduler(GpuExecutor(graphs=True), budget, max_active)
+    t0 = time.perf_counter()
+    sch.run(srv)
+    torch.cuda.synchronize()
+    srv_wall = time.perf_counter() - t0
+    worst = 0.0
+    for a, b in zip(seq, srv):
+        d = float(np.linalg.norm(a.result - b.result) / max(np.linalg.norm(a.result), 1e-30))
+        worst = max(worst, d)
+    rate = load * n / seq_wall
+    arr = poisson_arrivals(_copy_requests(base), rate, seed=seed)
+    sch2 = Scheduler(GpuExecutor(graphs=True), budget, max_active)
+    t0 = time.perf_counter()
+    sch2.run(arr)
+    torch.cuda.synchronize()
+    arr_wall = time.perf_counter() - t0
+    s_seq = summarize(seq, seq_wall)
+    s_srv = summarize(srv, srv_wall)
+    s_arr = summarize(arr, arr_wall)
+    return {
+        "workload": f"{n} jobs, images {kw.get('sizes', (256, 512, 1024, 2048, 4096))}, "
+                    f"visibilities log-uniform {kw.get('nvis_range', (1e4, 2e7))}, 1-"
+                    f"{kw.get('nchan_max', 8)} channels, half PSF-convolution / half major-cycle, "
+                    f"{kw.get('ncalls', 4)} calls per job",
+        "sequential": s_seq, "server_closed": s_srv, "server_poisson": s_arr,
+        "arrival_rate_per_s": rate, "max_active": max_active, "budget_bytes": budget,
+        "peak_admitted_bytes": sch.peak_bytes, "peak_active": sch.peak_active,
+        "throughput_gain": s_srv["req_per_s"] / s_seq["req_per_s"],
+        "max_rel_diff_alone_vs_mix": worst,
+    }
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=96.0)
+    ap.add_argument("--max-size", type=int, default=4096)
+    ap.add_argument("--max-nvis", type=float, default=2e7)
+    a = ap.parse_args()
+    sizes = tuple(s for s in (256, 512, 1024, 2048, 4096) if s <= a.max_size)
+    print(json.dumps(bench(a.n, a.max_active, a.budget_gb, sizes=sizes,
+                           nvis_range=(1e4, a.max_nvis))))
