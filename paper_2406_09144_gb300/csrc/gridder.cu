@@ -124,6 +124,8 @@ struct PrepArgs {
   const int* planes;     // [ngroups]
   const int* keybase;    // [ngroups]
   int ntu, ntv;
+  int ntb;               // row blocks per (tile, plane) bucket
+  int64_t rows_per_tb;
   int drop;
   // outputs in user order
   int* key;              // -1 = dropped
@@ -181,7 +183,8 @@ __global__ void vis_prepare(PrepArgs a) {
     const int ju = (int)iu0, jv = (int)iv0;
     const int tu = ju / TILE, tv = jv / TILE;
     const int P = a.wterm ? a.planes[g] : 1;
-    a.key[k] = a.keybase[g] + (tu * a.ntv + tv) * P + pf;
+    const int tb = (int)min((int64_t)a.ntb - 1, row / a.rows_per_tb);
+    a.key[k] = a.keybase[g] + ((tu * a.ntv + tv) * P + pf) * a.ntb + tb;
     a.cell[k] = ((uint32_t)ju << 18) | ((uint32_t)jv << 4) | (uint32_t)(pf & 15);
     a.du[k] = (float)(gu - iu0);
     a.dv[k] = (float)(gv - iv0);
@@ -253,7 +256,7 @@ struct ItemArgs {
   const int* keybase;    // [ngroups]
   const int* planes;     // [ngroups] (1 without w)
   const int64_t* ebase;  // [ngroups + 1] (group, plane, tile) enumeration base
-  int ngroups, ntiles, ntv, W, wterm;
+  int ngroups, ntiles, ntv, W, wterm, ntb;
   int* chunks;           // [E]
   const int* item_off;   // [E + 1] (emit pass)
   int4* items;
@@ -281,9 +284,9 @@ __device__ __forceinline__ void item_range(const ItemArgs& a, int64_t e, int* be
     *count = 0;
     return;
   }
-  const int64_t kb = (int64_t)a.keybase[g] + (int64_t)t * P;
-  *begin = a.off[kb + lo];
-  *count = a.off[kb + hi + 1] - *begin;
+  const int64_t kb = (int64_t)a.keybase[g] + (int64_t)t * P * a.ntb;
+  *begin = a.off[kb + (int64_t)lo * a.ntb];
+  *count = a.off[kb + (int64_t)(hi + 1) * a.ntb] - *begin;
 }
 
 __global__ void count_items(ItemArgs a, int64_t E) {
@@ -394,7 +397,14 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   const int ntiles = lay->ntu * lay->ntv;
   const bool wterm = geo.wterm;
 
-  // keys: (group, tile, first plane)
+  // keys: (group, tile, first plane, row block). Row blocks keep each bucket to a narrow range
+  // of rows, i.e. of times for time-ordered data, so a work item holds consecutive samples of
+  // the baselines crossing its tile, which stay in one grid cell for many samples.
+  int64_t kbase = 0;
+  for (int g = 0; g < ngroups; ++g) kbase += (int64_t)ntiles * (wterm ? planes[g] : 1);
+  const int ntb = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(nrow, 4096),
+                                                              (int64_t(1) << 26) / std::max<int64_t>(kbase, 1)));
+  const int64_t rows_per_tb = (nrow + ntb - 1) / ntb;
   std::vector<int> keybase(ngroups);
   int64_t K = 0;
   std::vector<int64_t> ebase(ngroups + 1);
@@ -402,7 +412,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   for (int g = 0; g < ngroups; ++g) {
     const int P = wterm ? planes[g] : 1;
     keybase[g] = (int)K;
-    K += (int64_t)ntiles * P;
+    K += (int64_t)ntiles * P * ntb;
     ebase[g] = E;
     E += (int64_t)ntiles * P;
   }
@@ -466,6 +476,8 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   pa.keybase = d_keybase;
   pa.ntu = lay->ntu;
   pa.ntv = lay->ntv;
+  pa.ntb = ntb;
+  pa.rows_per_tb = rows_per_tb;
   pa.drop = drop_oob;
   pa.key = d_key;
   pa.cell = cell_u;
@@ -554,6 +566,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   ia.ngroups = ngroups;
   ia.ntiles = ntiles;
   ia.ntv = lay->ntv;
+  ia.ntb = ntb;
   ia.W = geo.kern.W;
   ia.wterm = wterm;
   ia.chunks = d_chunks;

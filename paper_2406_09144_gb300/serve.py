@@ -165,20 +165,36 @@ def summarize(reqs, wall_s: float) -> dict:
 class GpuExecutor:
     """Runs admitted jobs on their own CUDA streams; one captured CUDA graph per job call."""
 
-    def __init__(self, device="cuda", graphs: bool = True, eps: float = 1e-5):
+    def __init__(self, device="cuda", graphs: bool = True, eps: float = 1e-5, workers: int = 2):
+        import concurrent.futures
+        import threading
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.graphs = graphs
         self.eps = eps
         self.streams = []
+        self.lock = threading.Lock()
+        # plan building is host work (validation, uploads, sort); worker threads overlap it with
+        # the device work of the jobs already admitted
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=workers)
+        self.graveyard = []
+        self.graveyard_bytes = 0
+        self.graveyard_limit = 32 << 30
 
     def _stream(self):
-        return self.streams.pop() if self.streams else self.torch.cuda.Stream(device=self.device)
+        with self.lock:
+            if self.streams:
+                return self.streams.pop()
+        return self.torch.cuda.Stream(device=self.device)
 
     def admit(self, r: Request):
+        return {"future": self.pool.submit(self._build, r), "ready": None}
+
+    def _build(self, r: Request):
         torch = self.torch
         from .binding import Plan
+        torch.cuda.set_device(self.device)
         s = self._stream()
         h = {"req": r, "stream": s, "event": None, "graph": None}
         with torch.cuda.stream(s):
@@ -201,7 +217,8 @@ class GpuExecutor:
             call()  # eager: sizes the per-stream workspace before any capture
             if self.graphs:
                 g = torch.cuda.CUDAGraph()
-                g.capture_begin()
+                # thread-local capture: other threads keep allocating and synchronising
+                g.capture_begin(capture_error_mode="thread_local")
                 call()
                 g.capture_end()
                 h["graph"] = g
@@ -211,11 +228,20 @@ class GpuExecutor:
         h["event"] = ev
         return h
 
-    def ready(self, h) -> bool:
-        return h["event"] is None or h["event"].query()
+    def _handle(self, h):
+        if h["ready"] is None:
+            if not h["future"].done():
+                return None
+            h["ready"] = h["future"].result()
+        return h["ready"]
 
-    def issue(self, h):
+    def ready(self, hh) -> bool:
+        h = self._handle(hh)
+        return h is not None and (h["event"] is None or h["event"].query())
+
+    def issue(self, hh):
         torch = self.torch
+        h = self._handle(hh)
         s = h["stream"]
         with torch.cuda.stream(s):
             if h["graph"] is not None:
@@ -226,13 +252,26 @@ class GpuExecutor:
             ev.record(s)
             h["event"] = ev
 
-    def finish(self, h):
+    def finish(self, hh):
+        h = self._handle(hh)
         h["event"].synchronize()
         h["req"].result = h["out"].cpu().numpy()
-        h["plan"].close()
+        # destroying a plan frees device memory, which synchronises the whole device; finished
+        # plans are parked and destroyed together once enough of them accumulate (or at close)
+        self.graveyard.append((h["plan"], h["graph"]))
+        self.graveyard_bytes += estimate_bytes(h["req"])
+        if self.graveyard_bytes > self.graveyard_limit:
+            self.close_finished()
         for k in ("graph", "plan", "sky", "out", "call"):
             h[k] = None
-        self.streams.append(h["stream"])
+        with self.lock:
+            self.streams.append(h["stream"])
+
+    def close_finished(self):
+        for plan, _ in self.graveyard:
+            plan.close()
+        self.graveyard = []
+        self.graveyard_bytes = 0
 
 
 def run_sequential(requests, device="cuda", eps=1e-5):
@@ -261,7 +300,7 @@ def run_sequential(requests, device="cuda", eps=1e-5):
 
 # ------------------------------------------------------------------------------ workload
 def make_requests(n: int, seed: int = 100, sizes=(256, 512, 1024, 2048, 4096),
-                  nvis_range=(1e4, 2e7), nchan_max: int = 8, ncalls: int = 4,
+                  nvis_range=(1e4, 2e7), nchan_max: int = 8, ncalls: int = 8,
                   psf_batch: int = 2) -> list:
     """Serving workload: image sizes uniform over `sizes`, visibility counts log-uniform over
     `nvis_range`, 1..nchan_max channels, half PSF-convolution and half major-cycle jobs, arrays
@@ -325,7 +364,9 @@ def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float
     # warm-up: one small job of each kind through both paths (module load, kernel attributes)
     warm = make_requests(2, seed=seed + 10 ** 6, sizes=(64,), nvis_range=(1e3, 2e3), nchan_max=1)
     run_sequential(_copy_requests(warm))
-    Scheduler(GpuExecutor(), budget, max_active).run(_copy_requests(warm))
+    ex0 = GpuExecutor()
+    Scheduler(ex0, budget, max_active).run(_copy_requests(warm))
+    ex0.close_finished()
     torch.cuda.synchronize()
 
     seq = _copy_requests(base)
@@ -334,22 +375,26 @@ def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float
     torch.cuda.synchronize()
     seq_wall = time.perf_counter() - t0
     srv = _copy_requests(base)
-    sch = Scheduler(GpuExecutor(graphs=True), budget, max_active)
+    ex1 = GpuExecutor(graphs=True)
+    sch = Scheduler(ex1, budget, max_active)
     t0 = time.perf_counter()
     sch.run(srv)
     torch.cuda.synchronize()
     srv_wall = time.perf_counter() - t0
+    ex1.close_finished()
     worst = 0.0
     for a, b in zip(seq, srv):
         d = float(np.linalg.norm(a.result - b.result) / max(np.linalg.norm(a.result), 1e-30))
         worst = max(worst, d)
     rate = load * n / seq_wall
     arr = poisson_arrivals(_copy_requests(base), rate, seed=seed)
-    sch2 = Scheduler(GpuExecutor(graphs=True), budget, max_active)
+    ex2 = GpuExecutor(graphs=True)
+    sch2 = Scheduler(ex2, budget, max_active)
     t0 = time.perf_counter()
     sch2.run(arr)
     torch.cuda.synchronize()
     arr_wall = time.perf_counter() - t0
+    ex2.close_finished()
     s_seq = summarize(seq, seq_wall)
     s_srv = summarize(srv, srv_wall)
     s_arr = summarize(arr, arr_wall)
@@ -357,7 +402,7 @@ def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float
         "workload": f"{n} jobs, images {kw.get('sizes', (256, 512, 1024, 2048, 4096))}, "
                     f"visibilities log-uniform {kw.get('nvis_range', (1e4, 2e7))}, 1-"
                     f"{kw.get('nchan_max', 8)} channels, half PSF-convolution / half major-cycle, "
-                    f"{kw.get('ncalls', 4)} calls per job",
+                    f"{kw.get('ncalls', 8)} calls per job",
         "sequential": s_seq, "server_closed": s_srv, "server_poisson": s_arr,
         "arrival_rate_per_s": rate, "max_active": max_active, "budget_bytes": budget,
         "peak_admitted_bytes": sch.peak_bytes, "peak_active": sch.peak_active,

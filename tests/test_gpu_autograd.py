@@ -1,8 +1,11 @@
 """Autograd wrappers: backward passes against the FP64 oracle and central finite differences.
 
-Tolerances: gradients against the oracle <= 1e-5 relative L2 (NUFFT accuracy eps); central
-differences (step 1e-3) of the quadratic / linear losses against <grad, e> <= 1e-3 relative,
-dominated by FP32 rounding of the loss values.
+Tolerances: gradients against the oracle <= 1e-5 relative L2 (NUFFT accuracy eps). Central
+differences of the linear (R, R^dagger) and quadratic (likelihood) losses are exact up to rounding
+for any step, so the step is chosen where FP32 rounding of the loss values stays below the
+1e-3 relative tolerance: 1.0 for the linear maps, 0.5 for the small likelihoods; at full size
+(16 x 2048^2) the step is 1e-3 along the gradient direction (no cancellation in <grad, e>) and
+0.1 along a random direction (1e-2, the FP32 rounding of sums over 4M pixels).
 """
 import numpy as np
 import pytest
@@ -49,7 +52,7 @@ def test_degrid_backward_is_R_dagger():
     assert rel(x.grad.cpu().numpy(), ref) <= 1e-5
     # central difference along a random direction (the loss is linear)
     e = torch.tensor(rng.standard_normal(plan.sky_shape), dtype=torch.float32, device="cuda")
-    h = 1e-3
+    h = 1.0
     with torch.no_grad():
         lp = (torch.conj(at) * plan.degrid(x + h * e)).real.double().sum()
         lm = (torch.conj(at) * plan.degrid(x - h * e)).real.double().sum()
@@ -72,7 +75,7 @@ def test_grid_backward_is_weighted_R():
     assert rel(y.grad.cpu().numpy(), ref) <= 1e-5
     e = torch.tensor(synth.complex_gaussian(plan.vis_shape, seed=5), dtype=torch.complex64,
                      device="cuda")
-    h = 1e-3
+    h = 1.0
     with torch.no_grad():
         lp = (gt.double() * plan.grid(y + h * e).double()).sum()
         lm = (gt.double() * plan.grid(y - h * e).double()).sum()
@@ -107,7 +110,7 @@ def test_likelihood_backward(exact):
     assert rel(s.grad.cpu().numpy(), rg * c[:, None, None, None]) <= 1e-5
     assert rel(d.grad.cpu().numpy(), -s0 * c[:, None, None, None]) <= 1e-6
     e = torch.tensor(rng.standard_normal(s0.shape), dtype=torch.float32, device="cuda")
-    h = 1e-3
+    h = 0.5
     with torch.no_grad():
         lp = (f(s + h * e, d, plan) * coef).sum()
         lm = (f(s - h * e, d, plan) * coef).sum()
@@ -128,12 +131,14 @@ def test_batch16_2048_psf_likelihood_fd_and_sampled_oracle():
     d = torch.randn((16, 1, 2048, 2048), generator=gen, device="cuda") * 100.0
     val = psf_likelihood(s, d, plan)
     val.sum().backward()
-    e = torch.randn(s.shape, generator=gen, device="cuda")
-    h = 1e-3
-    with torch.no_grad():
-        fd = (psf_likelihood(s + h * e, d, plan) - psf_likelihood(s - h * e, d, plan)) / (2 * h)
-        an = (s.grad.double() * e.double()).sum(dim=(1, 2, 3))
-    assert torch.allclose(fd, an, rtol=1e-3, atol=1e-3 * float(an.abs().max()))
+    g0 = s.grad.detach()
+    nrm = lambda t: t.double().pow(2).sum(dim=(1, 2, 3), keepdim=True).sqrt()
+    for e, h, tol in ((g0 * (nrm(s.detach()) / nrm(g0)).float(), 1e-3, 1e-3),
+                      (torch.randn(s.shape, generator=gen, device="cuda"), 0.1, 1e-2)):
+        with torch.no_grad():
+            fd = (psf_likelihood(s + h * e, d, plan) - psf_likelihood(s - h * e, d, plan)) / (2 * h)
+            an = (g0.double() * e.double()).sum(dim=(1, 2, 3))
+        assert torch.allclose(fd, an, rtol=tol, atol=tol * float(an.abs().max())), (fd, an)
     # FP64 oracle gradient PSF * s - d at sampled pixels of two batch elements
     P = psf.cpu().numpy()[0].astype(np.float64)
     rng = np.random.default_rng(8)

@@ -24,9 +24,11 @@ def test_results_alone_equal_results_in_the_mix():
     alone = run_sequential(_copy_requests(base))
     mix = poisson_arrivals(_copy_requests(base), rate_per_s=400.0, seed=1)
     budget = 3 * max(estimate_bytes(r) for r in base)
-    sch = Scheduler(GpuExecutor(graphs=True), budget, max_active=4)
+    ex = GpuExecutor(graphs=True)
+    sch = Scheduler(ex, budget, max_active=4)
     sch.run(mix)
     torch.cuda.synchronize()
+    ex.close_finished()
     assert sch.peak_bytes <= budget and sch.peak_active >= 2
     for a, b in zip(alone, mix):
         assert a.rid == b.rid and a.result.shape == b.result.shape
