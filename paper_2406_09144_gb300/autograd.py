@@ -24,7 +24,7 @@ def _weights(plan: Plan, device):
         import numpy as np
         src = plan._weights_host if getattr(plan, "_weights_host", None) is not None else \
             np.ones(plan.vis_shape, dtype=np.float32)
-        w = torch.as_tensor(src, dtype=torch.float32, device=device)
+        w = torch.tensor(np.array(src, dtype=np.float32), device=device)
         plan._weights_dev = w
     return w
 

@@ -85,6 +85,14 @@ __device__ __forceinline__ float es_eval(const EsKernel& k, float x) {
   return __expf(k.beta * (sqrtf(t) - 1.f));
 }
 
+// Same kernel with sqrt(t) taken as t * rsqrt(t): a few ulp in the square root, far below the
+// kernel's own approximation error; t = 0 (the footprint edge) maps to sqrt = 0.
+__device__ __forceinline__ float es_eval_fast(const EsKernel& k, float x) {
+  float z = x * k.inv_hw;
+  float t = fmaxf(1.f - z * z, 1e-30f);
+  return __expf(k.beta * (t * rsqrtf(t) - 1.f));
+}
+
 // ------------------------------------------------------------------ tiles and TMA
 constexpr int TILE = 32;       // grid cells per tile side (u and v)
 constexpr int MAXW = 16;       // largest kernel support

@@ -1030,36 +1030,47 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
     off[k] = cv[k] * BV + cu[k];
   }
   const int s0 = min(n, warp * seg), s1 = min(n, s0 + seg);
+  // per-warp staging of one batch of 32 visibilities: every lane evaluates the 2W kernel
+  // weights of its own visibility (phi(du - a) then phi(dv - b)) and its weighted value
+  constexpr int WS = 2 * W + 1;  // odd row stride: conflict-free per-lane row writes
+  __shared__ float wts[GRID_WARPS][32 * WS];
+  __shared__ float2 vals[GRID_WARPS][32];
+  float* mw = wts[warp];
+  float2* mv = vals[warp];
   int cur = -1;  // current origin offset rv * BV + ru, uniform across the warp
   float2 acc[NIT];
 #pragma unroll
   for (int k = 0; k < NIT; ++k) acc[k] = make_float2(0.f, 0.f);
   for (int base = s0; base < s1; base += 32) {
-    uint32_t cell = 0;
-    float du = 0.f, dv = 0.f;
-    float2 val = make_float2(0.f, 0.f);
-    if (base + lane < s1) {
+    const int nb = min(32, s1 - base);
+    int org = -2;
+    if (lane < nb) {
       const int i = it.x + order[base + lane];
-      cell = m.cell[i];
-      du = m.du[i];
-      dv = m.dv[i];
-      val = y[i];
+      const uint32_t cell = m.cell[i];
+      const float du = m.du[i], dv = m.dv[i];
+      float2 val = y[i];
       if (wterm) {
         const int rel = (p - (int)(cell & 15)) & 15;
         const float kw = es_eval(kern, m.dw[i] - (float)rel);
         val.x *= kw;
         val.y *= kw;
       }
+      org = ((int)((cell >> 4) & 0x3fff) - tv * TILE) * BV + (int)(cell >> 18) - tu * TILE;
+#pragma unroll
+      for (int a = 0; a < W; ++a) mw[lane * WS + a] = es_eval_fast(kern, du - (float)a);
+#pragma unroll
+      for (int b = 0; b < W; ++b) mw[lane * WS + W + b] = es_eval_fast(kern, dv - (float)b);
+      mv[lane] = val;
     }
-    const int nb = min(32, s1 - base);
-    for (int j = 0; j < nb; ++j) {
-      const uint32_t cj = __shfl_sync(0xffffffffu, cell, j);
-      const float duj = __shfl_sync(0xffffffffu, du, j);
-      const float dvj = __shfl_sync(0xffffffffu, dv, j);
-      const float vr = __shfl_sync(0xffffffffu, val.x, j);
-      const float vi = __shfl_sync(0xffffffffu, val.y, j);
-      const int org = ((int)((cj >> 4) & 0x3fff) - tv * TILE) * BV + (int)(cj >> 18) - tu * TILE;
-      if (org != cur) {
+    // run starts: a visibility whose footprint origin differs from its predecessor's
+    const int prev = __shfl_up_sync(0xffffffffu, org, 1);
+    const unsigned starts =
+        __ballot_sync(0xffffffffu, lane < nb && org != (lane == 0 ? cur : prev));
+    __syncwarp();
+    int j = 0;
+    while (j < nb) {
+      if ((starts >> j) & 1u) {
+        const int oj = __shfl_sync(0xffffffffu, org, j);
         if (cur >= 0) {
 #pragma unroll
           for (int k = 0; k < NIT; ++k)
@@ -1069,22 +1080,26 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
               g.x += acc[k].x;
               g.y += acc[k].y;
               *c = g;
-              acc[k] = make_float2(0.f, 0.f);
             }
         }
-        cur = org;
-      }
-      float kval = 0.f;
-      if (lane < 2 * W) kval = es_eval(kern, lane < W ? duj - (float)lane : dvj - (float)(lane - W));
 #pragma unroll
-      for (int k = 0; k < NIT; ++k) {
-        const float ku = __shfl_sync(0xffffffffu, kval, cu[k]);
-        const float kv = __shfl_sync(0xffffffffu, kval, (W + cv[k]) & 31);
-        const float wgt = ku * kv;
-        acc[k].x = fmaf(wgt, vr, acc[k].x);
-        acc[k].y = fmaf(wgt, vi, acc[k].y);
+        for (int k = 0; k < NIT; ++k) acc[k] = make_float2(0.f, 0.f);
+        cur = oj;
+      }
+      const unsigned rest = j < 31 ? (starts & ~((2u << j) - 1u)) : 0u;
+      const int e = rest ? __ffs(rest) - 1 : nb;
+      for (; j < e; ++j) {
+        const float2 v = mv[j];
+        const float* wj = mw + j * WS;
+#pragma unroll
+        for (int k = 0; k < NIT; ++k) {
+          const float wgt = wj[cu[k]] * wj[W + (cv[k] < W ? cv[k] : 0)];
+          acc[k].x = fmaf(wgt, v.x, acc[k].x);
+          acc[k].y = fmaf(wgt, v.y, acc[k].y);
+        }
       }
     }
+    __syncwarp();
   }
   if (cur >= 0) {
 #pragma unroll

@@ -171,6 +171,8 @@ class GpuExecutor:
         import torch
         self.torch = torch
         self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device(self.device.type, torch.cuda.current_device())
         self.graphs = graphs
         self.eps = eps
         self.streams = []
