@@ -395,12 +395,14 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
   set_kernel(&pg, p->geo.kern.W);
   pg.wterm = false;
   pg.nterm = false;
+  pg.async = s;  // the PSF geometry and layout are transients of plan creation
   FR_TRY(ensure_twiddles(p, ilog2(pg.Nu), s));
   FR_TRY(ensure_twiddles(p, ilog2(pg.Nv), s));
   std::vector<double> iu, iv;
   kernel_ft_tables(pg, iu, iv);
   FR_TRY(make_tables(&pg, iu, iv, s));
   VisLayout pl;
+  pl.async = s;
   std::vector<double> wlo(p->nsky, 0.0);
   std::vector<int> planes(p->nsky, 1);
   int r = build_layout(pg, d_uvw, p->nrow, freqs, d_freqs, p->nchan, d_weights, p->nsky, wlo, planes,
@@ -409,11 +411,14 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
   const size_t nimg2 = (size_t)pg.nx * pg.ny;
   const int hp = p->geo.ny + 2;
   if (r == FR_OK) {
+    // transients are stream-ordered: building a plan does not synchronise the device
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&grid, (size_t)pg.Nu * pg.Nv * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&b1, (size_t)pg.nx * pg.Nv * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&y, (size_t)std::max<int64_t>(pl.nsorted, 1) * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&h, (size_t)p->nsky * pg.nx * hp * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMallocAsync(&grid, (size_t)pg.Nu * pg.Nv * sizeof(float2), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&b1, (size_t)pg.nx * pg.Nv * sizeof(float2), s);
+    if (e == cudaSuccess)
+      e = cudaMallocAsync(&y, (size_t)std::max<int64_t>(pl.nsorted, 1) * sizeof(float2), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h, (size_t)p->nsky * pg.nx * hp * sizeof(float2), s);
+    if (e == cudaSuccess && grid) e = cudaMemsetAsync(grid, 0, (size_t)pg.Nu * pg.Nv * sizeof(float2), s);
     if (e == cudaSuccess) e = cudaMalloc(&p->psf_img, (size_t)p->nsky * nimg2 * sizeof(float));
     if (e == cudaSuccess)
       e = cudaMalloc(&p->transfer, (size_t)p->nsky * pg.nx * (p->geo.ny + 1) * sizeof(float));
@@ -423,7 +428,7 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
     }
   }
   if (r == FR_OK) {
-    bool zero = false;
+    bool zero = true;  // zeroed above
     r = run_grid(p, pg, pl, nullptr, nullptr, 1, p->psf_img, grid, b1, y, s, &zero);
   }
   if (r == FR_OK) r = zero_psf_edges(p->psf_img, p->nsky, pg.nx, pg.ny, s);
@@ -433,7 +438,7 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
   // psf_norm = sum of the kept weights per image (FP64)
   double* d_norm = nullptr;
   if (r == FR_OK) {
-    cudaError_t e = cudaMalloc(&d_norm, p->nsky * sizeof(double));
+    cudaError_t e = cudaMallocAsync(&d_norm, p->nsky * sizeof(double), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_norm, 0, p->nsky * sizeof(double), s);
     for (int g = 0; g < p->nsky && e == cudaSuccess; ++g) {
       const int64_t b = pl.group_begin[g], en = pl.group_begin[g + 1];
@@ -450,15 +455,11 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
       r = FR_ECUDA;
     }
   }
-  cudaStreamSynchronize(s);
-  cudaFree(d_norm);
-  cudaFree(grid);
-  cudaFree(b1);
-  cudaFree(y);
-  cudaFree(h);
-  cudaFree(pg.corr);
-  cudaFree(pg.tq);
+  for (void* q : {(void*)d_norm, (void*)grid, (void*)b1, (void*)y, (void*)h, (void*)pg.corr,
+                  (void*)pg.tq})
+    if (q) cudaFreeAsync(q, s);
   free_layout(&pl);
+  cudaStreamSynchronize(s);
   if (r == FR_OK) {
     p->has_psf = true;
     p->resident += (size_t)p->nsky * nimg2 * sizeof(float) +
@@ -563,21 +564,24 @@ static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int
   // device copies of the inputs (plan-time only)
   double *d_uvw = nullptr, *d_freqs = nullptr;
   float* d_w = nullptr;
-  struct Free {
+  struct Free {  // stream-ordered release: no device-wide synchronisation
     void* a;
-    ~Free() { cudaFree(a); }
+    cudaStream_t s;
+    ~Free() {
+      if (a) cudaFreeAsync(a, s);
+    }
   };
-  FR_CUDA_TRY(cudaMalloc(&d_uvw, (size_t)nrow * 3 * sizeof(double)));
-  Free f1{d_uvw};
-  FR_CUDA_TRY(cudaMalloc(&d_freqs, nchan * sizeof(double)));
-  Free f2{d_freqs};
+  FR_CUDA_TRY(cudaMallocAsync(&d_uvw, (size_t)nrow * 3 * sizeof(double), s));
+  Free f1{d_uvw, s};
+  FR_CUDA_TRY(cudaMallocAsync(&d_freqs, nchan * sizeof(double), s));
+  Free f2{d_freqs, s};
   FR_CUDA_TRY(cudaMemcpyAsync(d_uvw, uvw, (size_t)nrow * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
   FR_CUDA_TRY(cudaMemcpyAsync(d_freqs, freqs, nchan * sizeof(double), cudaMemcpyHostToDevice, s));
   if (weights) {
-    FR_CUDA_TRY(cudaMalloc(&d_w, (size_t)nrow * nchan * sizeof(float)));
+    FR_CUDA_TRY(cudaMallocAsync(&d_w, (size_t)nrow * nchan * sizeof(float), s));
     FR_CUDA_TRY(cudaMemcpyAsync(d_w, weights, (size_t)nrow * nchan * sizeof(float), cudaMemcpyHostToDevice, s));
   }
-  Free f3{d_w};
+  Free f3{d_w, s};
 
   std::vector<double> iu, iv;
   kernel_ft_tables(g, iu, iv);

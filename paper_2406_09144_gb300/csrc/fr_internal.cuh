@@ -114,6 +114,7 @@ struct Geometry {
   double dw = 0;                           // plane spacing (wavelengths)
   float* corr = nullptr;                   // [nx*ny] (-1)^(px+py) / (n Phi_u Phi_v Phi_w)
   int32_t* tq = nullptr;                   // [nx*ny] (t - t_c) / t_half * 2^30  (wterm)
+  cudaStream_t async = nullptr;            // tables are stream-ordered transients when set
 };
 
 // Visibilities sorted by (image group, tile, first w-plane) for one geometry.
@@ -140,6 +141,7 @@ struct VisLayout {
   int4* items = nullptr;     // {vis_begin, vis_count, tu << 16 | tv, 0}
   int64_t nitems = 0;
   size_t bytes = 0;
+  cudaStream_t async = nullptr;  // arrays are stream-ordered transients when set
 };
 
 // Per-stream scratch.

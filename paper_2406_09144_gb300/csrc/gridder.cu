@@ -337,11 +337,13 @@ static unsigned grid1d(int64_t n, int threads = 256) {
   return (unsigned)b;
 }
 
+// allocation of plan data; stream-ordered when `async` is set (transient layouts and tables)
 template <class T>
-static int dalloc(T** p, size_t n, size_t* acc) {
+static int dalloc(T** p, size_t n, size_t* acc, cudaStream_t async = nullptr) {
   *p = nullptr;
   if (n == 0) return FR_OK;
-  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  cudaError_t e = async ? cudaMallocAsync((void**)p, n * sizeof(T), async)
+                        : cudaMalloc((void**)p, n * sizeof(T));
   if (e != cudaSuccess) {
     set_error("cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
     *p = nullptr;
@@ -352,14 +354,14 @@ static int dalloc(T** p, size_t n, size_t* acc) {
 }
 
 void free_layout(VisLayout* lay) {
-  cudaFree(lay->cell);
-  cudaFree(lay->du);
-  cudaFree(lay->dv);
-  cudaFree(lay->dw);
-  cudaFree(lay->ph);
-  cudaFree(lay->perm);
-  cudaFree(lay->wgt);
-  cudaFree(lay->items);
+  for (void* q : {(void*)lay->cell, (void*)lay->du, (void*)lay->dv, (void*)lay->dw, (void*)lay->ph,
+                  (void*)lay->perm, (void*)lay->wgt, (void*)lay->items}) {
+    if (!q) continue;
+    if (lay->async)
+      cudaFreeAsync(q, lay->async);
+    else
+      cudaFree(q);
+  }
   lay->cell = nullptr;
   lay->du = lay->dv = lay->dw = lay->wgt = nullptr;
   lay->ph = lay->perm = nullptr;
@@ -367,17 +369,27 @@ void free_layout(VisLayout* lay) {
 }
 
 namespace {
-// RAII holder of temporary device buffers
+// RAII holder of plan-time temporaries, stream-ordered (cudaMallocAsync / cudaFreeAsync) so that
+// building a plan never synchronises the device: other streams keep running meanwhile
 struct Temps {
+  cudaStream_t s;
   std::vector<void*> p;
+  explicit Temps(cudaStream_t st) : s(st) {}
   ~Temps() {
-    for (void* q : p) cudaFree(q);
+    for (void* q : p) cudaFreeAsync(q, s);
   }
   template <class T>
   int alloc(T** out, size_t n) {
-    int r = dalloc(out, n, nullptr);
-    if (r == FR_OK && *out) p.push_back(*out);
-    return r;
+    *out = nullptr;
+    if (n == 0) return FR_OK;
+    cudaError_t e = cudaMallocAsync((void**)out, n * sizeof(T), s);
+    if (e != cudaSuccess) {
+      set_error("cudaMallocAsync of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+      *out = nullptr;
+      return FR_ENOMEM;
+    }
+    p.push_back(*out);
+    return FR_OK;
   }
 };
 }  // namespace
@@ -422,7 +434,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
     return FR_EUNSUPPORTED;
   }
 
-  Temps t;
+  Temps t(s);
   int *d_key, *d_count, *d_off, *d_keybase, *d_planes, *d_err;
   double* d_wlo;
   int64_t* d_ebase;
@@ -519,14 +531,14 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   const int64_t N = h_total;
 
   size_t acc = 0;
-  FR_TRY(dalloc(&lay->cell, N, &acc));
-  FR_TRY(dalloc(&lay->du, N, &acc));
-  FR_TRY(dalloc(&lay->dv, N, &acc));
-  FR_TRY(dalloc(&lay->wgt, N, &acc));
-  FR_TRY(dalloc(&lay->perm, N, &acc));
+  FR_TRY(dalloc(&lay->cell, N, &acc, lay->async));
+  FR_TRY(dalloc(&lay->du, N, &acc, lay->async));
+  FR_TRY(dalloc(&lay->dv, N, &acc, lay->async));
+  FR_TRY(dalloc(&lay->wgt, N, &acc, lay->async));
+  FR_TRY(dalloc(&lay->perm, N, &acc, lay->async));
   if (wterm) {
-    FR_TRY(dalloc(&lay->dw, N, &acc));
-    FR_TRY(dalloc(&lay->ph, N, &acc));
+    FR_TRY(dalloc(&lay->dw, N, &acc, lay->async));
+    FR_TRY(dalloc(&lay->ph, N, &acc, lay->async));
   }
   // cursor = offsets (reuse the count buffer)
   FR_CUDA_TRY(cudaMemcpyAsync(d_count, d_off, K * sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -596,7 +608,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   FR_CUDA_TRY(cudaStreamSynchronize(s));
   lay->plane_items.assign(pitems.begin(), pitems.end());
   lay->nitems = pitems[nq - 1];
-  FR_TRY(dalloc(&lay->items, lay->nitems, &acc));
+  FR_TRY(dalloc(&lay->items, lay->nitems, &acc, lay->async));
   ia.items = lay->items;
   if (lay->nitems > 0) {
     emit_items<<<grid1d(E), 256, 0, s>>>(ia, E);
@@ -721,7 +733,7 @@ int make_tables(Geometry* geo, const std::vector<double>& inv_phi_u,
   const int64_t n = (int64_t)geo->nx * geo->ny;
   std::vector<double> gx, gw;
   gauss_legendre(4 * geo->kern.W + 32, gx, gw);
-  Temps t;
+  Temps t(s);
   double *d_pu, *d_pv, *d_gx, *d_gw;
   FR_TRY(t.alloc(&d_pu, geo->nx));
   FR_TRY(t.alloc(&d_pv, geo->ny));
@@ -731,8 +743,8 @@ int make_tables(Geometry* geo, const std::vector<double>& inv_phi_u,
   FR_CUDA_TRY(cudaMemcpyAsync(d_pv, inv_phi_v.data(), geo->ny * sizeof(double), cudaMemcpyHostToDevice, s));
   FR_CUDA_TRY(cudaMemcpyAsync(d_gx, gx.data(), gx.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   FR_CUDA_TRY(cudaMemcpyAsync(d_gw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  FR_TRY(dalloc(&geo->corr, n, nullptr));
-  if (geo->wterm) FR_TRY(dalloc(&geo->tq, n, nullptr));
+  FR_TRY(dalloc(&geo->corr, n, nullptr, geo->async));
+  if (geo->wterm) FR_TRY(dalloc(&geo->tq, n, nullptr, geo->async));
   TableArgs a;
   a.nx = geo->nx;
   a.ny = geo->ny;
