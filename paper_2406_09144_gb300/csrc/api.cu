@@ -224,6 +224,7 @@ int ensure_twiddles(fr_plan* p, int log2l, cudaStream_t s) {
 // ------------------------------------------------------------------------ workspaces
 static void free_ws(Workspace* w) {
   cudaFree(w->b1);
+  cudaFree(w->b1g);
   cudaFree(w->grid);
   cudaFree(w->vbuf);
   cudaFree(w->h);
@@ -258,12 +259,15 @@ static int get_ws(fr_plan* p, cudaStream_t s, Workspace** out) {
   const Geometry& g = p->geo;
   int r;
   if ((r = ws_alloc(&w->b1, (size_t)g.nx * g.Nv, w.get())) ||
+      (r = ws_alloc(&w->b1g, (size_t)g.nx * g.Nv, w.get())) ||
       (r = ws_alloc(&w->grid, (size_t)g.Nu * g.Nv, w.get())) ||
       (r = ws_alloc(&w->vbuf, (size_t)std::max<int64_t>(p->lay.nsorted, 1), w.get()))) {
     free_ws(w.release());
     return r;
   }
-  cudaError_t e = cudaMemsetAsync(w->grid, 0, (size_t)g.Nu * g.Nv * sizeof(float2), s);
+  // the gridding half plane is only ever written inside the band: zero it once
+  cudaError_t e = cudaMemsetAsync(w->b1g, 0, (size_t)g.nx * g.Nv * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->grid, 0, (size_t)g.Nu * g.Nv * sizeof(float2), s);
   if (e != cudaSuccess) {
     set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(e));
     free_ws(w.release());
@@ -318,6 +322,10 @@ static PlaneArgs plane_args(const Geometry& geo, const VisLayout& lay, int g, in
   a.tq = geo.tq;
   a.wterm = geo.wterm ? 1 : 0;
   a.k64 = geo.wterm ? plane_k64(geo, plane_w(geo, lay, g, p)) : 0;
+  a.bu0 = lay.bu0;
+  a.bu1 = lay.bu1;
+  a.bv0 = lay.bv0;
+  a.bv1 = lay.bv1;
   return a;
 }
 
@@ -419,6 +427,8 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
       e = cudaMallocAsync(&y, (size_t)std::max<int64_t>(pl.nsorted, 1) * sizeof(float2), s);
     if (e == cudaSuccess) e = cudaMallocAsync(&h, (size_t)p->nsky * pg.nx * hp * sizeof(float2), s);
     if (e == cudaSuccess && grid) e = cudaMemsetAsync(grid, 0, (size_t)pg.Nu * pg.Nv * sizeof(float2), s);
+    // the gridding half plane must be zero outside the band of the PSF layout
+    if (e == cudaSuccess && b1) e = cudaMemsetAsync(b1, 0, (size_t)pg.nx * pg.Nv * sizeof(float2), s);
     if (e == cudaSuccess) e = cudaMalloc(&p->psf_img, (size_t)p->nsky * nimg2 * sizeof(float));
     if (e == cudaSuccess)
       e = cudaMalloc(&p->transfer, (size_t)p->nsky * pg.nx * (p->geo.ny + 1) * sizeof(float));
@@ -735,7 +745,7 @@ int fr_grid(fr_plan_t p, const fr_cf32* vis, int32_t apply_weights, float* dirty
   Workspace* w;
   FR_TRY(get_ws(p, s, &w));
   return run_grid(p, p->geo, p->lay, w, (const float2*)vis, apply_weights ? 1 : 0, dirty, w->grid,
-                  w->b1, w->vbuf, s, &w->grid_zero);
+                  w->b1g, w->vbuf, s, &w->grid_zero);
 }
 
 int fr_dirty_psf(fr_plan_t p, const fr_cf32* vis, float* dirty, float* psf, double* psf_norm,
@@ -821,7 +831,8 @@ int fr_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, int32_
     const float* sb = sky + b * n;
     float* gb = grad + b * n;
     FR_TRY(run_degrid(p, p->geo, p->lay, w, sb, w->tmp_vis, s));
-    FR_TRY(run_grid(p, p->geo, p->lay, w, w->tmp_vis, 1, gb, w->grid, w->b1, w->vbuf, s, &w->grid_zero));
+    FR_TRY(run_grid(p, p->geo, p->lay, w, w->tmp_vis, 1, gb, w->grid, w->b1g, w->vbuf, s,
+                    &w->grid_zero));
     {
       ProfScope ps(PC_REDUCE, s, (double)n * 16.0);
       lik_kernel<<<nblocks(n), RED_T, 0, s>>>(sb, gb, dirty + b * n, n, w->red + b);
@@ -864,7 +875,7 @@ int fr_major_cycle(fr_plan_t p, const float* sky, const float* dirty, float* res
   }
   const size_t n = (size_t)p->nsky * p->geo.nx * p->geo.ny;
   if (resid || resid_norm2) {
-    FR_TRY(run_grid(p, p->geo, p->lay, w, w->tmp_vis, 1, w->tmp_img, w->grid, w->b1, w->vbuf, s,
+    FR_TRY(run_grid(p, p->geo, p->lay, w, w->tmp_vis, 1, w->tmp_img, w->grid, w->b1g, w->vbuf, s,
                     &w->grid_zero));
     float* r = resid ? resid : w->tmp_img;
     FR_TRY(sub_images(dirty, w->tmp_img, r, n, s));

@@ -37,10 +37,11 @@ struct D1Op : OpBase {
   const int32_t* tq;
   long long k64;
   int wterm;
-  float2* b1t;  // [Nv][nx]
+  float2* b1t;  // [band v][nx]
   int nx, ny, Nv;
+  int vb0, nvb;  // occupied band of v: only these outputs are stored
   __host__ __device__ int nseq() const { return nx; }
-  __host__ __device__ int nout() const { return Nv; }
+  __host__ __device__ int nout() const { return nvb; }
   __device__ float2 load(int jx, int i) const {
     const int hy = ny >> 1;
     int jy;
@@ -57,8 +58,8 @@ struct D1Op : OpBase {
     plane_phase(__ldg(&tq[pix]), k64, &c, &s);
     return make_float2(val * c, -val * s);
   }
-  __device__ double store(int jx, int v, SeqView s) const {
-    b1t[(size_t)v * nx + jx] = s[v];
+  __device__ double store(int jx, int o, SeqView s) const {
+    b1t[(size_t)o * nx + jx] = s[vb0 + o];
     return 0.0;
   }
 };
@@ -67,8 +68,9 @@ struct D2Op : OpBase {
   const float2* b1t;
   float2* grid;  // [Nv][Nu]
   int nx, Nu, Nv;
-  __host__ __device__ int nseq() const { return Nv; }
-  __host__ __device__ int nout() const { return Nu; }
+  int vb0, nvb, ub0, nub;  // only band rows are transformed, only band columns stored
+  __host__ __device__ int nseq() const { return nvb; }
+  __host__ __device__ int nout() const { return nub; }
   __device__ float2 load(int v, int i) const {
     const int hx = nx >> 1;
     int jx;
@@ -78,10 +80,11 @@ struct D2Op : OpBase {
       jx = i - Nu + hx;
     else
       return make_float2(0.f, 0.f);
-    return b1t[(size_t)v * nx + jx];
+    return b1t[(size_t)v * nx + jx];  // v: band row index
   }
-  __device__ double store(int v, int u, SeqView s) const {
-    grid[(size_t)v * Nu + u] = s[u];
+  __device__ double store(int q, int o, SeqView s) const {
+    const int u = ub0 + o;
+    grid[(size_t)(vb0 + q) * Nu + u] = s[u];
     return 0.0;
   }
 };
@@ -89,19 +92,27 @@ struct D2Op : OpBase {
 struct G1Op : OpBase {
   static constexpr bool TRANSPOSED = true;
   float2* grid;  // [Nv][Nu]
-  float2* b1;    // [nx][Nv]
+  float2* b1;    // [nx][Nv], zero outside the band columns
   int nx, Nu, Nv;
-  __host__ __device__ int nseq() const { return Nv; }
+  int vb0, nvb, ub0, nub;  // rows outside the band are zero and transform to zero
+  __host__ __device__ int nseq() const { return nvb; }
   __host__ __device__ int nout() const { return nx; }
-  __device__ float2 load(int v, int i) const { return grid[(size_t)v * Nu + i]; }
-  __device__ void after_load(int seq0, int nb) const {
-    float4* p = reinterpret_cast<float4*>(grid + (size_t)seq0 * Nu);
-    const int n = nb * Nu / 2;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __device__ float2 load(int q, int i) const {
+    if (i < ub0 || i >= ub0 + nub) return make_float2(0.f, 0.f);  // zero outside the band
+    return grid[(size_t)(vb0 + q) * Nu + i];
   }
-  __device__ double store(int v, int o, SeqView s) const {
+  __device__ void after_load(int seq0, int nb) const {
+    // the gridder writes only inside the band: zeroing the band part of the rows restores an
+    // all-zero grid
+    const int n = nb * nub;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int r = i / nub, c = i - (i / nub) * nub;
+      grid[(size_t)(vb0 + seq0 + r) * Nu + ub0 + c] = make_float2(0.f, 0.f);
+    }
+  }
+  __device__ double store(int q, int o, SeqView s) const {
     const int i = (o - (nx >> 1) + Nu) & (Nu - 1);
-    b1[(size_t)o * Nv + v] = s[i];
+    b1[(size_t)o * Nv + vb0 + q] = s[i];
     return 0.0;
   }
 };
@@ -151,8 +162,12 @@ static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG
 
 int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
                    const float2* twv, const float2* twu, cudaStream_t s) {
-  const double img = (double)a.nx * a.ny, half = (double)a.nx * a.Nv, full = (double)a.Nu * a.Nv;
+  const int nvb = a.bv1 - a.bv0 + 1, nub = a.bu1 - a.bu0 + 1;
+  if (nvb <= 0 || nub <= 0) return FR_OK;
+  const double img = (double)a.nx * a.ny, half = (double)a.nx * nvb, full = (double)nvb * nub;
   D1Op o1;
+  o1.vb0 = a.bv0;
+  o1.nvb = nvb;
   o1.sky = sky;
   o1.corr = a.corr;
   o1.tq = a.tq;
@@ -173,22 +188,34 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
   o2.nx = a.nx;
   o2.Nu = a.Nu;
   o2.Nv = a.Nv;
+  o2.vb0 = a.bv0;
+  o2.nvb = nvb;
+  o2.ub0 = a.bu0;
+  o2.nub = nub;
   ProfScope ps(PC_FFT_COLS, s, half * 8.0 + full * 8.0);
   return d2(ilog2(a.Nu), o2, twu, s);
 }
 
 int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
                   const float2* twu, const float2* twv, cudaStream_t s) {
-  const double img = (double)a.nx * a.ny, half = (double)a.nx * a.Nv, full = (double)a.Nu * a.Nv;
+  const int nvb = a.bv1 - a.bv0 + 1, nub = a.bu1 - a.bu0 + 1;
+  if (nvb <= 0 || nub <= 0) return FR_OK;
+  const double img = (double)a.nx * a.ny, band_rows = (double)nvb * a.Nu,
+               band = (double)nvb * nub, half = (double)a.nx * a.Nv;
   G1Op o1;
   o1.grid = grid;
   o1.b1 = b1;
   o1.nx = a.nx;
   o1.Nu = a.Nu;
   o1.Nv = a.Nv;
+  o1.vb0 = a.bv0;
+  o1.nvb = nvb;
+  o1.ub0 = a.bu0;
+  o1.nub = nub;
   {
-    // grid in, grid zeroed, cropped plane out
-    ProfScope ps(PC_FFT_COLS, s, full * 16.0 + half * 8.0);
+    // band rows in, band zeroed, cropped band columns of the half plane out
+    ProfScope ps(PC_FFT_COLS, s, band * 16.0 + (double)a.nx * nvb * 8.0);
+    (void)band_rows;
     FR_TRY(g1(ilog2(a.Nu), o1, twu, s));
   }
   G2Op o2;

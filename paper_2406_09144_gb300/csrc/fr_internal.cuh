@@ -127,6 +127,9 @@ struct VisLayout {
   std::vector<int> plane_base;          // [ngroups] index of (g, 0) in plane_items
   std::vector<int64_t> group_begin;     // [ngroups + 1] sorted index range of each group
   std::vector<int64_t> plane_visits;    // [sum planes] visibilities processed per (g, p)
+  // grid band holding every kernel footprint (inclusive cell ranges); cells outside it are
+  // never read by the degridder and never written by the gridder
+  int bu0 = 0, bu1 = -1, bv0 = 0, bv1 = -1;
   int64_t nvis = 0;                     // visibilities in user order
   int64_t nsorted = 0;                  // kept after dropping
   int64_t ndropped = 0;
@@ -147,7 +150,8 @@ struct VisLayout {
 // Per-stream scratch.
 struct Workspace {
   cudaStream_t stream = nullptr;
-  float2* b1 = nullptr;      // [nx][Nv] half-transformed plane
+  float2* b1 = nullptr;      // [band v][nx] half-transformed plane of the degridding pre-pass
+  float2* b1g = nullptr;     // [nx][Nv] half plane of the gridding post-pass (zero off-band)
   float2* grid = nullptr;    // [Nu][Nv] oversampled grid (kept zero between fr_grid calls)
   bool grid_zero = false;
   float2* vbuf = nullptr;    // [nsorted] sorted visibilities (accumulator / weighted input)
@@ -193,6 +197,7 @@ int ensure_twiddles(fr_plan* p, int log2l, cudaStream_t s);
 struct PlaneArgs {
   // geometry
   int nx, ny, Nu, Nv;
+  int bu0, bu1, bv0, bv1;  // occupied grid band (inclusive)
   const float* corr;
   const int32_t* tq;
   long long k64;  // per-plane phase multiplier, Q64 cycles per tq unit (0 without w)

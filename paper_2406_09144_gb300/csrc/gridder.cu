@@ -12,6 +12,7 @@
 // image side. The paper names the wgridder for this operator but does not describe it.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -308,6 +309,32 @@ __global__ void emit_items(ItemArgs a, int64_t E) {
     int o = a.item_off[e];
     for (int s = 0; s < c; s += GRID_CHUNK, ++o)
       a.items[o] = make_int4(b + s, min(GRID_CHUNK, c - s), (tu << 16) | tv, 0);
+  }
+}
+
+// bounds of the footprint origins: band = {min iu0, max iu0, min iv0, max iv0}
+__global__ void band_kernel(const uint32_t* cell, int64_t n, int* band) {
+  int a = 1 << 30, b = -1, c = 1 << 30, d = -1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = cell[i];
+    const int u = (int)(x >> 18), v = (int)((x >> 4) & 0x3fff);
+    a = min(a, u);
+    b = max(b, u);
+    c = min(c, v);
+    d = max(d, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = min(a, __shfl_down_sync(0xffffffffu, a, o));
+    b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+    c = min(c, __shfl_down_sync(0xffffffffu, c, o));
+    d = max(d, __shfl_down_sync(0xffffffffu, d, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&band[0], a);
+    atomicMax(&band[1], b);
+    atomicMin(&band[2], c);
+    atomicMax(&band[3], d);
   }
 }
 
@@ -615,6 +642,30 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
     FR_LAUNCHED();
   }
   // visibility visits per (group, plane), for launch accounting
+  // occupied band of the grid: the union of all kernel footprints
+  {
+    int* d_band;
+    FR_TRY(t.alloc(&d_band, 4));
+    const int init[4] = {1 << 30, -1, 1 << 30, -1};
+    FR_CUDA_TRY(cudaMemcpyAsync(d_band, init, sizeof init, cudaMemcpyHostToDevice, s));
+    if (N > 0) {
+      band_kernel<<<grid1d(N), 256, 0, s>>>(lay->cell, N, d_band);
+      FR_LAUNCHED();
+    }
+    int hb[4];
+    FR_CUDA_TRY(cudaMemcpyAsync(hb, d_band, sizeof hb, cudaMemcpyDeviceToHost, s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+    const int W = geo.kern.W;
+    if (N > 0) {
+      lay->bu0 = hb[0];
+      lay->bu1 = std::min(geo.Nu - 1, hb[1] + W - 1);
+      lay->bv0 = hb[2];
+      lay->bv1 = std::min(geo.Nv - 1, hb[3] + W - 1);
+    } else {
+      lay->bu0 = lay->bv0 = 0;
+      lay->bu1 = lay->bv1 = -1;
+    }
+  }
   lay->plane_visits.assign(nq - 1, 0);
   if (nq > 1 && lay->nitems > 0) {
     long long* d_visits;
