@@ -160,8 +160,24 @@ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
 FR_HD int spad(int i) { return i + (i >> 4); }
 constexpr int spad_len(int n) { return n + (n >> 4); }
 
+// v[r] *= w^r for r in [r, R), with w^r built from pw[e] = w^(2^e) and at most two more
+// products per factor (a few ulp); all indices are compile-time, so everything stays in registers
+template <int R, int r>
+FR_HD void twiddle_rec(float2* v, const float2* pw, float2* wr) {
+  if constexpr (r < R) {
+    constexpr int h = ilog2(r);
+    if constexpr (r == (1 << h))
+      wr[r] = pw[h];
+    else
+      wr[r] = cmul(pw[h], wr[r - (1 << h)]);
+    v[r] = cmul(v[r], wr[r]);
+    twiddle_rec<R, r + 1>(v, pw, wr);
+  }
+}
+
 // One Stockham stage on a single task j, reading from `in` and writing to `out`
-// (both indexed through spad), used by the host emulation tests and as reference.
+// (both indexed through spad), with the same twiddle construction as the kernels; used by the
+// host emulation tests.
 template <int R, int DIR>
 FR_HD void stockham_task(const float2* in, float2* out, const float2* tw, int L, int Ns, int j) {
   float2 v[R];
@@ -169,14 +185,17 @@ FR_HD void stockham_task(const float2* in, float2* out, const float2* tw, int L,
   const int stride = L / R;
   const int tstep = L / (Ns * R);
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    float2 x = in[spad(j + r * stride)];
-    if (r > 0) {
-      float2 w = tw[(r * k * tstep) & (L - 1)];
+  for (int r = 0; r < R; ++r) v[r] = in[spad(j + r * stride)];
+  if (Ns > 1) {
+    constexpr int LB = ilog2(R);
+    float2 pw[LB];
+    for (int e = 0; e < LB; ++e) {
+      float2 w = tw[(k * tstep) << e];
       if (DIR > 0) w.y = -w.y;
-      x = cmul(x, w);
+      pw[e] = w;
     }
-    v[r] = x;
+    float2 wr[R];
+    twiddle_rec<R, 1>(v, pw, wr);
   }
   dft_r<R, DIR>(v);
   const int base = (j / Ns) * Ns * R + k;

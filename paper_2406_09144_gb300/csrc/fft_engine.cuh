@@ -16,8 +16,9 @@ namespace fr {
 template <int LOG2L>
 struct FftCfg {
   static constexpr int L = 1 << LOG2L;
-  // two sequences per CTA for the long transforms keep transposed stores 16 bytes wide
-  static constexpr int B = (L >= 16384) ? 1 : (L >= 4096 ? 2 : 4096 / L);
+  // L = 8192 and 16384 run one sequence per CTA so that two CTAs share an SM and overlap
+  // their load, transform and store phases; L = 4096 keeps two (16-byte transposed stores)
+  static constexpr int B = (L >= 8192) ? 1 : (L >= 4096 ? 2 : 4096 / L);
   static constexpr int NT = (B * L) / 16;     // threads: 16 points each
   static constexpr int LP = spad_len(L) + 1;  // odd stride between sequences
   static constexpr size_t SMEM = size_t(B) * LP * sizeof(float2);
@@ -50,16 +51,20 @@ __device__ __forceinline__ void fft_stages(float2* s, const float2* __restrict__
       const int k = j & (NS - 1);
       const float2* src = s + b * LP;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float2 x = src[spad(j + r * LR)];
-        if constexpr (ST > 0) {
-          if (r > 0) {
-            float2 w = __ldg(&tw[r * k * TSTEP]);
-            if (DIR > 0) w.y = -w.y;
-            x = cmul(x, w);
-          }
+      for (int r = 0; r < R; ++r) v[q][r] = src[spad(j + r * LR)];
+      if constexpr (ST > 0) {
+        // w^r for r < R from the table entries w^1, w^2, w^4, w^8 (w = exp(dir 2 pi i k / (NS R)))
+        // and at most two further products per factor: a few ulp, log2(R) loads per butterfly
+        constexpr int LB = stage_bits(LOG2L, ST);
+        float2 pw[LB];
+#pragma unroll
+        for (int e = 0; e < LB; ++e) {
+          float2 w = __ldg(&tw[(k * TSTEP) << e]);
+          if (DIR > 0) w.y = -w.y;
+          pw[e] = w;
         }
-        v[q][r] = x;
+        float2 wr[R];
+        twiddle_rec<R, 1>(v[q], pw, wr);
       }
       dft_r<R, DIR>(v[q]);
     }
