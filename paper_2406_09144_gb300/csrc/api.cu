@@ -321,7 +321,12 @@ static PlaneArgs plane_args(const Geometry& geo, const VisLayout& lay, int g, in
   a.corr = geo.corr;
   a.tq = geo.tq;
   a.wterm = geo.wterm ? 1 : 0;
-  a.k64 = geo.wterm ? plane_k64(geo, plane_w(geo, lay, g, p)) : 0;
+  a.taylor = geo.taylor ? 1 : 0;
+  a.n = p;
+  double f = 1.0;
+  for (int k = 2; k <= p; ++k) f *= k;
+  a.inv_fact = (float)(1.0 / f);
+  a.k64 = (geo.wterm && !geo.taylor) ? plane_k64(geo, plane_w(geo, lay, g, p)) : 0;
   a.bu0 = lay.bu0;
   a.bu1 = lay.bu1;
   a.bv0 = lay.bv0;
@@ -338,7 +343,7 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
   for (int g = 0; g < lay.ngroups; ++g) {
     const int P = geo.wterm ? lay.planes[g] : 1;
     for (int p = 0; p < P; ++p) {
-      const int q = lay.plane_base[g] + p;
+      const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
       PlaneArgs a = plane_args(geo, lay, g, p);
       FR_TRY(degrid_prepass(a, sky + g * img, w->b1, w->grid, pl->tw[ilog2(geo.Nv)],
@@ -362,7 +367,7 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
     const int P = geo.wterm ? lay.planes[g] : 1;
     bool written = false;
     for (int p = 0; p < P; ++p) {
-      const int q = lay.plane_base[g] + p;
+      const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
       FR_TRY(grid_plane(geo, lay, g, p, ybuf, grid, s));
       PlaneArgs a = plane_args(geo, lay, g, p);
@@ -567,6 +572,24 @@ static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int
       const double lo = wabs_min * flo / CL, hi = wabs_max * fhi / CL;
       w_lo[k] = lo;
       planes[k] = (int)std::floor((hi - lo) / g.dw) + 1 + g.kern.W;
+    }
+    // Small w-phase: the expansion exp(-i a tau) = sum_n (-i a tau)^n / n!, |tau| <= 1,
+    // a = 2 pi w t_half, truncated after N + 1 terms has remainder <= x^(N+1) / (N+1)! with
+    // x = max |a|. Use it when it needs fewer "planes" than w-stacking, keeping the remainder
+    // far below eps.
+    const double x = 2.0 * M_PI * (wabs_max * fmax / CL) * g.t_half;
+    double term = x, fact = 1.0;
+    int n_terms = 1;
+    while (n_terms < 12 && term / fact > 1e-2 * eps) {
+      ++n_terms;
+      term *= x;
+      fact *= n_terms;
+    }
+    const int pmin = *std::min_element(planes.begin(), planes.end());
+    if (n_terms < pmin) {
+      g.taylor = true;
+      g.nterms = n_terms;
+      for (int k = 0; k < p->nsky; ++k) planes[k] = n_terms;
     }
   }
   for (int L : {g.Nu, g.Nv}) FR_TRY(ensure_twiddles(p, ilog2(L), s));
@@ -915,7 +938,7 @@ int fr_plan_get_info(fr_plan_t p, fr_plan_info* info) {
   }
   info->wplanes_total = tot;
   info->wplanes_max = mx;
-  info->dw = p->geo.wterm ? p->geo.dw : 0.0;
+  info->dw = (p->geo.wterm && !p->geo.taylor) ? p->geo.dw : 0.0;  // 0: no w-term or expansion
   info->nvis_dropped = p->lay.ndropped;
   info->work_items = p->lay.nitems;
   info->flags = p->flags;

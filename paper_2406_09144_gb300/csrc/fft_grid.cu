@@ -30,6 +30,14 @@ __device__ __forceinline__ void plane_phase(int32_t tq, long long k64, float* c,
   sincospif(2.f * f, s, c);
 }
 
+// tau^n / n! for the small-w expansion, tau = tq * 2^-30 = (t - t_c) / t_half
+__device__ __forceinline__ float taylor_factor(int32_t tq, int n, float inv_fact) {
+  const float tau = (float)tq * 9.313225746154785e-10f;
+  float p = inv_fact;
+  for (int i = 0; i < n; ++i) p *= tau;
+  return p;
+}
+
 struct D1Op : OpBase {
   static constexpr bool TRANSPOSED = true;
   const float* sky;
@@ -37,6 +45,8 @@ struct D1Op : OpBase {
   const int32_t* tq;
   long long k64;
   int wterm;
+  int taylor, n;
+  float inv_fact;
   float2* b1t;  // [band v][nx]
   int nx, ny, Nv;
   int vb0, nvb;  // occupied band of v: only these outputs are stored
@@ -54,6 +64,7 @@ struct D1Op : OpBase {
     const int pix = jx * ny + jy;
     const float val = __ldg(&sky[pix]) * __ldg(&corr[pix]);
     if (!wterm) return make_float2(val, 0.f);
+    if (taylor) return make_float2(val * taylor_factor(__ldg(&tq[pix]), n, inv_fact), 0.f);
     float c, s;
     plane_phase(__ldg(&tq[pix]), k64, &c, &s);
     return make_float2(val * c, -val * s);
@@ -124,6 +135,8 @@ struct G2Op : OpBase {
   const int32_t* tq;
   long long k64;
   int wterm, accumulate;
+  int taylor, n;
+  float inv_fact;
   int nx, ny, Nv;
   __host__ __device__ int nseq() const { return nx; }
   __host__ __device__ int nout() const { return ny; }
@@ -133,7 +146,9 @@ struct G2Op : OpBase {
     const float2 z = s[i];
     const int pix = jx * ny + jy;
     float val;
-    if (wterm) {
+    if (wterm && taylor) {
+      val = z.x * taylor_factor(__ldg(&tq[pix]), n, inv_fact);
+    } else if (wterm) {
       float c, sn;
       plane_phase(__ldg(&tq[pix]), k64, &c, &sn);
       val = z.x * c - z.y * sn;  // Re(z exp(+2 pi i w_p (t - t_c)))
@@ -173,6 +188,9 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
   o1.tq = a.tq;
   o1.k64 = a.k64;
   o1.wterm = a.wterm;
+  o1.taylor = a.taylor;
+  o1.n = a.n;
+  o1.inv_fact = a.inv_fact;
   o1.b1t = b1;
   o1.nx = a.nx;
   o1.ny = a.ny;
@@ -225,6 +243,9 @@ int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, in
   o2.tq = a.tq;
   o2.k64 = a.k64;
   o2.wterm = a.wterm;
+  o2.taylor = a.taylor;
+  o2.n = a.n;
+  o2.inv_fact = a.inv_fact;
   o2.accumulate = accumulate;
   o2.nx = a.nx;
   o2.ny = a.ny;

@@ -112,6 +112,11 @@ struct Geometry {
   bool wterm = false, nterm = false;
   double t_min = 0, t_c = 0, t_half = 0;  // w-stacking image-side extent
   double dw = 0;                           // plane spacing (wavelengths)
+  // Small w-phase: exp(-2 pi i w (t - t_c)) = sum_n (-i a)^n tau^n / n!, a = 2 pi w t_half,
+  // tau = (t - t_c) / t_half in [-1, 1], truncated after `nterms` terms; each term is one
+  // "plane" with the real image multiplier tau^n / n! and the visibility weight (-i a)^n.
+  bool taylor = false;
+  int nterms = 0;
   float* corr = nullptr;                   // [nx*ny] (-1)^(px+py) / (n Phi_u Phi_v Phi_w)
   int32_t* tq = nullptr;                   // [nx*ny] (t - t_c) / t_half * 2^30  (wterm)
   cudaStream_t async = nullptr;            // tables are stream-ordered transients when set
@@ -202,6 +207,9 @@ struct PlaneArgs {
   const int32_t* tq;
   long long k64;  // per-plane phase multiplier, Q64 cycles per tq unit (0 without w)
   int wterm;
+  int taylor;      // 1: term n of the small-w expansion instead of a w-plane phase
+  int n;           // term index
+  float inv_fact;  // 1 / n!
 };
 int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
                    const float2* twv, const float2* twu, cudaStream_t s);

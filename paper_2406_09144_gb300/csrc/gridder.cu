@@ -120,6 +120,8 @@ struct PrepArgs {
   int Nu, Nv, W;
   double dl, dm;
   int wterm;
+  int taylor;            // small-w expansion: every visibility in every term, dw_out = a
+  double a_scale;        // 2 pi t_half (a = a_scale * w)
   double t_c, dw;
   const double* w_lo;    // [ngroups]
   const int* planes;     // [ngroups]
@@ -166,7 +168,9 @@ __global__ void vis_prepare(PrepArgs a) {
     }
     int pf = 0;
     double dwv = 0.0;
-    if (ok && a.wterm) {
+    if (ok && a.wterm && a.taylor) {
+      dwv = a.a_scale * w;
+    } else if (ok && a.wterm) {
       const double y = (w - a.w_lo[g]) / a.dw + hw;
       pf = (int)ceil(y - hw);
       if (pf < 0) pf = 0;
@@ -183,7 +187,7 @@ __global__ void vis_prepare(PrepArgs a) {
     }
     const int ju = (int)iu0, jv = (int)iv0;
     const int tu = ju / TILE, tv = jv / TILE;
-    const int P = a.wterm ? a.planes[g] : 1;
+    const int P = (a.wterm && !a.taylor) ? a.planes[g] : 1;
     const int tb = (int)min((int64_t)a.ntb - 1, row / a.rows_per_tb);
     a.key[k] = a.keybase[g] + ((tu * a.ntv + tv) * P + pf) * a.ntb + tb;
     a.cell[k] = ((uint32_t)ju << 18) | ((uint32_t)jv << 4) | (uint32_t)(pf & 15);
@@ -435,12 +439,15 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   lay->nvis = M;
   const int ntiles = lay->ntu * lay->ntv;
   const bool wterm = geo.wterm;
+  // w-stacking splits visibilities by first w-plane; the small-w expansion puts every
+  // visibility in every term, so its layout has one plane dimension like the w = 0 case
+  const bool stack = geo.wterm && !geo.taylor;
 
   // keys: (group, tile, first plane, row block). Row blocks keep each bucket to a narrow range
   // of rows, i.e. of times for time-ordered data, so a work item holds consecutive samples of
   // the baselines crossing its tile, which stay in one grid cell for many samples.
   int64_t kbase = 0;
-  for (int g = 0; g < ngroups; ++g) kbase += (int64_t)ntiles * (wterm ? planes[g] : 1);
+  for (int g = 0; g < ngroups; ++g) kbase += (int64_t)ntiles * (stack ? planes[g] : 1);
   const int ntb = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(nrow, 4096),
                                                               (int64_t(1) << 26) / std::max<int64_t>(kbase, 1)));
   const int64_t rows_per_tb = (nrow + ntb - 1) / ntb;
@@ -449,7 +456,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   std::vector<int64_t> ebase(ngroups + 1);
   int64_t E = 0;
   for (int g = 0; g < ngroups; ++g) {
-    const int P = wterm ? planes[g] : 1;
+    const int P = stack ? planes[g] : 1;
     keybase[g] = (int)K;
     K += (int64_t)ntiles * P * ntb;
     ebase[g] = E;
@@ -486,7 +493,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
     FR_TRY(t.alloc(&ph_u, M));
   }
   std::vector<int> pl(ngroups);
-  for (int g = 0; g < ngroups; ++g) pl[g] = wterm ? planes[g] : 1;
+  for (int g = 0; g < ngroups; ++g) pl[g] = stack ? planes[g] : 1;
   FR_CUDA_TRY(cudaMemcpyAsync(d_keybase, keybase.data(), ngroups * sizeof(int), cudaMemcpyHostToDevice, s));
   FR_CUDA_TRY(cudaMemcpyAsync(d_planes, pl.data(), ngroups * sizeof(int), cudaMemcpyHostToDevice, s));
   FR_CUDA_TRY(cudaMemcpyAsync(d_wlo, w_lo.data(), ngroups * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -508,6 +515,8 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   pa.dl = geo.dl;
   pa.dm = geo.dm;
   pa.wterm = wterm;
+  pa.taylor = geo.taylor ? 1 : 0;
+  pa.a_scale = 2.0 * M_PI * geo.t_half;
   pa.t_c = geo.t_c;
   pa.dw = geo.dw;
   pa.w_lo = d_wlo;
@@ -607,7 +616,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   ia.ntv = lay->ntv;
   ia.ntb = ntb;
   ia.W = geo.kern.W;
-  ia.wterm = wterm;
+  ia.wterm = stack;
   ia.chunks = d_chunks;
   ia.item_off = d_item_off;
   ia.items = nullptr;
@@ -686,7 +695,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
 struct TableArgs {
   int nx, ny;
   double dl, dm;
-  int wterm, nterm;
+  int wterm, nterm, taylor;
   double t_c, t_half, dw;
   const double* inv_phi_u;  // [nx] 1 / Phi_u(px / Nu)
   const double* inv_phi_v;  // [ny]
@@ -718,15 +727,18 @@ __global__ void make_tables_kernel(TableArgs a) {
       const double t = -r2 / (1.0 + nn);  // n - 1 without cancellation
       const double tp = t - a.t_c;
       a.tq[pix] = (int32_t)llrint(tp / a.t_half * 1073741824.0);
-      // Phi_w(dw * tp) = (W/2) int_{-1}^{1} exp(beta (sqrt(1 - z^2) - 1)) cos(pi k W z) dz
-      const double k = a.dw * tp;
-      double phi = 0.0;
-      for (int q = 0; q < a.nq; ++q) {
-        const double z = a.gl_x[q];
-        phi += a.gl_w[q] * exp(a.beta * (sqrt(1.0 - z * z) - 1.0)) * cos(M_PI * k * 2.0 * a.hw * z);
+      if (!a.taylor) {
+        // Phi_w(dw * tp) = (W/2) int_{-1}^{1} exp(beta (sqrt(1 - z^2) - 1)) cos(pi k W z) dz
+        const double k = a.dw * tp;
+        double phi = 0.0;
+        for (int q = 0; q < a.nq; ++q) {
+          const double z = a.gl_x[q];
+          phi += a.gl_w[q] * exp(a.beta * (sqrt(1.0 - z * z) - 1.0)) *
+                 cos(M_PI * k * 2.0 * a.hw * z);
+        }
+        phi *= a.hw;
+        c /= phi;
       }
-      phi *= a.hw;
-      c /= phi;
     }
     if ((px + py) & 1) c = -c;
     a.corr[pix] = (float)c;
@@ -802,6 +814,7 @@ int make_tables(Geometry* geo, const std::vector<double>& inv_phi_u,
   a.dl = geo->dl;
   a.dm = geo->dm;
   a.wterm = geo->wterm;
+  a.taylor = geo->taylor ? 1 : 0;
   a.nterm = geo->nterm;
   a.t_c = geo->t_c;
   a.t_half = geo->t_half;
@@ -911,10 +924,24 @@ __device__ __forceinline__ void kernel_weights(const EsKernel& k, float d, float
   for (int a = 0; a < W; ++a) out[a] = es_eval(k, d - (float)a);
 }
 
+// z * (s i a)^n for s = -1 (degridding) or +1 (its adjoint), |a| << 1, small n
+__device__ __forceinline__ float2 rot_pow(float2 z, int n, float a, int s) {
+  float an = 1.f;
+  for (int k = 0; k < n; ++k) an *= a;
+  z.x *= an;
+  z.y *= an;
+  switch ((s > 0 ? n : 4 - (n & 3)) & 3) {  // multiply by i^q
+    case 1: return make_float2(-z.y, z.x);
+    case 2: return make_float2(-z.x, -z.y);
+    case 3: return make_float2(z.y, -z.x);
+    default: return z;
+  }
+}
+
 template <int W>
 __global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUtensorMap tmap,
                                                      const int4* __restrict__ items, MetaPtrs m,
-                                                     EsKernel kern, int p, int wterm,
+                                                     EsKernel kern, int p, int wmode, int last,
                                                      float2* __restrict__ vacc,
                                                      float2* __restrict__ vis_out, int* status) {
   constexpr int BU = TILE + W - 1;
@@ -967,19 +994,22 @@ __global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUt
       acc.y = fmaf(kv[b], ra.y, acc.y);
     }
     int rel = 0;
-    if (wterm) {
+    if (wmode == 1) {  // w-stacking: kernel weight of this plane
       rel = (p - (int)(cell & 15)) & 15;
       const float kw = es_eval(kern, m.dw[i] - (float)rel);
       acc.x *= kw;
       acc.y *= kw;
-      if (rel > 0) {
-        const float2 prev = vacc[i];
-        acc.x += prev.x;
-        acc.y += prev.y;
-      }
+    } else if (wmode == 2) {  // small-w expansion: term p carries (-i a)^p
+      rel = p;
+      acc = rot_pow(acc, p, m.dw[i], -1);
     }
-    if (!wterm || rel == W - 1) {
-      if (wterm) {
+    if (wmode && rel > 0) {
+      const float2 prev = vacc[i];
+      acc.x += prev.x;
+      acc.y += prev.y;
+    }
+    if (!wmode || rel == last) {
+      if (wmode) {
         // exp(-2 pi i w t_c)
         const float f = (float)(int)m.ph[i] * 2.3283064365386963e-10f;
         float s, c;
@@ -1016,7 +1046,7 @@ constexpr size_t grid_smem_bytes() {
 template <int W>
 __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __restrict__ items,
                                                                MetaPtrs m, EsKernel kern, int p,
-                                                               int wterm,
+                                                               int wmode,
                                                                const float2* __restrict__ y,
                                                                float2* __restrict__ grid, int Nu,
                                                                int Nv) {
@@ -1112,11 +1142,13 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
       const uint32_t cell = m.cell[i];
       const float du = m.du[i], dv = m.dv[i];
       float2 val = y[i];
-      if (wterm) {
+      if (wmode == 1) {  // w-stacking: kernel weight of this plane
         const int rel = (p - (int)(cell & 15)) & 15;
         const float kw = es_eval(kern, m.dw[i] - (float)rel);
         val.x *= kw;
         val.y *= kw;
+      } else if (wmode == 2) {  // small-w expansion: adjoint weight (i a)^p
+        val = rot_pow(val, p, m.dw[i], 1);
       }
       org = ((int)((cell >> 4) & 0x3fff) - tv * TILE) * BV + (int)(cell >> 18) - tu * TILE;
 #pragma unroll
@@ -1255,13 +1287,17 @@ int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, i
       return FR_EUNSUPPORTED;                              \
   }
 
+// 0: no w-term; 1: w-stacking; 2: small-w expansion
+static int wmode_of(const Geometry& geo) { return !geo.wterm ? 0 : (geo.taylor ? 2 : 1); }
+
 template <int W>
 static int launch_degrid(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n, int p,
                          const CUtensorMap& tmap, float2* vacc, float2* vis_out, int* status,
                          cudaStream_t s) {
   MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
-  degrid_kernel<W><<<(unsigned)n, 256, 0, s>>>(tmap, lay.items + i0, m, geo.kern, p,
-                                               geo.wterm ? 1 : 0, vacc, vis_out, status);
+  degrid_kernel<W><<<(unsigned)n, 256, 0, s>>>(tmap, lay.items + i0, m, geo.kern, p, wmode_of(geo),
+                                               geo.taylor ? geo.nterms - 1 : W - 1, vacc, vis_out,
+                                               status);
   FR_LAUNCHED();
   return FR_OK;
 }
@@ -1278,8 +1314,7 @@ static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, in
     attr = true;
   }
   grid_kernel<W><<<(unsigned)n, GRID_WARPS * 32, smem, s>>>(lay.items + i0, m, geo.kern, p,
-                                                            geo.wterm ? 1 : 0, y, grid, geo.Nu,
-                                                            geo.Nv);
+                                                            wmode_of(geo), y, grid, geo.Nu, geo.Nv);
   FR_LAUNCHED();
   return FR_OK;
 }
@@ -1287,25 +1322,29 @@ static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, in
 // algorithmic bytes per visibility visit: cell, du, dv (, dw) in; accumulator / output traffic
 static double meta_bytes(const Geometry& geo) { return 12.0 + (geo.wterm ? 4.0 : 0.0); }
 
+static double band_cells(const VisLayout& lay) {
+  return (double)std::max(0, lay.bu1 - lay.bu0 + 1) * std::max(0, lay.bv1 - lay.bv0 + 1);
+}
+
 int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const CUtensorMap& tmap,
                  float2* vacc, float2* vis_out, int* status, cudaStream_t s) {
-  const int q = lay.plane_base[g] + p;
+  const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);  // expansion terms share one layout
   const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
   if (i1 <= i0) return FR_OK;
-  // each grid cell read once, per visit: metadata + accumulator read/write (or output + perm)
+  // each band cell read once, per visit: metadata + accumulator read/write (or output + perm)
   ProfScope ps(PC_DEGRID, s,
-               (double)geo.Nu * geo.Nv * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 16.0));
+               band_cells(lay) * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 16.0));
   FR_W_DISPATCH(geo.kern.W, launch_degrid, geo, lay, i0, i1 - i0, p, tmap, vacc, vis_out, status, s);
 }
 
 int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const float2* ysorted,
                float2* grid, cudaStream_t s) {
-  const int q = lay.plane_base[g] + p;
+  const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);  // expansion terms share one layout
   const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
   if (i1 <= i0) return FR_OK;
-  // each grid cell written once, per visit: metadata + weighted visibility
+  // each band cell written once, per visit: metadata + weighted visibility
   ProfScope ps(PC_GRID, s,
-               (double)geo.Nu * geo.Nv * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 8.0));
+               band_cells(lay) * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 8.0));
   FR_W_DISPATCH(geo.kern.W, launch_grid, geo, lay, i0, i1 - i0, p, ysorted, grid, s);
 }
 

@@ -83,6 +83,28 @@ def test_grid_matches_oracle(case):
     assert rel(got1, ref1) <= EPS
 
 
+@pytest.mark.parametrize("wc,nchan,per", [(0.003, 1, False), (0.02, 2, True), (0.05, 3, False)])
+def test_small_w_expansion_matches_oracle(wc, nchan, per):
+    """A w-phase far below one turn takes the truncated expansion in w instead of w-stacking;
+    R, R^dagger and a point source's closed form must still match the oracle."""
+    obs = synth.random_observation(1400, nchan, 64, 32, 2e-3, seed=44, wmax_cycles=wc,
+                                   per_channel_sky=per)
+    plan = make_plan(obs, mfs=not per)
+    info = plan.info()
+    assert info["dw"] == 0.0 and info["wplanes_max"] < info["support"] + 1
+    sky = synth.random_skies(obs.nsky, 64, 32, seed=12)
+    ref = oracle.degrid(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize)
+    assert rel(plan.degrid(dev(sky)).cpu().numpy(), ref) <= EPS
+    vis = synth.complex_gaussian(plan.vis_shape, seed=13)
+    refd = oracle.grid(vis, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, 64, 32,
+                       weights=obs.weights.astype(np.float32), nsky=obs.nsky)
+    assert rel(plan.grid(dev(vis, torch.complex64)).cpu().numpy(), refd) <= EPS
+    pt = np.zeros((obs.nsky, 64, 32))
+    pt[:, 3, 29] = 1.0
+    refp = oracle.degrid(pt, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize)
+    assert rel(plan.degrid(dev(pt)).cpu().numpy(), refp) <= EPS
+
+
 def test_grid_twice_is_identical_workspace_stays_clean():
     obs = synth.random_observation(900, 1, 32, 32, 2e-3, seed=33, wmax_cycles=2.0)
     plan = make_plan(obs)
