@@ -586,7 +586,8 @@ static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int
       fact *= n_terms;
     }
     const int pmin = *std::min_element(planes.begin(), planes.end());
-    if (n_terms < pmin) {
+    const bool converged = term / fact <= 1e-2 * eps;  // the 12-term cap alone is not enough
+    if (converged && n_terms < pmin) {
       g.taylor = true;
       g.nterms = n_terms;
       for (int k = 0; k < p->nsky; ++k) planes[k] = n_terms;
