@@ -226,6 +226,8 @@ static void free_ws(Workspace* w) {
   cudaFree(w->b1);
   cudaFree(w->b1g);
   cudaFree(w->grid);
+  cudaFree(w->grid_terms);
+  cudaFree(w->grid_terms_g);
   cudaFree(w->vbuf);
   cudaFree(w->h);
   cudaFree(w->tmp_img);
@@ -284,6 +286,41 @@ static int get_ws(fr_plan* p, cudaStream_t s, Workspace** out) {
   return FR_OK;
 }
 
+// resident term grids for the one-pass expansion degridder (allocated on first use); zeroed once
+// so that tile cells outside the band, which no footprint reads, hold finite values
+static int ws_reserve_terms(const Geometry& g, Workspace* w, cudaStream_t s) {
+  if (w->grid_terms) return FR_OK;
+  const size_t n = (size_t)g.nterms * g.Nu * g.Nv;
+  FR_TRY(ws_alloc(&w->grid_terms, n, w));
+  FR_CUDA_TRY(cudaMemsetAsync(w->grid_terms, 0, n * sizeof(float2), s));
+  int r = make_tmap(&w->tmap_terms, w->grid_terms, g.Nu, g.nterms * g.Nv, g.kern.W);
+  if (r) {
+    cudaFree(w->grid_terms);
+    w->bytes -= n * sizeof(float2);
+    w->grid_terms = nullptr;
+  }
+  return r;
+}
+
+static int ws_reserve_terms_g(const Geometry& g, Workspace* w, cudaStream_t s) {
+  const size_t n = (size_t)g.nterms * g.Nu * g.Nv;
+  if (!w->grid_terms_g) {
+    FR_TRY(ws_alloc(&w->grid_terms_g, n, w));
+    w->terms_g_zero = false;
+  }
+  if (!w->terms_g_zero) {
+    FR_CUDA_TRY(cudaMemsetAsync(w->grid_terms_g, 0, n * sizeof(float2), s));
+    w->terms_g_zero = true;
+  }
+  return FR_OK;
+}
+
+// the small-w expansion keeps all its term grids resident when they fit
+static bool use_term_grids(const Geometry& g) {
+  return g.wterm && g.taylor && degrid_terms_fits(g) &&
+         (size_t)g.nterms * g.Nu * g.Nv * sizeof(float2) <= TERM_GRIDS_MAX_BYTES;
+}
+
 static int ws_reserve_h(Workspace* w, size_t n) {
   if (w->h_bytes >= n * sizeof(float2)) return FR_OK;
   cudaFree(w->h);
@@ -340,8 +377,22 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
   if (lay.ndropped > 0)
     FR_CUDA_TRY(cudaMemsetAsync(vis, 0, (size_t)lay.nvis * sizeof(float2), s));
   const size_t img = (size_t)geo.nx * geo.ny;
+  // small-w expansion: every term grid built first, then one interpolation pass reads them all
+  const bool terms = use_term_grids(geo);
+  if (terms) FR_TRY(ws_reserve_terms(geo, w, s));
   for (int g = 0; g < lay.ngroups; ++g) {
     const int P = geo.wterm ? lay.planes[g] : 1;
+    if (terms) {
+      const int q = lay.plane_base[g];
+      if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
+      for (int p = 0; p < P; ++p) {
+        PlaneArgs a = plane_args(geo, lay, g, p);
+        FR_TRY(degrid_prepass(a, sky + g * img, w->b1, w->grid_terms + (size_t)p * geo.Nu * geo.Nv,
+                              pl->tw[ilog2(geo.Nv)], pl->tw[ilog2(geo.Nu)], s));
+      }
+      FR_TRY(degrid_terms(geo, lay, g, w->tmap_terms, vis, pl->status, s));
+      continue;
+    }
     for (int p = 0; p < P; ++p) {
       const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
@@ -360,9 +411,31 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
                     const float2* vis, int apply_weights, float* dirty, float2* grid, float2* b1,
                     float2* ybuf, cudaStream_t s, bool* grid_zero) {
   FR_TRY(grid_prepare(geo, lay, vis, apply_weights, ybuf, s));
+  const size_t img = (size_t)geo.nx * geo.ny;
+  if (w && use_term_grids(geo)) {
+    // small-w expansion: one spreading pass fills every term grid, then each term is transformed
+    // and accumulated into the image with its own pixel factor
+    FR_TRY(ws_reserve_terms_g(geo, w, s));
+    const size_t plane = (size_t)geo.Nu * geo.Nv;
+    for (int g = 0; g < lay.ngroups; ++g) {
+      const int q = lay.plane_base[g];
+      if (lay.plane_items[q + 1] <= lay.plane_items[q]) {
+        FR_CUDA_TRY(cudaMemsetAsync(dirty + g * img, 0, img * sizeof(float), s));
+        continue;
+      }
+      w->terms_g_zero = false;
+      FR_TRY(grid_terms(geo, lay, g, ybuf, w->grid_terms_g, s));
+      for (int p = 0; p < geo.nterms; ++p) {
+        PlaneArgs a = plane_args(geo, lay, g, p);
+        FR_TRY(grid_postpass(a, w->grid_terms_g + p * plane, b1, dirty + g * img, p ? 1 : 0,
+                             pl->tw[ilog2(geo.Nu)], pl->tw[ilog2(geo.Nv)], s));
+      }
+      w->terms_g_zero = true;  // the post-pass zeroes the band it reads
+    }
+    return FR_OK;
+  }
   if (!*grid_zero) FR_CUDA_TRY(cudaMemsetAsync(grid, 0, (size_t)geo.Nu * geo.Nv * sizeof(float2), s));
   *grid_zero = true;
-  const size_t img = (size_t)geo.nx * geo.ny;
   for (int g = 0; g < lay.ngroups; ++g) {
     const int P = geo.wterm ? lay.planes[g] : 1;
     bool written = false;
@@ -377,7 +450,6 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
     }
     if (!written) FR_CUDA_TRY(cudaMemsetAsync(dirty + g * img, 0, img * sizeof(float), s));
   }
-  (void)w;
   return FR_OK;
 }
 
@@ -958,8 +1030,10 @@ int fr_plan_footprint(fr_plan_t p, size_t* resident_bytes, size_t* workspace_byt
     for (Workspace* w : p->ws) m = std::max(m, w->bytes);
     if (p->ws.empty()) {
       const Geometry& g = p->geo;
-      m = ((size_t)g.nx * g.Nv + (size_t)g.Nu * g.Nv + (size_t)std::max<int64_t>(p->lay.nsorted, 1)) *
+      m = (2 * (size_t)g.nx * g.Nv + (size_t)g.Nu * g.Nv +
+           (size_t)std::max<int64_t>(p->lay.nsorted, 1)) *
           sizeof(float2);
+      if (use_term_grids(g)) m += 2 * (size_t)g.nterms * g.Nu * g.Nv * sizeof(float2);
     }
     *workspace_bytes = m;
   }

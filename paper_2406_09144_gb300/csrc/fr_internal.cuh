@@ -97,6 +97,8 @@ __device__ __forceinline__ float es_eval_fast(const EsKernel& k, float x) {
 constexpr int TILE = 32;       // grid cells per tile side (u and v)
 constexpr int MAXW = 16;       // largest kernel support
 constexpr int GRID_CHUNK = 512;  // visibilities per (tile, plane) work item at most
+constexpr int DEGRID_TERMS_SMEM = 200 * 1024;  // shared tiles of all expansion terms at most
+constexpr size_t TERM_GRIDS_MAX_BYTES = (size_t)4 << 30;  // resident expansion term grids at most
 
 // Padded tile box: rows BU = TILE + W - 1, columns BV = BU rounded up to even (16-byte rows).
 __host__ __device__ inline int box_u(int W) { return TILE + W - 1; }
@@ -168,6 +170,10 @@ struct Workspace {
   size_t red_n = 0;
   CUtensorMap tmap;          // TMA descriptor of `grid`
   bool tmap_ok = false;
+  float2* grid_terms = nullptr;  // [nterms][Nv][Nu] term grids of the small-w expansion
+  CUtensorMap tmap_terms;        // TMA descriptor of `grid_terms` (rows nterms * Nv)
+  float2* grid_terms_g = nullptr;  // [nterms][Nv][Nu] gridding term grids (kept zero)
+  bool terms_g_zero = false;
   size_t bytes = 0;
 };
 
@@ -245,6 +251,12 @@ int make_tmap(CUtensorMap* m, float2* grid, int Nu, int Nv, int W);
 int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p,
                  const CUtensorMap& tmap, float2* vacc, float2* vis_out, int* status,
                  cudaStream_t s);
+// small-w expansion: all nterms term grids stacked [nterms][Nv][Nu] behind one tensor map
+bool degrid_terms_fits(const Geometry& geo);
+int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtensorMap& tmap,
+                 float2* vis_out, int* status, cudaStream_t s);
+int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* ysorted,
+               float2* grid_terms, cudaStream_t s);
 int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const float2* ysorted,
                float2* grid, cudaStream_t s);
 int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, int apply_weights,

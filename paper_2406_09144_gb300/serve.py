@@ -70,7 +70,8 @@ def estimate_bytes(req: Request) -> int:
     n = req.nx * req.ny
     m = req.nvis
     plan = m * 28 + n * 8 + req.nsky * (4 * n * 4 + 2 * n * 4)     # sorted vis, tables, PSF, T
-    work = n * 4 * 8 + n * 2 * 8 + m * 8                           # grid, half plane, vis buffer
+    work = n * 4 * 8 + n * 4 * 8 + m * 8                           # grid, half planes, vis buffer
+    work += 2 * 4 * n * 4 * 8                                      # small-w expansion term grids
     build = 16 * n * 8 + 8 * n * 8 + m * 32                        # PSF-build grid and sort temps
     io = req.sky.size * 4 * 2 + (m * 8 * 2 if req.kind == "major" else 0)
     if req.kind == "psf":
