@@ -149,6 +149,7 @@ struct VisLayout {
   uint32_t* perm = nullptr;  // user index (row * nchan + chan) | conj flag << 31
   float* wgt = nullptr;
   int4* items = nullptr;     // {vis_begin, vis_count, tu << 16 | tv, 0}
+  bool presorted = false;    // each item's visibilities ordered by footprint origin
   int64_t nitems = 0;
   size_t bytes = 0;
   cudaStream_t async = nullptr;  // arrays are stream-ordered transients when set

@@ -425,6 +425,8 @@ struct Temps {
 };
 }  // namespace
 
+static int presort_items(VisLayout* lay, int64_t N, bool wterm, cudaStream_t s);
+
 int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const double* h_freqs,
                  const double* d_freqs, int nchan, const float* d_weights, int ngroups,
                  const std::vector<double>& w_lo, const std::vector<int>& planes, bool drop_oob,
@@ -649,6 +651,14 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   if (lay->nitems > 0) {
     emit_items<<<grid1d(E), 256, 0, s>>>(ia, E);
     FR_LAUNCHED();
+  }
+  // Without w-stacking every work item is a fixed chunk of one tile's range, so each chunk can be
+  // ordered by footprint origin once here instead of in every gridding call. (With w-stacking the
+  // item ranges of neighbouring planes overlap with different chunk boundaries.)
+  lay->presorted = false;
+  if (!stack && lay->nitems > 0) {
+    FR_TRY(presort_items(lay, N, wterm, s));
+    lay->presorted = true;
   }
   // visibility visits per (group, plane), for launch accounting
   // occupied band of the grid: the union of all kernel footprints
@@ -1176,6 +1186,68 @@ __device__ __forceinline__ void sort_by_origin(const MetaPtrs& m, const int4 it,
   __syncthreads();
 }
 
+struct SortArrays {
+  uint32_t* cell;
+  float* du;
+  float* dv;
+  float* dw;
+  uint32_t* ph;
+  uint32_t* perm;
+  float* wgt;
+};
+
+// orders every work item's visibilities by footprint origin: out[item start + rank] = in[...]
+__global__ void __launch_bounds__(GRID_WARPS * 32) presort_kernel(const int4* __restrict__ items,
+                                                                  SortArrays in, SortArrays out) {
+  __shared__ int hist[TILE * TILE];
+  __shared__ short order[GRID_CHUNK];
+  __shared__ int wsum[GRID_WARPS];
+  const int4 it = items[blockIdx.x];
+  MetaPtrs m{in.cell, nullptr, nullptr, nullptr, nullptr, nullptr};
+  sort_by_origin(m, it, it.z >> 16, it.z & 0xffff, hist, order, wsum);
+  for (int r = threadIdx.x; r < it.y; r += blockDim.x) {
+    const int i = it.x + order[r], o = it.x + r;
+    out.cell[o] = in.cell[i];
+    out.du[o] = in.du[i];
+    out.dv[o] = in.dv[i];
+    out.perm[o] = in.perm[i];
+    out.wgt[o] = in.wgt[i];
+    if (in.dw) {
+      out.dw[o] = in.dw[i];
+      out.ph[o] = in.ph[i];
+    }
+  }
+}
+
+static int presort_items(VisLayout* lay, int64_t N, bool wterm, cudaStream_t s) {
+  Temps t(s);
+  SortArrays in{lay->cell, lay->du, lay->dv, wterm ? lay->dw : nullptr,
+                wterm ? lay->ph : nullptr, lay->perm, lay->wgt};
+  SortArrays out{};
+  FR_TRY(t.alloc(&out.cell, N));
+  FR_TRY(t.alloc(&out.du, N));
+  FR_TRY(t.alloc(&out.dv, N));
+  FR_TRY(t.alloc(&out.perm, N));
+  FR_TRY(t.alloc(&out.wgt, N));
+  if (wterm) {
+    FR_TRY(t.alloc(&out.dw, N));
+    FR_TRY(t.alloc(&out.ph, N));
+  }
+  presort_kernel<<<(unsigned)lay->nitems, GRID_WARPS * 32, 0, s>>>(lay->items, in, out);
+  FR_LAUNCHED();
+  const size_t b = (size_t)N * 4;
+  FR_CUDA_TRY(cudaMemcpyAsync(lay->cell, out.cell, b, cudaMemcpyDeviceToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(lay->du, out.du, b, cudaMemcpyDeviceToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(lay->dv, out.dv, b, cudaMemcpyDeviceToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(lay->perm, out.perm, b, cudaMemcpyDeviceToDevice, s));
+  FR_CUDA_TRY(cudaMemcpyAsync(lay->wgt, out.wgt, b, cudaMemcpyDeviceToDevice, s));
+  if (wterm) {
+    FR_CUDA_TRY(cudaMemcpyAsync(lay->dw, out.dw, b, cudaMemcpyDeviceToDevice, s));
+    FR_CUDA_TRY(cudaMemcpyAsync(lay->ph, out.ph, b, cudaMemcpyDeviceToDevice, s));
+  }
+  return FR_OK;
+}
+
 // Within a work item the visibilities are first ordered by their footprint origin with a
 // shared-memory counting sort, so each warp walks runs of visibilities that share an origin;
 // a run is accumulated in registers and added to the warp's sub-grid once, when the origin
@@ -1183,7 +1255,7 @@ __device__ __forceinline__ void sort_by_origin(const MetaPtrs& m, const int4 it,
 template <int W>
 __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __restrict__ items,
                                                                MetaPtrs m, EsKernel kern, int p,
-                                                               int wmode,
+                                                               int wmode, bool presorted,
                                                                const float2* __restrict__ y,
                                                                float2* __restrict__ grid, int Nu,
                                                                int Nv) {
@@ -1206,7 +1278,10 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   const int seg = (((n + GRID_WARPS - 1) / GRID_WARPS) + 31) & ~31;
   const int nused = n > 0 ? (n + seg - 1) / seg : 0;
   for (int i = threadIdx.x; i < nused * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
-  sort_by_origin(m, it, tu, tv, hist, order, wsum);
+  if (presorted)
+    __syncthreads();
+  else
+    sort_by_origin(m, it, tu, tv, hist, order, wsum);
 
   float2* mysub = sub + warp * SUB;
   int off[NIT], cu[NIT], cv[NIT];
@@ -1233,7 +1308,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
     const int nb = min(32, s1 - base);
     int org = -2;
     if (lane < nb) {
-      const int i = it.x + order[base + lane];
+      const int i = it.x + (presorted ? base + lane : (int)order[base + lane]);
       const uint32_t cell = m.cell[i];
       const float du = m.du[i], dv = m.dv[i];
       float2 val = y[i];
@@ -1333,7 +1408,7 @@ constexpr size_t grid_terms_smem_bytes() {
 
 template <int W>
 __global__ void __launch_bounds__(GRID_WARPS * 32) grid_terms_kernel(
-    const int4* __restrict__ items, MetaPtrs m, EsKernel kern, int t0, int nc,
+    const int4* __restrict__ items, MetaPtrs m, EsKernel kern, int t0, int nc, bool presorted,
     const float2* __restrict__ y, float2* __restrict__ grid_terms, int Nu, int Nv) {
   constexpr int BU = TILE + W - 1;
   constexpr int BV = (TILE + W - 1 + 1) & ~1;
@@ -1351,7 +1426,10 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_terms_kernel(
   const int tu = it.z >> 16, tv = it.z & 0xffff;
   const int n = it.y;
   for (int i = threadIdx.x; i < nc * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
-  sort_by_origin(m, it, tu, tv, hist, order, wsum);
+  if (presorted)
+    __syncthreads();
+  else
+    sort_by_origin(m, it, tu, tv, hist, order, wsum);
 
   int off[NIT], cu[NIT], cv[NIT];
 #pragma unroll
@@ -1390,7 +1468,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_terms_kernel(
     const int nb = min(32, s1 - base);
     int org = -2;
     if (lane < nb) {
-      const int i = it.x + order[base + lane];
+      const int i = it.x + (presorted ? base + lane : (int)order[base + lane]);
       const uint32_t cell = m.cell[i];
       const float du = m.du[i], dv = m.dv[i];
       const float a = m.dw[i];
@@ -1549,7 +1627,8 @@ static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, in
     attr = true;
   }
   grid_kernel<W><<<(unsigned)n, GRID_WARPS * 32, smem, s>>>(lay.items + i0, m, geo.kern, p,
-                                                            wmode_of(geo), y, grid, geo.Nu, geo.Nv);
+                                                            wmode_of(geo), lay.presorted, y, grid,
+                                                            geo.Nu, geo.Nv);
   FR_LAUNCHED();
   return FR_OK;
 }
@@ -1567,7 +1646,7 @@ static int launch_grid_terms(const Geometry& geo, const VisLayout& lay, int64_t 
   }
   grid_terms_kernel<W><<<(unsigned)n, GRID_WARPS * 32, (size_t)nc * (TILE + W - 1) *
                                                            ((TILE + W) & ~1) * sizeof(float2),
-                         s>>>(lay.items + i0, m, geo.kern, t0, nc, y, grid_terms, geo.Nu, geo.Nv);
+                         s>>>(lay.items + i0, m, geo.kern, t0, nc, lay.presorted, y, grid_terms, geo.Nu, geo.Nv);
   FR_LAUNCHED();
   return FR_OK;
 }
