@@ -17,6 +17,7 @@
 #include <cstring>
 
 #include "fr_internal.cuh"
+#include "vis_common.cuh"
 
 namespace fr {
 
@@ -893,61 +894,6 @@ int make_tmap(CUtensorMap* m, float2* grid, int Nu, int Nv, int W) {
   return FR_OK;
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait: gives up after ~2^20 polls with back-off (well above a microsecond copy)
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
-  for (int it = 0; it < (1 << 20); ++it) {
-    if (mbar_try_wait(bar, phase)) return true;
-    if (it > 64) __nanosleep(256);
-  }
-  return false;
-}
-
-// ---------------------------------------------------------------------------- degrid
-struct MetaPtrs {
-  const uint32_t* cell;
-  const float* du;
-  const float* dv;
-  const float* dw;
-  const uint32_t* ph;
-  const uint32_t* perm;
-};
-
-template <int W>
-__device__ __forceinline__ void kernel_weights(const EsKernel& k, float d, float* out) {
-#pragma unroll
-  for (int a = 0; a < W; ++a) out[a] = es_eval(k, d - (float)a);
-}
-
-// z * (s i a)^n for s = -1 (degridding) or +1 (its adjoint), |a| << 1, small n
-__device__ __forceinline__ float2 rot_pow(float2 z, int n, float a, int s) {
-  float an = 1.f;
-  for (int k = 0; k < n; ++k) an *= a;
-  z.x *= an;
-  z.y *= an;
-  switch ((s > 0 ? n : 4 - (n & 3)) & 3) {  // multiply by i^q
-    case 1: return make_float2(-z.y, z.x);
-    case 2: return make_float2(-z.x, -z.y);
-    case 3: return make_float2(z.y, -z.x);
-    default: return z;
-  }
-}
-
 template <int W>
 __global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUtensorMap tmap,
                                                      const int4* __restrict__ items, MetaPtrs m,
@@ -1032,91 +978,6 @@ __global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUt
     } else {
       vacc[i] = acc;
     }
-  }
-}
-
-// float2 stride between the term tiles of degrid_terms_kernel (a multiple of 128 bytes)
-__host__ __device__ constexpr int terms_tile_stride(int W) {
-  return ((TILE + W - 1) * ((TILE + W) & ~1) + 15) & ~15;
-}
-
-// Degridder for the small-w expansion: all N term grids are resident (stacked rows [N * Nv][Nu]),
-// one CTA per work item stages the item's tile of every term with N TMA copies on one
-// mbarrier, and each thread evaluates its visibility's separable kernel once and combines the N
-// interpolations with the weights (-i a)^n before the final phase and scatter.
-template <int W>
-__global__ void __launch_bounds__(256) degrid_terms_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                           const int4* __restrict__ items,
-                                                           MetaPtrs m, EsKernel kern, int nterms,
-                                                           int Nv, float2* __restrict__ vis_out,
-                                                           int* status) {
-  constexpr int BU = TILE + W - 1;
-  constexpr int BV = (TILE + W - 1 + 1) & ~1;
-  constexpr int TS = terms_tile_stride(W);  // 128-byte aligned TMA destinations
-  extern __shared__ __align__(128) float2 tiles[];  // [nterms][TS]
-  __shared__ __align__(8) uint64_t mbar;
-  const int4 it = items[blockIdx.x];
-  const int tu = it.z >> 16, tv = it.z & 0xffff;
-  const uint32_t bar = smem_u32(&mbar);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"((uint32_t)(BU * BV * sizeof(float2)) * (uint32_t)nterms)
-                 : "memory");
-    for (int n = 0; n < nterms; ++n)
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-          "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tiles + n * TS)),
-          "l"((uint64_t)&tmap), "r"(2 * TILE * tu), "r"(n * Nv + TILE * tv), "r"(bar)
-          : "memory");
-  }
-  __syncthreads();
-  if (!mbar_wait_bounded(bar, 0)) {
-    if (threadIdx.x == 0) {
-      atomicOr(status, ST_TIMEOUT);
-      mbar_wait_bounded(bar, 0);  // let the copies in flight land before the CTA exits
-    }
-    return;
-  }
-  const int end = it.x + it.y;
-  for (int i = it.x + threadIdx.x; i < end; i += blockDim.x) {
-    const uint32_t cell = m.cell[i];
-    const int ru = (int)(cell >> 18) - tu * TILE;
-    const int rv = (int)((cell >> 4) & 0x3fff) - tv * TILE;
-    float ku[W], kv[W];
-    kernel_weights<W>(kern, m.du[i], ku);
-    kernel_weights<W>(kern, m.dv[i], kv);
-    const float a = m.dw[i];
-    float2 acc = make_float2(0.f, 0.f);
-    for (int n = 0; n < nterms; ++n) {
-      const float2* tile = tiles + n * TS;
-      float2 sn = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int b = 0; b < W; ++b) {
-        const float2* row = tile + (rv + b) * BV + ru;
-        float2 ra = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-          const float2 g = row[c];
-          ra.x = fmaf(ku[c], g.x, ra.x);
-          ra.y = fmaf(ku[c], g.y, ra.y);
-        }
-        sn.x = fmaf(kv[b], ra.x, sn.x);
-        sn.y = fmaf(kv[b], ra.y, sn.y);
-      }
-      const float2 t = rot_pow(sn, n, a, -1);
-      acc.x += t.x;
-      acc.y += t.y;
-    }
-    // exp(-2 pi i w t_c)
-    const float f = (float)(int)m.ph[i] * 2.3283064365386963e-10f;
-    float s, c;
-    sincospif(2.f * f, &s, &c);
-    acc = make_float2(acc.x * c + acc.y * s, acc.y * c - acc.x * s);
-    const uint32_t pm = m.perm[i];
-    if (pm >> 31) acc.y = -acc.y;
-    vis_out[pm & 0x7fffffffu] = acc;
   }
 }
 
@@ -1393,149 +1254,6 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   }
 }
 
-// Gridder for the small-w expansion: one pass spreads every visibility into up to
-// TERMS_PER_PASS term grids at once (terms t0 .. t0 + nc - 1, weights (i a)^n), so the sort, the
-// kernel weights and the run bookkeeping are shared by all terms. The terms' sub-grids are shared
-// by the CTA's warps and a run is added to them with shared float atomics; runs are long (a
-// baseline track crosses a cell in tens of integrations), so the atomics are rare next to the
-// per-visibility multiply-adds.
-constexpr int TERMS_PER_PASS = 4;
-
-template <int W>
-constexpr size_t grid_terms_smem_bytes() {
-  return (size_t)TERMS_PER_PASS * (TILE + W - 1) * ((TILE + W) & ~1) * sizeof(float2);
-}
-
-template <int W>
-__global__ void __launch_bounds__(GRID_WARPS * 32) grid_terms_kernel(
-    const int4* __restrict__ items, MetaPtrs m, EsKernel kern, int t0, int nc, bool presorted,
-    const float2* __restrict__ y, float2* __restrict__ grid_terms, int Nu, int Nv) {
-  constexpr int BU = TILE + W - 1;
-  constexpr int BV = (TILE + W - 1 + 1) & ~1;
-  constexpr int SUB = BU * BV;
-  constexpr int CELLS = W * W;
-  constexpr int NIT = (CELLS + 31) / 32;
-  constexpr int NT = GRID_WARPS * 32;
-  constexpr int TP = TERMS_PER_PASS;
-  extern __shared__ float2 sub[];  // [nc][SUB]
-  __shared__ int hist[TILE * TILE];
-  __shared__ short order[GRID_CHUNK];
-  __shared__ int wsum[GRID_WARPS];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int4 it = items[blockIdx.x];
-  const int tu = it.z >> 16, tv = it.z & 0xffff;
-  const int n = it.y;
-  for (int i = threadIdx.x; i < nc * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
-  if (presorted)
-    __syncthreads();
-  else
-    sort_by_origin(m, it, tu, tv, hist, order, wsum);
-
-  int off[NIT], cu[NIT], cv[NIT];
-#pragma unroll
-  for (int k = 0; k < NIT; ++k) {
-    const int idx = lane + 32 * k;
-    cv[k] = idx / W;
-    cu[k] = idx % W;
-    off[k] = cv[k] * BV + cu[k];
-  }
-  const int seg = (((n + GRID_WARPS - 1) / GRID_WARPS) + 31) & ~31;
-  const int s0 = min(n, warp * seg), s1 = min(n, s0 + seg);
-  constexpr int WS = 2 * W + 1;
-  __shared__ float wts[GRID_WARPS][32 * WS];
-  __shared__ float2 vals[GRID_WARPS][TP][32];
-  float* mw = wts[warp];
-  int cur = -1;
-  float2 acc[TP][NIT];
-#pragma unroll
-  for (int t = 0; t < TP; ++t)
-#pragma unroll
-    for (int k = 0; k < NIT; ++k) acc[t][k] = make_float2(0.f, 0.f);
-  auto flush = [&]() {
-#pragma unroll
-    for (int t = 0; t < TP; ++t)
-      if (t < nc) {
-#pragma unroll
-        for (int k = 0; k < NIT; ++k)
-          if (lane + 32 * k < CELLS) {
-            float* c = reinterpret_cast<float*>(sub + t * SUB + cur + off[k]);
-            atomicAdd(c, acc[t][k].x);
-            atomicAdd(c + 1, acc[t][k].y);
-          }
-      }
-  };
-  for (int base = s0; base < s1; base += 32) {
-    const int nb = min(32, s1 - base);
-    int org = -2;
-    if (lane < nb) {
-      const int i = it.x + (presorted ? base + lane : (int)order[base + lane]);
-      const uint32_t cell = m.cell[i];
-      const float du = m.du[i], dv = m.dv[i];
-      const float a = m.dw[i];
-      float2 val = rot_pow(y[i], t0, a, 1);  // y (i a)^t0, then one factor i a per term
-#pragma unroll
-      for (int t = 0; t < TP; ++t) {
-        vals[warp][t][lane] = val;
-        val = make_float2(-val.y * a, val.x * a);
-      }
-      org = ((int)((cell >> 4) & 0x3fff) - tv * TILE) * BV + (int)(cell >> 18) - tu * TILE;
-#pragma unroll
-      for (int b = 0; b < W; ++b) mw[lane * WS + b] = es_eval_fast(kern, du - (float)b);
-#pragma unroll
-      for (int b = 0; b < W; ++b) mw[lane * WS + W + b] = es_eval_fast(kern, dv - (float)b);
-    }
-    const int prev = __shfl_up_sync(0xffffffffu, org, 1);
-    const unsigned starts =
-        __ballot_sync(0xffffffffu, lane < nb && org != (lane == 0 ? cur : prev));
-    __syncwarp();
-    int j = 0;
-    while (j < nb) {
-      if ((starts >> j) & 1u) {
-        const int oj = __shfl_sync(0xffffffffu, org, j);
-        if (cur >= 0) flush();
-#pragma unroll
-        for (int t = 0; t < TP; ++t)
-#pragma unroll
-          for (int k = 0; k < NIT; ++k) acc[t][k] = make_float2(0.f, 0.f);
-        cur = oj;
-      }
-      const unsigned rest = j < 31 ? (starts & ~((2u << j) - 1u)) : 0u;
-      const int e = rest ? __ffs(rest) - 1 : nb;
-      for (; j < e; ++j) {
-        const float* wj = mw + j * WS;
-        float wgt[NIT];
-#pragma unroll
-        for (int k = 0; k < NIT; ++k) wgt[k] = wj[cu[k]] * wj[W + (cv[k] < W ? cv[k] : 0)];
-#pragma unroll
-        for (int t = 0; t < TP; ++t)
-          if (t < nc) {
-            const float2 v = vals[warp][t][j];
-#pragma unroll
-            for (int k = 0; k < NIT; ++k) {
-              acc[t][k].x = fmaf(wgt[k], v.x, acc[t][k].x);
-              acc[t][k].y = fmaf(wgt[k], v.y, acc[t][k].y);
-            }
-          }
-      }
-    }
-    __syncwarp();
-  }
-  if (cur >= 0) flush();
-  __syncthreads();
-  const size_t plane = (size_t)Nu * Nv;
-  for (int t = 0; t < nc; ++t) {
-    float2* g = grid_terms + (size_t)(t0 + t) * plane;
-    for (int idx = threadIdx.x; idx < SUB; idx += NT) {
-      const int r = idx / BV, c = idx - r * BV;
-      if (c >= BU) continue;
-      const float2 v = sub[t * SUB + idx];
-      if (v.x == 0.f && v.y == 0.f) continue;
-      const int gv = tv * TILE + r, gu = tu * TILE + c;
-      if (gu < Nu && gv < Nv) atomicAdd(&g[(size_t)gv * Nu + gu], v);
-    }
-  }
-}
-
 struct GridPrepArgs {
   const uint32_t* perm;
   const float* wgt;
@@ -1580,25 +1298,6 @@ int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, i
   return FR_OK;
 }
 
-#define FR_W_DISPATCH(W, F, ...)                           \
-  switch (W) {                                             \
-    case 4: return F<4>(__VA_ARGS__);                      \
-    case 5: return F<5>(__VA_ARGS__);                      \
-    case 6: return F<6>(__VA_ARGS__);                      \
-    case 7: return F<7>(__VA_ARGS__);                      \
-    case 8: return F<8>(__VA_ARGS__);                      \
-    case 9: return F<9>(__VA_ARGS__);                      \
-    case 10: return F<10>(__VA_ARGS__);                    \
-    case 11: return F<11>(__VA_ARGS__);                    \
-    case 12: return F<12>(__VA_ARGS__);                    \
-    case 13: return F<13>(__VA_ARGS__);                    \
-    case 14: return F<14>(__VA_ARGS__);                    \
-    case 15: return F<15>(__VA_ARGS__);                    \
-    case 16: return F<16>(__VA_ARGS__);                    \
-    default:                                               \
-      ::fr::set_error("kernel support %d unsupported", W); \
-      return FR_EUNSUPPORTED;                              \
-  }
 
 // 0: no w-term; 1: w-stacking; 2: small-w expansion
 static int wmode_of(const Geometry& geo) { return !geo.wterm ? 0 : (geo.taylor ? 2 : 1); }
@@ -1633,65 +1332,7 @@ static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, in
   return FR_OK;
 }
 
-template <int W>
-static int launch_grid_terms(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
-                             int t0, int nc, const float2* y, float2* grid_terms, cudaStream_t s) {
-  MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
-  constexpr size_t smem = grid_terms_smem_bytes<W>();
-  static bool attr = false;
-  if (!attr) {
-    FR_CUDA_TRY(cudaFuncSetAttribute(grid_terms_kernel<W>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
-  grid_terms_kernel<W><<<(unsigned)n, GRID_WARPS * 32, (size_t)nc * (TILE + W - 1) *
-                                                           ((TILE + W) & ~1) * sizeof(float2),
-                         s>>>(lay.items + i0, m, geo.kern, t0, nc, lay.presorted, y, grid_terms, geo.Nu, geo.Nv);
-  FR_LAUNCHED();
-  return FR_OK;
-}
 
-// algorithmic bytes per visibility visit: cell, du, dv (, dw) in; accumulator / output traffic
-static double meta_bytes(const Geometry& geo) { return 12.0 + (geo.wterm ? 4.0 : 0.0); }
-
-template <int W>
-static int launch_degrid_terms(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
-                               const CUtensorMap& tmap, float2* vis_out, int* status,
-                               cudaStream_t s) {
-  MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
-  const size_t smem = (size_t)geo.nterms * terms_tile_stride(W) * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    FR_CUDA_TRY(cudaFuncSetAttribute(degrid_terms_kernel<W>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     DEGRID_TERMS_SMEM));
-    attr = true;
-  }
-  degrid_terms_kernel<W><<<(unsigned)n, 256, smem, s>>>(tmap, lay.items + i0, m, geo.kern,
-                                                        geo.nterms, geo.Nv, vis_out, status);
-  FR_LAUNCHED();
-  return FR_OK;
-}
-
-static double band_cells(const VisLayout& lay) {
-  return (double)std::max(0, lay.bu1 - lay.bu0 + 1) * std::max(0, lay.bv1 - lay.bv0 + 1);
-}
-
-bool degrid_terms_fits(const Geometry& geo) {
-  return (size_t)geo.nterms * terms_tile_stride(geo.kern.W) * sizeof(float2) <= DEGRID_TERMS_SMEM;
-}
-
-int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtensorMap& tmap,
-                 float2* vis_out, int* status, cudaStream_t s) {
-  const int q = lay.plane_base[g];
-  const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
-  if (i1 <= i0) return FR_OK;
-  // every band cell of every term read once; per visibility: metadata, phase, perm, output
-  ProfScope ps(PC_DEGRID, s,
-               geo.nterms * band_cells(lay) * 8.0 +
-                   (double)lay.plane_visits[q] * (meta_bytes(geo) + 16.0));
-  FR_W_DISPATCH(geo.kern.W, launch_degrid_terms, geo, lay, i0, i1 - i0, tmap, vis_out, status, s);
-}
 
 int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const CUtensorMap& tmap,
                  float2* vacc, float2* vis_out, int* status, cudaStream_t s) {
@@ -1702,25 +1343,6 @@ int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const 
   ProfScope ps(PC_DEGRID, s,
                band_cells(lay) * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 16.0));
   FR_W_DISPATCH(geo.kern.W, launch_degrid, geo, lay, i0, i1 - i0, p, tmap, vacc, vis_out, status, s);
-}
-
-int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* ysorted,
-               float2* grid_terms, cudaStream_t s) {
-  const int q = lay.plane_base[g];
-  const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
-  if (i1 <= i0) return FR_OK;
-  for (int t0 = 0; t0 < geo.nterms; t0 += TERMS_PER_PASS) {
-    const int nc = std::min(TERMS_PER_PASS, geo.nterms - t0);
-    // each band cell of every term written once; per visit: metadata + weighted visibility
-    ProfScope ps(PC_GRID, s,
-                 nc * band_cells(lay) * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 8.0));
-    int r;
-    auto launch = [&](int W) -> int {
-      FR_W_DISPATCH(W, launch_grid_terms, geo, lay, i0, i1 - i0, t0, nc, ysorted, grid_terms, s);
-    };
-    if ((r = launch(geo.kern.W))) return r;
-  }
-  return FR_OK;
 }
 
 int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const float2* ysorted,

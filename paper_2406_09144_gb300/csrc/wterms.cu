@@ -1,0 +1,358 @@
+// Kernels of the small-w expansion (Eq. rime with exp(-2 pi i w (n - 1)) expanded in powers of
+// w about the field centre): all term grids stay resident, the degridder interpolates every term
+// in one pass over the visibilities and the gridder spreads into several term grids per pass.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "fr_internal.cuh"
+#include "vis_common.cuh"
+
+namespace fr {
+
+// float2 stride between the term tiles of degrid_terms_kernel (a multiple of 128 bytes)
+__host__ __device__ constexpr int terms_tile_stride(int W) {
+  return ((TILE + W - 1) * ((TILE + W) & ~1) + 15) & ~15;
+}
+
+// Degridder for the small-w expansion: all N term grids are resident (stacked rows [N * Nv][Nu]),
+// one CTA per work item stages the item's tile of every term with N TMA copies on one
+// mbarrier, and each thread evaluates its visibility's separable kernel once and combines the N
+// interpolations with the weights (-i a)^n before the final phase and scatter.
+template <int W>
+__global__ void __launch_bounds__(256) degrid_terms_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                           const int4* __restrict__ items,
+                                                           MetaPtrs m, EsKernel kern, int nterms,
+                                                           int Nv, float2* __restrict__ vis_out,
+                                                           int* status) {
+  constexpr int BU = TILE + W - 1;
+  constexpr int BV = (TILE + W - 1 + 1) & ~1;
+  constexpr int TS = terms_tile_stride(W);  // 128-byte aligned TMA destinations
+  extern __shared__ __align__(128) float2 tiles[];  // [nterms][TS]
+  __shared__ __align__(8) uint64_t mbar;
+  const int4 it = items[blockIdx.x];
+  const int tu = it.z >> 16, tv = it.z & 0xffff;
+  const uint32_t bar = smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)(BU * BV * sizeof(float2)) * (uint32_t)nterms)
+                 : "memory");
+    for (int n = 0; n < nterms; ++n)
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+          "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tiles + n * TS)),
+          "l"((uint64_t)&tmap), "r"(2 * TILE * tu), "r"(n * Nv + TILE * tv), "r"(bar)
+          : "memory");
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0)) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, ST_TIMEOUT);
+      mbar_wait_bounded(bar, 0);  // let the copies in flight land before the CTA exits
+    }
+    return;
+  }
+  const int end = it.x + it.y;
+  for (int i = it.x + threadIdx.x; i < end; i += blockDim.x) {
+    const uint32_t cell = m.cell[i];
+    const int ru = (int)(cell >> 18) - tu * TILE;
+    const int rv = (int)((cell >> 4) & 0x3fff) - tv * TILE;
+    float ku[W], kv[W];
+    kernel_weights<W>(kern, m.du[i], ku);
+    kernel_weights<W>(kern, m.dv[i], kv);
+    const float a = m.dw[i];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int n = 0; n < nterms; ++n) {
+      const float2* tile = tiles + n * TS;
+      float2 sn = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
+        const float2* row = tile + (rv + b) * BV + ru;
+        float2 ra = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < W; ++c) ra = ffma2(make_float2(ku[c], ku[c]), row[c], ra);
+        sn = ffma2(make_float2(kv[b], kv[b]), ra, sn);
+      }
+      const float2 t = rot_pow(sn, n, a, -1);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    // exp(-2 pi i w t_c)
+    const float f = (float)(int)m.ph[i] * 2.3283064365386963e-10f;
+    float s, c;
+    sincospif(2.f * f, &s, &c);
+    acc = make_float2(acc.x * c + acc.y * s, acc.y * c - acc.x * s);
+    const uint32_t pm = m.perm[i];
+    if (pm >> 31) acc.y = -acc.y;
+    vis_out[pm & 0x7fffffffu] = acc;
+  }
+}
+
+// Gridder for the small-w expansion: one pass spreads every visibility into NC <=
+// TERMS_PER_PASS term grids at once (terms t0 .. t0 + NC - 1, weights (i a)^n), so the kernel
+// weights and the run bookkeeping are shared by all terms. Work items arrive ordered by
+// footprint origin (plan-time sort), so each warp walks runs of equal origin in a contiguous
+// segment and accumulates a run in registers. The terms' sub-grids are shared by the CTA's warps
+// and a run is added to them with shared float atomics; runs are long (a baseline track crosses a
+// cell in tens of integrations), so the atomics are rare next to the multiply-adds.
+//
+// Footprint cells per lane: lane l < R * W owns column u = l % W and the rows r + R k (k < K) with
+// r = l / W, R = 32 / W, K = ceil(W / R), so one kernel weight phi(du - u) serves all its cells.
+// The staged v-weights of a visibility are stored as [r][k] so that a lane reads its K of them
+// with one vector load when K = 2.
+constexpr int TERMS_PER_PASS = 4;
+constexpr int TERMS_WARPS = 8;
+
+template <int W>
+struct TermsLanes {
+  static constexpr int R = 32 / W;                      // rows per pass of the warp
+  static constexpr int K = (W + R - 1) / R;             // passes (cells per lane)
+  static constexpr int NV = R * K;                      // staged v-weights (zero padded)
+  static constexpr int WS = (NV + W + 1) & ~1;          // staged floats per visibility (even)
+};
+
+// dynamic shared memory: NC term sub-grids, then per-warp staged values and kernel weights
+template <int W>
+constexpr size_t grid_terms_smem_bytes(int nc) {
+  return (size_t)nc * (TILE + W - 1) * ((TILE + W) & ~1) * sizeof(float2) +
+         (size_t)TERMS_WARPS * nc * 32 * sizeof(float2) +
+         (size_t)TERMS_WARPS * 32 * TermsLanes<W>::WS * sizeof(float);
+}
+
+template <int W, int NC>
+__global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
+    const int4* __restrict__ items, MetaPtrs m, EsKernel kern, int t0,
+    const float2* __restrict__ y, float2* __restrict__ grid_terms, int Nu, int Nv) {
+  using L = TermsLanes<W>;
+  constexpr int BU = TILE + W - 1;
+  constexpr int BV = (TILE + W - 1 + 1) & ~1;
+  constexpr int SUB = BU * BV;
+  constexpr int NT = TERMS_WARPS * 32;
+  constexpr int K = L::K, WS = L::WS;
+  extern __shared__ float2 sub[];  // [NC][SUB], then vals [warp][32][NC], then wts [warp][32][WS]
+  float2* vals_all = sub + NC * SUB;
+  float* wts = reinterpret_cast<float*>(vals_all + TERMS_WARPS * 32 * NC);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int4 it = items[blockIdx.x];
+  const int tu = it.z >> 16, tv = it.z & 0xffff;
+  const int n = it.y;
+  for (int i = threadIdx.x; i < NC * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  const bool active = lane < L::R * W;
+  const int cu = lane % W, r0 = lane / W;
+  int off[K];
+  bool valid[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int v = r0 + L::R * k;
+    valid[k] = active && v < W;
+    off[k] = v * BV + cu;
+  }
+  const int seg = (((n + TERMS_WARPS - 1) / TERMS_WARPS) + 31) & ~31;
+  const int s0 = min(n, warp * seg), s1 = min(n, s0 + seg);
+  float* mw = wts + warp * 32 * WS;
+  float2* mv = vals_all + warp * 32 * NC;
+  int cur = -1;
+  float2 acc[NC][K];
+#pragma unroll
+  for (int t = 0; t < NC; ++t)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[t][k] = make_float2(0.f, 0.f);
+  auto flush = [&]() {
+#pragma unroll
+    for (int t = 0; t < NC; ++t)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (valid[k]) {
+          float* c = reinterpret_cast<float*>(sub + t * SUB + cur + off[k]);
+          atomicAdd(c, acc[t][k].x);
+          atomicAdd(c + 1, acc[t][k].y);
+        }
+  };
+  auto add = [&](int j) {
+    const float* wj = mw + j * WS;
+    const float wu = wj[L::NV + cu];
+    float wv[K];
+    if constexpr (K == 2) {
+      const float2 p = *reinterpret_cast<const float2*>(wj + 2 * r0);
+      wv[0] = p.x;
+      wv[1] = p.y;
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) wv[k] = wj[r0 * K + k];
+    }
+    float2 vt[NC];
+    if constexpr (NC % 2 == 0) {
+#pragma unroll
+      for (int t = 0; t < NC; t += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(mv + j * NC + t);
+        vt[t] = make_float2(q.x, q.y);
+        vt[t + 1] = make_float2(q.z, q.w);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NC; ++t) vt[t] = mv[j * NC + t];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float g = wu * wv[k];
+      const float2 gg = make_float2(g, g);
+#pragma unroll
+      for (int t = 0; t < NC; ++t) acc[t][k] = ffma2(gg, vt[t], acc[t][k]);
+    }
+  };
+  for (int base = s0; base < s1; base += 32) {
+    const int nb = min(32, s1 - base);
+    int org = -2;
+    if (lane < nb) {
+      const int i = it.x + base + lane;
+      const uint32_t cell = m.cell[i];
+      const float du = m.du[i], dv = m.dv[i];
+      const float a = m.dw[i];
+      float2 val = rot_pow(y[i], t0, a, 1);  // y (i a)^t0, then one factor i a per term
+#pragma unroll
+      for (int t = 0; t < NC; ++t) {
+        mv[lane * NC + t] = val;
+        val = make_float2(-val.y * a, val.x * a);
+      }
+      org = ((int)((cell >> 4) & 0x3fff) - tv * TILE) * BV + (int)(cell >> 18) - tu * TILE;
+      float* w = mw + lane * WS;
+#pragma unroll
+      for (int b = 0; b < L::NV; ++b) {  // v-weights in [r][k] order, zero past W
+        const int v = b / K + L::R * (b % K);
+        w[b] = v < W ? es_eval_fast(kern, dv - (float)v) : 0.f;
+      }
+#pragma unroll
+      for (int b = 0; b < W; ++b) w[L::NV + b] = es_eval_fast(kern, du - (float)b);
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, org, 1);
+    const unsigned starts =
+        __ballot_sync(0xffffffffu, lane < nb && org != (lane == 0 ? cur : prev));
+    __syncwarp();
+    int j = 0;
+    while (j < nb) {
+      if ((starts >> j) & 1u) {
+        const int oj = __shfl_sync(0xffffffffu, org, j);
+        if (cur >= 0) flush();
+#pragma unroll
+        for (int t = 0; t < NC; ++t)
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc[t][k] = make_float2(0.f, 0.f);
+        cur = oj;
+      }
+      const unsigned rest = j < 31 ? (starts & ~((2u << j) - 1u)) : 0u;
+      const int e = rest ? __ffs(rest) - 1 : nb;
+      for (; j + 1 < e; j += 2) {  // two visibilities per step for more independent loads
+        add(j);
+        add(j + 1);
+      }
+      if (j < e) add(j++);
+    }
+    __syncwarp();
+  }
+  if (cur >= 0) flush();
+  __syncthreads();
+  const size_t plane = (size_t)Nu * Nv;
+  for (int t = 0; t < NC; ++t) {
+    float2* g = grid_terms + (size_t)(t0 + t) * plane;
+    for (int idx = threadIdx.x; idx < SUB; idx += NT) {
+      const int r = idx / BV, c = idx - r * BV;
+      if (c >= BU) continue;
+      const float2 v = sub[t * SUB + idx];
+      if (v.x == 0.f && v.y == 0.f) continue;
+      const int gv = tv * TILE + r, gu = tu * TILE + c;
+      if (gu < Nu && gv < Nv) atomicAdd(&g[(size_t)gv * Nu + gu], v);
+    }
+  }
+}
+
+template <int W>
+static int launch_degrid_terms(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
+                               const CUtensorMap& tmap, float2* vis_out, int* status,
+                               cudaStream_t s) {
+  MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
+  const size_t smem = (size_t)geo.nterms * terms_tile_stride(W) * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    FR_CUDA_TRY(cudaFuncSetAttribute(degrid_terms_kernel<W>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     DEGRID_TERMS_SMEM));
+    attr = true;
+  }
+  degrid_terms_kernel<W><<<(unsigned)n, 256, smem, s>>>(tmap, lay.items + i0, m, geo.kern,
+                                                        geo.nterms, geo.Nv, vis_out, status);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+template <int W, int NC>
+static int launch_grid_terms_nc(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
+                                int t0, const float2* y, float2* grid_terms, cudaStream_t s) {
+  MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
+  constexpr size_t smem = grid_terms_smem_bytes<W>(NC);
+  static bool attr = false;
+  if (!attr) {
+    FR_CUDA_TRY(cudaFuncSetAttribute(grid_terms_kernel<W, NC>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  grid_terms_kernel<W, NC><<<(unsigned)n, TERMS_WARPS * 32, smem, s>>>(
+      lay.items + i0, m, geo.kern, t0, y, grid_terms, geo.Nu, geo.Nv);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+template <int W>
+static int launch_grid_terms(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
+                             int t0, int nc, const float2* y, float2* grid_terms, cudaStream_t s) {
+  switch (nc) {
+    case 1: return launch_grid_terms_nc<W, 1>(geo, lay, i0, n, t0, y, grid_terms, s);
+    case 2: return launch_grid_terms_nc<W, 2>(geo, lay, i0, n, t0, y, grid_terms, s);
+    case 3: return launch_grid_terms_nc<W, 3>(geo, lay, i0, n, t0, y, grid_terms, s);
+    default: return launch_grid_terms_nc<W, 4>(geo, lay, i0, n, t0, y, grid_terms, s);
+  }
+}
+
+bool degrid_terms_fits(const Geometry& geo) {
+  return (size_t)geo.nterms * terms_tile_stride(geo.kern.W) * sizeof(float2) <= DEGRID_TERMS_SMEM;
+}
+
+int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtensorMap& tmap,
+                 float2* vis_out, int* status, cudaStream_t s) {
+  const int q = lay.plane_base[g];
+  const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
+  if (i1 <= i0) return FR_OK;
+  // every band cell of every term read once; per visibility: metadata, phase, perm, output
+  ProfScope ps(PC_DEGRID, s,
+               geo.nterms * band_cells(lay) * 8.0 +
+                   (double)lay.plane_visits[q] * (meta_bytes(geo) + 16.0));
+  FR_W_DISPATCH(geo.kern.W, launch_degrid_terms, geo, lay, i0, i1 - i0, tmap, vis_out, status, s);
+}
+
+int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* ysorted,
+               float2* grid_terms, cudaStream_t s) {
+  if (!lay.presorted) {
+    set_error("internal: the multi-term gridder needs origin-ordered work items");
+    return FR_EUNSUPPORTED;
+  }
+  const int q = lay.plane_base[g];
+  const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
+  if (i1 <= i0) return FR_OK;
+  for (int t0 = 0; t0 < geo.nterms; t0 += TERMS_PER_PASS) {
+    const int nc = std::min(TERMS_PER_PASS, geo.nterms - t0);
+    // each band cell of every term written once; per visit: metadata + weighted visibility
+    ProfScope ps(PC_GRID, s,
+                 nc * band_cells(lay) * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 8.0));
+    int r;
+    auto launch = [&](int W) -> int {
+      FR_W_DISPATCH(W, launch_grid_terms, geo, lay, i0, i1 - i0, t0, nc, ysorted, grid_terms, s);
+    };
+    if ((r = launch(geo.kern.W))) return r;
+  }
+  return FR_OK;
+}
+
+}  // namespace fr
