@@ -96,7 +96,10 @@ __device__ __forceinline__ float es_eval_fast(const EsKernel& k, float x) {
 // ------------------------------------------------------------------ tiles and TMA
 constexpr int TILE = 32;       // grid cells per tile side (u and v)
 constexpr int MAXW = 16;       // largest kernel support
-constexpr int GRID_CHUNK = 512;  // visibilities per (tile, plane) work item at most
+// visibilities per work item at most: w-stacking items (sorted by origin in every gridding call)
+// and fixed per-tile chunks (sorted once when the plan is built)
+constexpr int STACK_CHUNK = 512;
+constexpr int ITEM_CHUNK = 2048;
 constexpr int DEGRID_TERMS_SMEM = 200 * 1024;  // shared tiles of all expansion terms at most
 constexpr size_t TERM_GRIDS_MAX_BYTES = (size_t)4 << 30;  // resident expansion term grids at most
 

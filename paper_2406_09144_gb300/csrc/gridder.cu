@@ -262,7 +262,7 @@ struct ItemArgs {
   const int* keybase;    // [ngroups]
   const int* planes;     // [ngroups] (1 without w)
   const int64_t* ebase;  // [ngroups + 1] (group, plane, tile) enumeration base
-  int ngroups, ntiles, ntv, W, wterm, ntb;
+  int ngroups, ntiles, ntv, W, wterm, ntb, chunk;
   int* chunks;           // [E]
   const int* item_off;   // [E + 1] (emit pass)
   int4* items;
@@ -300,7 +300,7 @@ __global__ void count_items(ItemArgs a, int64_t E) {
        e += (int64_t)gridDim.x * blockDim.x) {
     int b, c, t;
     item_range(a, e, &b, &c, &t);
-    a.chunks[e] = (c + GRID_CHUNK - 1) / GRID_CHUNK;
+    a.chunks[e] = (c + a.chunk - 1) / a.chunk;
   }
 }
 
@@ -312,8 +312,8 @@ __global__ void emit_items(ItemArgs a, int64_t E) {
     if (c == 0) continue;
     const int tu = t / a.ntv, tv = t - (t / a.ntv) * a.ntv;
     int o = a.item_off[e];
-    for (int s = 0; s < c; s += GRID_CHUNK, ++o)
-      a.items[o] = make_int4(b + s, min(GRID_CHUNK, c - s), (tu << 16) | tv, 0);
+    for (int s = 0; s < c; s += a.chunk, ++o)
+      a.items[o] = make_int4(b + s, min(a.chunk, c - s), (tu << 16) | tv, 0);
   }
 }
 
@@ -619,6 +619,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
   ia.ntv = lay->ntv;
   ia.ntb = ntb;
   ia.W = geo.kern.W;
+  ia.chunk = stack ? STACK_CHUNK : ITEM_CHUNK;
   ia.wterm = stack;
   ia.chunks = d_chunks;
   ia.item_off = d_item_off;
@@ -997,6 +998,7 @@ constexpr size_t grid_smem_bytes() {
 
 // Counting sort of a work item's visibilities by footprint origin (rv * TILE + ru) into
 // `order` (indices relative to the item start); all GRID_WARPS * 32 threads take part.
+template <int CHUNK>
 __device__ __forceinline__ void sort_by_origin(const MetaPtrs& m, const int4 it, int tu, int tv,
                                                int* hist, short* order, int* wsum) {
   constexpr int NT = GRID_WARPS * 32;
@@ -1005,9 +1007,9 @@ __device__ __forceinline__ void sort_by_origin(const MetaPtrs& m, const int4 it,
   const int n = it.y;
   for (int i = threadIdx.x; i < NKEY; i += NT) hist[i] = 0;
   __syncthreads();
-  int mykey[GRID_CHUNK / NT];
+  int mykey[CHUNK / NT];
 #pragma unroll
-  for (int r = 0; r < GRID_CHUNK / NT; ++r) {
+  for (int r = 0; r < CHUNK / NT; ++r) {
     const int t = threadIdx.x + r * NT;
     mykey[r] = -1;
     if (t < n) {
@@ -1042,7 +1044,7 @@ __device__ __forceinline__ void sort_by_origin(const MetaPtrs& m, const int4 it,
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < GRID_CHUNK / NT; ++r)
+  for (int r = 0; r < CHUNK / NT; ++r)
     if (mykey[r] >= 0) order[atomicAdd(&hist[mykey[r]], 1)] = (short)(threadIdx.x + r * NT);
   __syncthreads();
 }
@@ -1061,11 +1063,11 @@ struct SortArrays {
 __global__ void __launch_bounds__(GRID_WARPS * 32) presort_kernel(const int4* __restrict__ items,
                                                                   SortArrays in, SortArrays out) {
   __shared__ int hist[TILE * TILE];
-  __shared__ short order[GRID_CHUNK];
+  __shared__ short order[ITEM_CHUNK];
   __shared__ int wsum[GRID_WARPS];
   const int4 it = items[blockIdx.x];
   MetaPtrs m{in.cell, nullptr, nullptr, nullptr, nullptr, nullptr};
-  sort_by_origin(m, it, it.z >> 16, it.z & 0xffff, hist, order, wsum);
+  sort_by_origin<ITEM_CHUNK>(m, it, it.z >> 16, it.z & 0xffff, hist, order, wsum);
   for (int r = threadIdx.x; r < it.y; r += blockDim.x) {
     const int i = it.x + order[r], o = it.x + r;
     out.cell[o] = in.cell[i];
@@ -1129,7 +1131,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   constexpr int NKEY = TILE * TILE;
   extern __shared__ float2 sub[];  // [GRID_WARPS][SUB]
   __shared__ int hist[NKEY];
-  __shared__ short order[GRID_CHUNK];
+  __shared__ short order[STACK_CHUNK];  // only w-stacking items are sorted here
   __shared__ int wsum[GRID_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int4 it = items[blockIdx.x];
@@ -1142,7 +1144,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   if (presorted)
     __syncthreads();
   else
-    sort_by_origin(m, it, tu, tv, hist, order, wsum);
+    sort_by_origin<STACK_CHUNK>(m, it, tu, tv, hist, order, wsum);
 
   float2* mysub = sub + warp * SUB;
   int off[NIT], cu[NIT], cv[NIT];

@@ -204,15 +204,30 @@ __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
       for (int t = 0; t < NC; ++t) acc[t][k] = ffma2(gg, vt[t], acc[t][k]);
     }
   };
+  // the next batch's metadata is loaded while the current batch is processed
+  uint32_t n_cell = 0;
+  float n_du = 0.f, n_dv = 0.f, n_a = 0.f;
+  float2 n_y = make_float2(0.f, 0.f);
+  auto fetch = [&](int base) {
+    if (base + lane < s1) {
+      const int i = it.x + base + lane;
+      n_cell = m.cell[i];
+      n_du = m.du[i];
+      n_dv = m.dv[i];
+      n_a = m.dw[i];
+      n_y = y[i];
+    }
+  };
+  fetch(s0);
   for (int base = s0; base < s1; base += 32) {
     const int nb = min(32, s1 - base);
+    const uint32_t cell = n_cell;
+    const float du = n_du, dv = n_dv, a = n_a;
+    const float2 yv = n_y;
+    fetch(base + 32);
     int org = -2;
     if (lane < nb) {
-      const int i = it.x + base + lane;
-      const uint32_t cell = m.cell[i];
-      const float du = m.du[i], dv = m.dv[i];
-      const float a = m.dw[i];
-      float2 val = rot_pow(y[i], t0, a, 1);  // y (i a)^t0, then one factor i a per term
+      float2 val = rot_pow(yv, t0, a, 1);  // y (i a)^t0, then one factor i a per term
 #pragma unroll
       for (int t = 0; t < NC; ++t) {
         mv[lane * NC + t] = val;
