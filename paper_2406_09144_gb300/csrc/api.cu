@@ -228,6 +228,8 @@ static void free_ws(Workspace* w) {
   cudaFree(w->grid);
   cudaFree(w->grid_terms);
   cudaFree(w->grid_terms_g);
+  cudaFree(w->b1_terms);
+  cudaFree(w->b1g_terms);
   cudaFree(w->vbuf);
   cudaFree(w->h);
   cudaFree(w->tmp_img);
@@ -291,6 +293,7 @@ static int get_ws(fr_plan* p, cudaStream_t s, Workspace** out) {
 static int ws_reserve_terms(const Geometry& g, Workspace* w, cudaStream_t s) {
   if (w->grid_terms) return FR_OK;
   const size_t n = (size_t)g.nterms * g.Nu * g.Nv;
+  if (!w->b1_terms) FR_TRY(ws_alloc(&w->b1_terms, (size_t)g.nterms * g.nx * g.Nv, w));
   FR_TRY(ws_alloc(&w->grid_terms, n, w));
   FR_CUDA_TRY(cudaMemsetAsync(w->grid_terms, 0, n * sizeof(float2), s));
   int r = make_tmap(&w->tmap_terms, w->grid_terms, g.Nu, g.nterms * g.Nv, g.kern.W);
@@ -307,6 +310,12 @@ static int ws_reserve_terms_g(const Geometry& g, Workspace* w, cudaStream_t s) {
   if (!w->grid_terms_g) {
     FR_TRY(ws_alloc(&w->grid_terms_g, n, w));
     w->terms_g_zero = false;
+  }
+  if (!w->b1g_terms) {
+    // the post-pass writes only the band columns of each half plane: zero the rest once
+    const size_t nb = (size_t)g.nterms * g.nx * g.Nv;
+    FR_TRY(ws_alloc(&w->b1g_terms, nb, w));
+    FR_CUDA_TRY(cudaMemsetAsync(w->b1g_terms, 0, nb * sizeof(float2), s));
   }
   if (!w->terms_g_zero) {
     FR_CUDA_TRY(cudaMemsetAsync(w->grid_terms_g, 0, n * sizeof(float2), s));
@@ -385,11 +394,10 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
     if (terms) {
       const int q = lay.plane_base[g];
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
-      for (int p = 0; p < P; ++p) {
-        PlaneArgs a = plane_args(geo, lay, g, p);
-        FR_TRY(degrid_prepass(a, sky + g * img, w->b1, w->grid_terms + (size_t)p * geo.Nu * geo.Nv,
-                              pl->tw[ilog2(geo.Nv)], pl->tw[ilog2(geo.Nu)], s));
-      }
+      PlaneArgs a = plane_args(geo, lay, g, 0);
+      FR_TRY(degrid_prepass_terms(a, P, sky + g * img, w->b1_terms, (size_t)geo.nx * geo.Nv,
+                                  w->grid_terms, (size_t)geo.Nu * geo.Nv, pl->tw[ilog2(geo.Nv)],
+                                  pl->tw[ilog2(geo.Nu)], s));
       FR_TRY(degrid_terms(geo, lay, g, w->tmap_terms, vis, pl->status, s));
       continue;
     }
@@ -425,11 +433,10 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
       }
       w->terms_g_zero = false;
       FR_TRY(grid_terms(geo, lay, g, ybuf, w->grid_terms_g, s));
-      for (int p = 0; p < geo.nterms; ++p) {
-        PlaneArgs a = plane_args(geo, lay, g, p);
-        FR_TRY(grid_postpass(a, w->grid_terms_g + p * plane, b1, dirty + g * img, p ? 1 : 0,
-                             pl->tw[ilog2(geo.Nu)], pl->tw[ilog2(geo.Nv)], s));
-      }
+      PlaneArgs a = plane_args(geo, lay, g, 0);
+      FR_TRY(grid_postpass_terms(a, geo.nterms, w->grid_terms_g, plane, w->b1g_terms,
+                                 (size_t)geo.nx * geo.Nv, dirty + g * img, pl->tw[ilog2(geo.Nu)],
+                                 pl->tw[ilog2(geo.Nv)], s));
       w->terms_g_zero = true;  // the post-pass zeroes the band it reads
     }
     return FR_OK;
@@ -1033,7 +1040,8 @@ int fr_plan_footprint(fr_plan_t p, size_t* resident_bytes, size_t* workspace_byt
       m = (2 * (size_t)g.nx * g.Nv + (size_t)g.Nu * g.Nv +
            (size_t)std::max<int64_t>(p->lay.nsorted, 1)) *
           sizeof(float2);
-      if (use_term_grids(g)) m += 2 * (size_t)g.nterms * g.Nu * g.Nv * sizeof(float2);
+      if (use_term_grids(g))
+        m += 2 * (size_t)g.nterms * (g.Nu + g.nx) * g.Nv * sizeof(float2);
     }
     *workspace_bytes = m;
   }

@@ -162,6 +162,75 @@ int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
   return FR_OK;
 }
 
+// Summing pass: for each of op.nterms() inputs per sequence (blockIdx.x selects B sequences),
+// load, transform and add op.value(t, seq, o, view) into per-thread accumulators; one
+// op.store(seq, o, sum) per output at the end. Row-major outputs (o fastest), nout <= L.
+//   float2 load(int t, int seq, int i); float value(int t, int seq, int o, SeqView v);
+//   void store(int seq, int o, float sum)
+template <int LOG2L, int DIR, class Op>
+__global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB)
+    fft_pass_sum_kernel(Op op, const float2* __restrict__ tw) {
+  using C = FftCfg<LOG2L>;
+  constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
+  constexpr int PER = B * L / NT;
+  extern __shared__ float2 smem[];
+  const int nseq = op.nseq(), nout = op.nout(), nterm = op.nterms();
+  const int seq0 = blockIdx.x * B;
+  float acc[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) acc[k] = 0.f;
+  for (int t = 0; t < nterm; ++t) {
+    float2 r[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = threadIdx.x + k * NT;
+      const int b = idx / L, i = idx % L;
+      r[k] = (seq0 + b < nseq) ? op.load(t, seq0 + b, i) : make_float2(0.f, 0.f);
+    }
+    if (t > 0) __syncthreads();  // the previous term's outputs have been read
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = threadIdx.x + k * NT;
+      smem[(idx / L) * LP + spad(idx % L)] = r[k];
+    }
+    __syncthreads();
+    fft_stages<LOG2L, 0, DIR>(smem, tw);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = threadIdx.x + k * NT;
+      if (idx < B * nout) {
+        const int b = idx / nout, o = idx % nout;
+        if (seq0 + b < nseq) acc[k] += op.value(t, seq0 + b, o, SeqView{smem + b * LP});
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + k * NT;
+    if (idx < B * nout) {
+      const int b = idx / nout, o = idx % nout;
+      if (seq0 + b < nseq) op.store(seq0 + b, o, acc[k]);
+    }
+  }
+}
+
+template <int LOG2L, int DIR, class Op>
+int launch_pass_sum(const Op& op, const float2* tw, cudaStream_t s) {
+  using C = FftCfg<LOG2L>;
+  const int nblk = (op.nseq() + C::B - 1) / C::B;
+  if (nblk == 0) return FR_OK;
+  auto kern = fft_pass_sum_kernel<LOG2L, DIR, Op>;
+  static bool attr = false;
+  if (!attr) {
+    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    attr = true;
+  }
+  kern<<<nblk, C::NT, C::SMEM, s>>>(op, tw);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
 // Defaults for the optional parts of an op.
 struct OpBase {
   static constexpr bool TRANSPOSED = false;

@@ -30,6 +30,13 @@ __device__ __forceinline__ void plane_phase(int32_t tq, long long k64, float* c,
   sincospif(2.f * f, s, c);
 }
 
+// 1 / k! for the expansion terms
+__constant__ float c_inv_fact[MAX_TERMS] = {
+    1.f,           1.f,           1.f / 2.f,          1.f / 6.f,           1.f / 24.f,
+    1.f / 120.f,   1.f / 720.f,   1.f / 5040.f,       1.f / 40320.f,       1.f / 362880.f,
+    1.f / 3628800.f, 1.f / 39916800.f, 1.f / 479001600.f, 1.f / 6227020800.f, 1.f / 87178291200.f,
+    1.f / 1307674368000.f};
+
 // tau^n / n! for the small-w expansion, tau = tq * 2^-30 = (t - t_c) / t_half
 __device__ __forceinline__ float taylor_factor(int32_t tq, int n, float inv_fact) {
   const float tau = (float)tq * 9.313225746154785e-10f;
@@ -45,9 +52,9 @@ struct D1Op : OpBase {
   const int32_t* tq;
   long long k64;
   int wterm;
-  int taylor, n;
-  float inv_fact;
-  float2* b1t;  // [band v][nx]
+  int taylor, n;  // expansion term n + blockIdx.y
+  float2* b1t;  // [band v][nx], term blockIdx.y at b1t + blockIdx.y * b1t_stride
+  size_t b1t_stride;
   int nx, ny, Nv;
   int vb0, nvb;  // occupied band of v: only these outputs are stored
   __host__ __device__ int nseq() const { return nx; }
@@ -64,20 +71,24 @@ struct D1Op : OpBase {
     const int pix = jx * ny + jy;
     const float val = __ldg(&sky[pix]) * __ldg(&corr[pix]);
     if (!wterm) return make_float2(val, 0.f);
-    if (taylor) return make_float2(val * taylor_factor(__ldg(&tq[pix]), n, inv_fact), 0.f);
+    if (taylor) {
+      const int m = n + blockIdx.y;
+      return make_float2(val * taylor_factor(__ldg(&tq[pix]), m, c_inv_fact[m]), 0.f);
+    }
     float c, s;
     plane_phase(__ldg(&tq[pix]), k64, &c, &s);
     return make_float2(val * c, -val * s);
   }
   __device__ double store(int jx, int o, SeqView s) const {
-    b1t[(size_t)o * nx + jx] = s[vb0 + o];
+    b1t[blockIdx.y * b1t_stride + (size_t)o * nx + jx] = s[vb0 + o];
     return 0.0;
   }
 };
 
 struct D2Op : OpBase {
   const float2* b1t;
-  float2* grid;  // [Nv][Nu]
+  float2* grid;  // [Nv][Nu]; term blockIdx.y at the strides below
+  size_t b1t_stride, grid_stride;
   int nx, Nu, Nv;
   int vb0, nvb, ub0, nub;  // only band rows are transformed, only band columns stored
   __host__ __device__ int nseq() const { return nvb; }
@@ -91,26 +102,27 @@ struct D2Op : OpBase {
       jx = i - Nu + hx;
     else
       return make_float2(0.f, 0.f);
-    return b1t[(size_t)v * nx + jx];  // v: band row index
+    return b1t[blockIdx.y * b1t_stride + (size_t)v * nx + jx];  // v: band row index
   }
   __device__ double store(int q, int o, SeqView s) const {
     const int u = ub0 + o;
-    grid[(size_t)(vb0 + q) * Nu + u] = s[u];
+    grid[blockIdx.y * grid_stride + (size_t)(vb0 + q) * Nu + u] = s[u];
     return 0.0;
   }
 };
 
 struct G1Op : OpBase {
   static constexpr bool TRANSPOSED = true;
-  float2* grid;  // [Nv][Nu]
+  float2* grid;  // [Nv][Nu]; term blockIdx.y at the strides below
   float2* b1;    // [nx][Nv], zero outside the band columns
+  size_t grid_stride, b1_stride;
   int nx, Nu, Nv;
   int vb0, nvb, ub0, nub;  // rows outside the band are zero and transform to zero
   __host__ __device__ int nseq() const { return nvb; }
   __host__ __device__ int nout() const { return nx; }
   __device__ float2 load(int q, int i) const {
     if (i < ub0 || i >= ub0 + nub) return make_float2(0.f, 0.f);  // zero outside the band
-    return grid[(size_t)(vb0 + q) * Nu + i];
+    return grid[blockIdx.y * grid_stride + (size_t)(vb0 + q) * Nu + i];
   }
   __device__ void after_load(int seq0, int nb) const {
     // the gridder writes only inside the band: zeroing the band part of the rows restores an
@@ -118,12 +130,13 @@ struct G1Op : OpBase {
     const int n = nb * nub;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int r = i / nub, c = i - (i / nub) * nub;
-      grid[(size_t)(vb0 + seq0 + r) * Nu + ub0 + c] = make_float2(0.f, 0.f);
+      grid[blockIdx.y * grid_stride + (size_t)(vb0 + seq0 + r) * Nu + ub0 + c] =
+          make_float2(0.f, 0.f);
     }
   }
   __device__ double store(int q, int o, SeqView s) const {
     const int i = (o - (nx >> 1) + Nu) & (Nu - 1);
-    b1[(size_t)o * Nv + vb0 + q] = s[i];
+    b1[blockIdx.y * b1_stride + (size_t)o * Nv + vb0 + q] = s[i];
     return 0.0;
   }
 };
@@ -161,6 +174,32 @@ struct G2Op : OpBase {
   }
 };
 
+// Gridding post-pass, second half, for all expansion terms at once: each term's half plane is
+// transformed in turn and Re(Z_t) tau^t / t! summed per pixel before one store of corr * sum.
+struct G2TermsOp {
+  const float2* b1;  // term t at b1 + t * b1_stride, [nx][Nv]
+  size_t b1_stride;
+  float* dirty;
+  const float* corr;
+  const int32_t* tq;
+  int nterm;
+  int nx, ny, Nv;
+  __host__ __device__ int nseq() const { return nx; }
+  __host__ __device__ int nout() const { return ny; }
+  __device__ int nterms() const { return nterm; }
+  __device__ float2 load(int t, int jx, int i) const {
+    return b1[t * b1_stride + (size_t)jx * Nv + i];
+  }
+  __device__ float value(int t, int jx, int jy, SeqView s) const {
+    const int i = (jy - (ny >> 1) + Nv) & (Nv - 1);
+    return s[i].x * taylor_factor(__ldg(&tq[jx * ny + jy]), t, c_inv_fact[t]);
+  }
+  __device__ void store(int jx, int jy, float sum) const {
+    const int pix = jx * ny + jy;
+    dirty[pix] = sum * __ldg(&corr[pix]);
+  }
+};
+
 template <int LG>
 static int run_d1(const D1Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, 1, tw, s); }
 template <int LG>
@@ -174,6 +213,19 @@ static int d1(int lg, const D1Op& op, const float2* tw, cudaStream_t s) { FR_LOG
 static int d2(int lg, const D2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2, op, tw, s); }
 static int g1(int lg, const G1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1, op, tw, s); }
 static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2, op, tw, s); }
+template <int LG>
+static int run_d1t(const D1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, nt, tw, s); }
+template <int LG>
+static int run_d2t(const D2Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, nt, tw, s); }
+template <int LG>
+static int run_g1t(const G1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, nt, tw, s); }
+template <int LG>
+static int run_g2t(const G2TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass_sum<LG, 1>(op, tw, s); }
+static int d1t(int lg, const D1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1t, op, nt, tw, s); }
+static int d2t(int lg, const D2Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2t, op, nt, tw, s); }
+static int g1t(int lg, const G1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1t, op, nt, tw, s); }
+static int g2t(int lg, const G2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2t, op, tw, s); }
+
 
 int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
                    const float2* twv, const float2* twu, cudaStream_t s) {
@@ -190,8 +242,8 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
   o1.wterm = a.wterm;
   o1.taylor = a.taylor;
   o1.n = a.n;
-  o1.inv_fact = a.inv_fact;
   o1.b1t = b1;
+  o1.b1t_stride = 0;
   o1.nx = a.nx;
   o1.ny = a.ny;
   o1.Nv = a.Nv;
@@ -203,6 +255,7 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
   D2Op o2;
   o2.b1t = b1;
   o2.grid = grid;
+  o2.b1t_stride = o2.grid_stride = 0;
   o2.nx = a.nx;
   o2.Nu = a.Nu;
   o2.Nv = a.Nv;
@@ -223,6 +276,7 @@ int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, in
   G1Op o1;
   o1.grid = grid;
   o1.b1 = b1;
+  o1.grid_stride = o1.b1_stride = 0;
   o1.nx = a.nx;
   o1.Nu = a.Nu;
   o1.Nv = a.Nv;
@@ -253,6 +307,86 @@ int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, in
   ProfScope ps(PC_FFT_ROWS, s,
                half * 8.0 + img * (4.0 + (a.wterm ? 4.0 : 0.0) + (accumulate ? 8.0 : 4.0)));
   return g2(ilog2(a.Nv), o2, twv, s);
+}
+
+int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float2* b1,
+                         size_t b1_stride, float2* grid, size_t grid_stride, const float2* twv,
+                         const float2* twu, cudaStream_t s) {
+  const int nvb = a.bv1 - a.bv0 + 1, nub = a.bu1 - a.bu0 + 1;
+  if (nvb <= 0 || nub <= 0 || nterms <= 0) return FR_OK;
+  const double img = (double)a.nx * a.ny, half = (double)a.nx * nvb, full = (double)nvb * nub;
+  D1Op o1;
+  o1.vb0 = a.bv0;
+  o1.nvb = nvb;
+  o1.sky = sky;
+  o1.corr = a.corr;
+  o1.tq = a.tq;
+  o1.k64 = 0;
+  o1.wterm = 1;
+  o1.taylor = 1;
+  o1.n = 0;
+  o1.b1t = b1;
+  o1.b1t_stride = b1_stride;
+  o1.nx = a.nx;
+  o1.ny = a.ny;
+  o1.Nv = a.Nv;
+  {
+    // per term: sky + corr + tq in (cached after the first term), half plane out
+    ProfScope ps(PC_FFT_ROWS, s, img * 12.0 + nterms * half * 8.0);
+    FR_TRY(d1t(ilog2(a.Nv), o1, nterms, twv, s));
+  }
+  D2Op o2;
+  o2.b1t = b1;
+  o2.grid = grid;
+  o2.b1t_stride = b1_stride;
+  o2.grid_stride = grid_stride;
+  o2.nx = a.nx;
+  o2.Nu = a.Nu;
+  o2.Nv = a.Nv;
+  o2.vb0 = a.bv0;
+  o2.nvb = nvb;
+  o2.ub0 = a.bu0;
+  o2.nub = nub;
+  ProfScope ps(PC_FFT_COLS, s, nterms * (half * 8.0 + full * 8.0));
+  return d2t(ilog2(a.Nu), o2, nterms, twu, s);
+}
+
+int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t grid_stride,
+                        float2* b1, size_t b1_stride, float* dirty, const float2* twu,
+                        const float2* twv, cudaStream_t s) {
+  const int nvb = a.bv1 - a.bv0 + 1, nub = a.bu1 - a.bu0 + 1;
+  if (nvb <= 0 || nub <= 0 || nterms <= 0) return FR_OK;
+  const double img = (double)a.nx * a.ny, band = (double)nvb * nub,
+               half = (double)a.nx * a.Nv;
+  G1Op o1;
+  o1.grid = grid;
+  o1.b1 = b1;
+  o1.grid_stride = grid_stride;
+  o1.b1_stride = b1_stride;
+  o1.nx = a.nx;
+  o1.Nu = a.Nu;
+  o1.Nv = a.Nv;
+  o1.vb0 = a.bv0;
+  o1.nvb = nvb;
+  o1.ub0 = a.bu0;
+  o1.nub = nub;
+  {
+    ProfScope ps(PC_FFT_COLS, s, nterms * (band * 16.0 + (double)a.nx * nvb * 8.0));
+    FR_TRY(g1t(ilog2(a.Nu), o1, nterms, twu, s));
+  }
+  G2TermsOp o2;
+  o2.b1 = b1;
+  o2.b1_stride = b1_stride;
+  o2.dirty = dirty;
+  o2.corr = a.corr;
+  o2.tq = a.tq;
+  o2.nterm = nterms;
+  o2.nx = a.nx;
+  o2.ny = a.ny;
+  o2.Nv = a.Nv;
+  // per term a half plane in; corr + tq in and the image out once
+  ProfScope ps(PC_FFT_ROWS, s, nterms * half * 8.0 + img * 12.0);
+  return g2t(ilog2(a.Nv), o2, twv, s);
 }
 
 int fft_max_log2() { return 14; }

@@ -178,6 +178,8 @@ struct Workspace {
   CUtensorMap tmap_terms;        // TMA descriptor of `grid_terms` (rows nterms * Nv)
   float2* grid_terms_g = nullptr;  // [nterms][Nv][Nu] gridding term grids (kept zero)
   bool terms_g_zero = false;
+  float2* b1_terms = nullptr;   // [nterms][band v][nx] degridding half planes
+  float2* b1g_terms = nullptr;  // [nterms][nx][Nv] gridding half planes (zero off-band)
   size_t bytes = 0;
 };
 
@@ -221,6 +223,15 @@ struct PlaneArgs {
   int n;           // term index
   float inv_fact;  // 1 / n!
 };
+constexpr int MAX_TERMS = 16;  // small-w expansion terms at most (the plan uses <= 12)
+// All nterms expansion terms in one launch per pass: term t's half plane at b1 + t * b1_stride,
+// its grid at grid + t * grid_stride; the gridding post-pass sums the terms into `dirty`.
+int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float2* b1,
+                         size_t b1_stride, float2* grid, size_t grid_stride, const float2* twv,
+                         const float2* twu, cudaStream_t s);
+int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t grid_stride,
+                        float2* b1, size_t b1_stride, float* dirty, const float2* twu,
+                        const float2* twv, cudaStream_t s);
 int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
                    const float2* twv, const float2* twu, cudaStream_t s);
 int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
