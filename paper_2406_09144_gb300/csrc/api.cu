@@ -292,11 +292,12 @@ static int get_ws(fr_plan* p, cudaStream_t s, Workspace** out) {
 // so that tile cells outside the band, which no footprint reads, hold finite values
 static int ws_reserve_terms(const Geometry& g, Workspace* w, cudaStream_t s) {
   if (w->grid_terms) return FR_OK;
-  const size_t n = (size_t)g.nterms * g.Nu * g.Nv;
+  const int T = term_grid_count(g);
+  const size_t n = (size_t)T * g.Nu * g.Nv;
   if (!w->b1_terms) FR_TRY(ws_alloc(&w->b1_terms, (size_t)g.nterms * g.nx * g.Nv, w));
   FR_TRY(ws_alloc(&w->grid_terms, n, w));
   FR_CUDA_TRY(cudaMemsetAsync(w->grid_terms, 0, n * sizeof(float2), s));
-  int r = make_tmap(&w->tmap_terms, w->grid_terms, g.Nu, g.nterms * g.Nv, g.kern.W);
+  int r = make_tmap_terms(&w->tmap_terms, w->grid_terms, g.Nu, g.Nv, T, g.kern.W);
   if (r) {
     cudaFree(w->grid_terms);
     w->bytes -= n * sizeof(float2);
@@ -327,7 +328,7 @@ static int ws_reserve_terms_g(const Geometry& g, Workspace* w, cudaStream_t s) {
 // the small-w expansion keeps all its term grids resident when they fit
 static bool use_term_grids(const Geometry& g) {
   return g.wterm && g.taylor && degrid_terms_fits(g) &&
-         (size_t)g.nterms * g.Nu * g.Nv * sizeof(float2) <= TERM_GRIDS_MAX_BYTES;
+         (size_t)term_grid_count(g) * g.Nu * g.Nv * sizeof(float2) <= TERM_GRIDS_MAX_BYTES;
 }
 
 static int ws_reserve_h(Workspace* w, size_t n) {
@@ -396,7 +397,7 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
       PlaneArgs a = plane_args(geo, lay, g, 0);
       FR_TRY(degrid_prepass_terms(a, P, sky + g * img, w->b1_terms, (size_t)geo.nx * geo.Nv,
-                                  w->grid_terms, (size_t)geo.Nu * geo.Nv, pl->tw[ilog2(geo.Nv)],
+                                  w->grid_terms, term_grid_count(geo), pl->tw[ilog2(geo.Nv)],
                                   pl->tw[ilog2(geo.Nu)], s));
       FR_TRY(degrid_terms(geo, lay, g, w->tmap_terms, vis, pl->status, s));
       continue;
@@ -464,8 +465,9 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
 static int choose_support(double eps) {
   // measured against the FP64 oracle: W = ceil(log10(1/eps)) + 1 left the relative L2 error of
   // R at about 1.2 eps for eps = 1e-5; one more cell of support restores a margin
-  int W = (int)std::ceil(std::log10(1.0 / eps)) + 2;
-  return std::min(16, std::max(4, W));
+  // (eps in [1e-6, 1e-2] gives 4 ..8; the clamp also absorbs rounding of log10 at the ends)
+  int W = (int)std::ceil(std::log10(1.0 / eps) - 1e-9) + 2;
+  return std::min(MAXW, std::max(MINW, W));
 }
 
 static void set_kernel(Geometry* g, int W) {

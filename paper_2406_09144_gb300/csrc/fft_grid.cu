@@ -111,6 +111,39 @@ struct D2Op : OpBase {
   }
 };
 
+// D2 for the interleaved term grids of the expansion degridder: sequence s = (band row q,
+// term t) with t fastest, output G[v][u][t] (T >= nterm terms per cell). The transposed store
+// writes the B terms of a cell next to each other.
+struct D2TermsOp : OpBase {
+  static constexpr bool TRANSPOSED = true;
+  const float2* b1t;  // term t at b1t + t * b1t_stride, [band v][nx]
+  size_t b1t_stride;
+  float2* grid;  // [Nv][Nu][T]
+  int nterm, T;
+  int nx, Nu, Nv;
+  int vb0, nvb, ub0, nub;
+  __host__ __device__ int nseq() const { return nvb * nterm; }
+  __host__ __device__ int nout() const { return nub; }
+  __device__ float2 load(int sq, int i) const {
+    const int q = sq / nterm, t = sq - (sq / nterm) * nterm;
+    const int hx = nx >> 1;
+    int jx;
+    if (i < hx)
+      jx = i + hx;
+    else if (i >= Nu - hx)
+      jx = i - Nu + hx;
+    else
+      return make_float2(0.f, 0.f);
+    return b1t[t * b1t_stride + (size_t)q * nx + jx];
+  }
+  __device__ double store(int sq, int o, SeqView s) const {
+    const int q = sq / nterm, t = sq - (sq / nterm) * nterm;
+    const int u = ub0 + o;
+    grid[((size_t)(vb0 + q) * Nu + u) * T + t] = s[u];
+    return 0.0;
+  }
+};
+
 struct G1Op : OpBase {
   static constexpr bool TRANSPOSED = true;
   float2* grid;  // [Nv][Nu]; term blockIdx.y at the strides below
@@ -216,13 +249,13 @@ static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG
 template <int LG>
 static int run_d1t(const D1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, nt, tw, s); }
 template <int LG>
-static int run_d2t(const D2Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, nt, tw, s); }
+static int run_d2i(const D2TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, 1, tw, s); }
+static int d2i(int lg, const D2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2i, op, tw, s); }
 template <int LG>
 static int run_g1t(const G1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, nt, tw, s); }
 template <int LG>
 static int run_g2t(const G2TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass_sum<LG, 1>(op, tw, s); }
 static int d1t(int lg, const D1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1t, op, nt, tw, s); }
-static int d2t(int lg, const D2Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2t, op, nt, tw, s); }
 static int g1t(int lg, const G1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1t, op, nt, tw, s); }
 static int g2t(int lg, const G2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2t, op, tw, s); }
 
@@ -310,7 +343,7 @@ int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, in
 }
 
 int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float2* b1,
-                         size_t b1_stride, float2* grid, size_t grid_stride, const float2* twv,
+                         size_t b1_stride, float2* grid, int T, const float2* twv,
                          const float2* twu, cudaStream_t s) {
   const int nvb = a.bv1 - a.bv0 + 1, nub = a.bu1 - a.bu0 + 1;
   if (nvb <= 0 || nub <= 0 || nterms <= 0) return FR_OK;
@@ -335,11 +368,12 @@ int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float
     ProfScope ps(PC_FFT_ROWS, s, img * 12.0 + nterms * half * 8.0);
     FR_TRY(d1t(ilog2(a.Nv), o1, nterms, twv, s));
   }
-  D2Op o2;
+  D2TermsOp o2;
   o2.b1t = b1;
-  o2.grid = grid;
   o2.b1t_stride = b1_stride;
-  o2.grid_stride = grid_stride;
+  o2.grid = grid;
+  o2.nterm = nterms;
+  o2.T = T;
   o2.nx = a.nx;
   o2.Nu = a.Nu;
   o2.Nv = a.Nv;
@@ -348,7 +382,7 @@ int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float
   o2.ub0 = a.bu0;
   o2.nub = nub;
   ProfScope ps(PC_FFT_COLS, s, nterms * (half * 8.0 + full * 8.0));
-  return d2t(ilog2(a.Nu), o2, nterms, twu, s);
+  return d2i(ilog2(a.Nu), o2, twu, s);
 }
 
 int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t grid_stride,

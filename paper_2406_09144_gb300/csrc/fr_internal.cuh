@@ -95,7 +95,7 @@ __device__ __forceinline__ float es_eval_fast(const EsKernel& k, float x) {
 
 // ------------------------------------------------------------------ tiles and TMA
 constexpr int TILE = 32;       // grid cells per tile side (u and v)
-constexpr int MAXW = 16;       // largest kernel support
+constexpr int MINW = 4, MAXW = 8;  // kernel supports of eps in [1e-6, 1e-2]
 // visibilities per work item at most: w-stacking items (sorted by origin in every gridding call)
 // and fixed per-tile chunks (sorted once when the plan is built)
 constexpr int STACK_CHUNK = 512;
@@ -174,8 +174,8 @@ struct Workspace {
   size_t red_n = 0;
   CUtensorMap tmap;          // TMA descriptor of `grid`
   bool tmap_ok = false;
-  float2* grid_terms = nullptr;  // [nterms][Nv][Nu] term grids of the small-w expansion
-  CUtensorMap tmap_terms;        // TMA descriptor of `grid_terms` (rows nterms * Nv)
+  float2* grid_terms = nullptr;  // [Nv][Nu][T] interleaved term grids of the small-w expansion
+  CUtensorMap tmap_terms;        // 3-D TMA descriptor of `grid_terms`
   float2* grid_terms_g = nullptr;  // [nterms][Nv][Nu] gridding term grids (kept zero)
   bool terms_g_zero = false;
   float2* b1_terms = nullptr;   // [nterms][band v][nx] degridding half planes
@@ -226,8 +226,9 @@ struct PlaneArgs {
 constexpr int MAX_TERMS = 16;  // small-w expansion terms at most (the plan uses <= 12)
 // All nterms expansion terms in one launch per pass: term t's half plane at b1 + t * b1_stride,
 // its grid at grid + t * grid_stride; the gridding post-pass sums the terms into `dirty`.
+// (the degridding pre-pass writes the interleaved term grids G[v][u][t], t < T)
 int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float2* b1,
-                         size_t b1_stride, float2* grid, size_t grid_stride, const float2* twv,
+                         size_t b1_stride, float2* grid, int T, const float2* twv,
                          const float2* twu, cudaStream_t s);
 int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t grid_stride,
                         float2* b1, size_t b1_stride, float* dirty, const float2* twu,
@@ -266,8 +267,11 @@ int make_tmap(CUtensorMap* m, float2* grid, int Nu, int Nv, int W);
 int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p,
                  const CUtensorMap& tmap, float2* vacc, float2* vis_out, int* status,
                  cudaStream_t s);
-// small-w expansion: all nterms term grids stacked [nterms][Nv][Nu] behind one tensor map
+// small-w expansion: interleaved term grids [Nv][Nu][T] behind one 3-D tensor map (degridding),
+// stacked [nterms][Nv][Nu] grids (gridding)
 bool degrid_terms_fits(const Geometry& geo);
+int term_grid_count(const Geometry& geo);  // T: terms per cell of the interleaved term grids
+int make_tmap_terms(CUtensorMap* m, float2* grid, int Nu, int Nv, int T, int W);
 int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtensorMap& tmap,
                  float2* vis_out, int* status, cudaStream_t s);
 int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* ysorted,

@@ -81,14 +81,6 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     case 6: return F<6>(__VA_ARGS__);                      \
     case 7: return F<7>(__VA_ARGS__);                      \
     case 8: return F<8>(__VA_ARGS__);                      \
-    case 9: return F<9>(__VA_ARGS__);                      \
-    case 10: return F<10>(__VA_ARGS__);                    \
-    case 11: return F<11>(__VA_ARGS__);                    \
-    case 12: return F<12>(__VA_ARGS__);                    \
-    case 13: return F<13>(__VA_ARGS__);                    \
-    case 14: return F<14>(__VA_ARGS__);                    \
-    case 15: return F<15>(__VA_ARGS__);                    \
-    case 16: return F<16>(__VA_ARGS__);                    \
     default:                                               \
       ::fr::set_error("kernel support %d unsupported", W); \
       return FR_EUNSUPPORTED;                              \

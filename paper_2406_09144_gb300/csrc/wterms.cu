@@ -10,25 +10,25 @@
 
 namespace fr {
 
-// float2 stride between the term tiles of degrid_terms_kernel (a multiple of 128 bytes)
-__host__ __device__ constexpr int terms_tile_stride(int W) {
-  return ((TILE + W - 1) * ((TILE + W) & ~1) + 15) & ~15;
-}
+// Term grids of the degridder are interleaved: G[v][u][t] for t < T (the term count rounded up
+// to even, the padding term zero), so one 3-D TMA box brings every term of a tile and a thread
+// reads two terms of a cell with one 16-byte shared load.
+__host__ __device__ constexpr int terms_padded(int nterms) { return (nterms + 1) & ~1; }
 
-// Degridder for the small-w expansion: all N term grids are resident (stacked rows [N * Nv][Nu]),
-// one CTA per work item stages the item's tile of every term with N TMA copies on one
-// mbarrier, and each thread evaluates its visibility's separable kernel once and combines the N
-// interpolations with the weights (-i a)^n before the final phase and scatter.
-template <int W>
+// Degridder for the small-w expansion: one CTA per work item stages the item's tile of all T
+// term grids with one TMA copy; each thread evaluates its visibility's separable kernel once,
+// interpolates all terms and combines them with the weights (-i a)^t by Horner's rule before the
+// final phase and scatter.
+template <int W, int T>
 __global__ void __launch_bounds__(256) degrid_terms_kernel(const __grid_constant__ CUtensorMap tmap,
                                                            const int4* __restrict__ items,
-                                                           MetaPtrs m, EsKernel kern, int nterms,
-                                                           int Nv, float2* __restrict__ vis_out,
+                                                           MetaPtrs m, EsKernel kern,
+                                                           float2* __restrict__ vis_out,
                                                            int* status) {
   constexpr int BU = TILE + W - 1;
   constexpr int BV = (TILE + W - 1 + 1) & ~1;
-  constexpr int TS = terms_tile_stride(W);  // 128-byte aligned TMA destinations
-  extern __shared__ __align__(128) float2 tiles[];  // [nterms][TS]
+  constexpr int H = T / 2;                                      // float4 per cell
+  extern __shared__ __align__(128) float4 tile[];               // [BU][BV][H]
   __shared__ __align__(8) uint64_t mbar;
   const int4 it = items[blockIdx.x];
   const int tu = it.z >> 16, tv = it.z & 0xffff;
@@ -37,20 +37,19 @@ __global__ void __launch_bounds__(256) degrid_terms_kernel(const __grid_constant
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"((uint32_t)(BU * BV * sizeof(float2)) * (uint32_t)nterms)
+                 "r"((uint32_t)(BU * BV * T * sizeof(float2)))
                  : "memory");
-    for (int n = 0; n < nterms; ++n)
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-          "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tiles + n * TS)),
-          "l"((uint64_t)&tmap), "r"(2 * TILE * tu), "r"(n * Nv + TILE * tv), "r"(bar)
-          : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(tile)),
+        "l"((uint64_t)&tmap), "r"(0), "r"(TILE * tu), "r"(TILE * tv), "r"(bar)
+        : "memory");
   }
   __syncthreads();
   if (!mbar_wait_bounded(bar, 0)) {
     if (threadIdx.x == 0) {
       atomicOr(status, ST_TIMEOUT);
-      mbar_wait_bounded(bar, 0);  // let the copies in flight land before the CTA exits
+      mbar_wait_bounded(bar, 0);  // let the copy in flight land before the CTA exits
     }
     return;
   }
@@ -63,22 +62,34 @@ __global__ void __launch_bounds__(256) degrid_terms_kernel(const __grid_constant
     kernel_weights<W>(kern, m.du[i], ku);
     kernel_weights<W>(kern, m.dv[i], kv);
     const float a = m.dw[i];
-    float2 acc = make_float2(0.f, 0.f);
-    for (int n = 0; n < nterms; ++n) {
-      const float2* tile = tiles + n * TS;
-      float2 sn = make_float2(0.f, 0.f);
+    float2 sn[T];
 #pragma unroll
-      for (int b = 0; b < W; ++b) {
-        const float2* row = tile + (rv + b) * BV + ru;
-        float2 ra = make_float2(0.f, 0.f);
+    for (int t = 0; t < T; ++t) sn[t] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < W; ++c) ra = ffma2(make_float2(ku[c], ku[c]), row[c], ra);
-        sn = ffma2(make_float2(kv[b], kv[b]), ra, sn);
+    for (int b = 0; b < W; ++b) {
+      const float4* row = tile + ((rv + b) * BV + ru) * H;
+      float2 ra[T];
+#pragma unroll
+      for (int t = 0; t < T; ++t) ra[t] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const float2 k2 = make_float2(ku[c], ku[c]);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          const float4 q = row[c * H + h];
+          ra[2 * h] = ffma2(k2, make_float2(q.x, q.y), ra[2 * h]);
+          ra[2 * h + 1] = ffma2(k2, make_float2(q.z, q.w), ra[2 * h + 1]);
+        }
       }
-      const float2 t = rot_pow(sn, n, a, -1);
-      acc.x += t.x;
-      acc.y += t.y;
+      const float2 k2 = make_float2(kv[b], kv[b]);
+#pragma unroll
+      for (int t = 0; t < T; ++t) sn[t] = ffma2(k2, ra[t], sn[t]);
     }
+    // sum_t (-i a)^t sn[t] by Horner's rule; (-i a) (x + i y) = a y - i a x
+    float2 acc = sn[T - 1];
+#pragma unroll
+    for (int t = T - 2; t >= 0; --t)
+      acc = make_float2(fmaf(a, acc.y, sn[t].x), fmaf(-a, acc.x, sn[t].y));
     // exp(-2 pi i w t_c)
     const float f = (float)(int)m.ph[i] * 2.3283064365386963e-10f;
     float s, c;
@@ -88,6 +99,34 @@ __global__ void __launch_bounds__(256) degrid_terms_kernel(const __grid_constant
     if (pm >> 31) acc.y = -acc.y;
     vis_out[pm & 0x7fffffffu] = acc;
   }
+}
+
+int make_tmap_terms(CUtensorMap* m, float2* grid, int Nu, int Nv, int T, int W) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      set_error("cuTensorMapEncodeTiled unavailable");
+      return FR_ECUDA;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  // G[v][u][t]: x = the T terms of a cell (2 floats each), y = u, z = v
+  cuuint64_t dims[3] = {(cuuint64_t)2 * T, (cuuint64_t)Nu, (cuuint64_t)Nv};
+  cuuint64_t strides[2] = {(cuuint64_t)T * sizeof(float2), (cuuint64_t)Nu * T * sizeof(float2)};
+  cuuint32_t box[3] = {(cuuint32_t)(2 * T), (cuuint32_t)box_v(W), (cuuint32_t)box_u(W)};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)grid, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (term grids) failed (%d)", (int)r);
+    return FR_ECUDA;
+  }
+  return FR_OK;
 }
 
 // Gridder for the small-w expansion: one pass spreads every visibility into NC <=
@@ -284,23 +323,40 @@ __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
   }
 }
 
+template <int W, int T>
+static int launch_degrid_terms_t(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
+                                 const CUtensorMap& tmap, float2* vis_out, int* status,
+                                 cudaStream_t s) {
+  MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
+  constexpr size_t smem = (size_t)(TILE + W - 1) * ((TILE + W) & ~1) * T * sizeof(float2);
+  static_assert(smem <= DEGRID_TERMS_SMEM, "term tile exceeds the shared-memory budget");
+  static bool attr = false;
+  if (!attr) {
+    FR_CUDA_TRY(cudaFuncSetAttribute(degrid_terms_kernel<W, T>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  degrid_terms_kernel<W, T><<<(unsigned)n, 256, smem, s>>>(tmap, lay.items + i0, m, geo.kern,
+                                                           vis_out, status);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
 template <int W>
 static int launch_degrid_terms(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
                                const CUtensorMap& tmap, float2* vis_out, int* status,
                                cudaStream_t s) {
-  MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
-  const size_t smem = (size_t)geo.nterms * terms_tile_stride(W) * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    FR_CUDA_TRY(cudaFuncSetAttribute(degrid_terms_kernel<W>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     DEGRID_TERMS_SMEM));
-    attr = true;
+  switch (terms_padded(geo.nterms)) {
+    case 2: return launch_degrid_terms_t<W, 2>(geo, lay, i0, n, tmap, vis_out, status, s);
+    case 4: return launch_degrid_terms_t<W, 4>(geo, lay, i0, n, tmap, vis_out, status, s);
+    case 6: return launch_degrid_terms_t<W, 6>(geo, lay, i0, n, tmap, vis_out, status, s);
+    case 8: return launch_degrid_terms_t<W, 8>(geo, lay, i0, n, tmap, vis_out, status, s);
+    case 10: return launch_degrid_terms_t<W, 10>(geo, lay, i0, n, tmap, vis_out, status, s);
+    case 12: return launch_degrid_terms_t<W, 12>(geo, lay, i0, n, tmap, vis_out, status, s);
+    default:
+      set_error("small-w expansion with %d terms unsupported", geo.nterms);
+      return FR_EUNSUPPORTED;
   }
-  degrid_terms_kernel<W><<<(unsigned)n, 256, smem, s>>>(tmap, lay.items + i0, m, geo.kern,
-                                                        geo.nterms, geo.Nv, vis_out, status);
-  FR_LAUNCHED();
-  return FR_OK;
 }
 
 template <int W, int NC>
@@ -332,8 +388,13 @@ static int launch_grid_terms(const Geometry& geo, const VisLayout& lay, int64_t 
 }
 
 bool degrid_terms_fits(const Geometry& geo) {
-  return (size_t)geo.nterms * terms_tile_stride(geo.kern.W) * sizeof(float2) <= DEGRID_TERMS_SMEM;
+  const int W = geo.kern.W;
+  return geo.nterms >= 1 && geo.nterms <= 12 &&
+         (size_t)(TILE + W - 1) * ((TILE + W) & ~1) * terms_padded(geo.nterms) * sizeof(float2) <=
+             DEGRID_TERMS_SMEM;
 }
+
+int term_grid_count(const Geometry& geo) { return terms_padded(geo.nterms); }
 
 int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtensorMap& tmap,
                  float2* vis_out, int* status, cudaStream_t s) {
