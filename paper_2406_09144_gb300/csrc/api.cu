@@ -419,7 +419,6 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
 static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Workspace* w,
                     const float2* vis, int apply_weights, float* dirty, float2* grid, float2* b1,
                     float2* ybuf, cudaStream_t s, bool* grid_zero) {
-  FR_TRY(grid_prepare(geo, lay, vis, apply_weights, ybuf, s));
   const size_t img = (size_t)geo.nx * geo.ny;
   if (w && use_term_grids(geo)) {
     // small-w expansion: one spreading pass fills every term grid, then each term is transformed
@@ -433,7 +432,7 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
         continue;
       }
       w->terms_g_zero = false;
-      FR_TRY(grid_terms(geo, lay, g, ybuf, w->grid_terms_g, s));
+      FR_TRY(grid_terms(geo, lay, g, vis, apply_weights, w->grid_terms_g, s));
       PlaneArgs a = plane_args(geo, lay, g, 0);
       FR_TRY(grid_postpass_terms(a, geo.nterms, w->grid_terms_g, plane, w->b1g_terms,
                                  (size_t)geo.nx * geo.Nv, dirty + g * img, pl->tw[ilog2(geo.Nu)],
@@ -442,6 +441,7 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
     }
     return FR_OK;
   }
+  FR_TRY(grid_prepare(geo, lay, vis, apply_weights, ybuf, s));
   if (!*grid_zero) FR_CUDA_TRY(cudaMemsetAsync(grid, 0, (size_t)geo.Nu * geo.Nv * sizeof(float2), s));
   *grid_zero = true;
   for (int g = 0; g < lay.ngroups; ++g) {

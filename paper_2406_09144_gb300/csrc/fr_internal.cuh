@@ -274,8 +274,8 @@ int term_grid_count(const Geometry& geo);  // T: terms per cell of the interleav
 int make_tmap_terms(CUtensorMap* m, float2* grid, int Nu, int Nv, int T, int W);
 int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtensorMap& tmap,
                  float2* vis_out, int* status, cudaStream_t s);
-int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* ysorted,
-               float2* grid_terms, cudaStream_t s);
+int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* vis,
+               int apply_weights, float2* grid_terms, cudaStream_t s);
 int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const float2* ysorted,
                float2* grid, cudaStream_t s);
 int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, int apply_weights,

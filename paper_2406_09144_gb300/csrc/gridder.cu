@@ -1269,22 +1269,8 @@ struct GridPrepArgs {
 __global__ void grid_prepare_kernel(GridPrepArgs a) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t pm = a.perm[i];
-    float2 v = a.vis ? a.vis[pm & 0x7fffffffu] : make_float2(1.f, 0.f);
-    if (pm >> 31) v.y = -v.y;
-    if (a.apply_weights) {
-      const float w = a.wgt[i];
-      v.x *= w;
-      v.y *= w;
-    }
-    if (a.wterm) {
-      // exp(+2 pi i w t_c)
-      const float f = (float)(int)a.ph[i] * 2.3283064365386963e-10f;
-      float s, c;
-      sincospif(2.f * f, &s, &c);
-      v = make_float2(v.x * c - v.y * s, v.x * s + v.y * c);
-    }
-    a.y[i] = v;
+    a.y[i] = gridding_input(a.vis, a.perm[i], a.apply_weights ? a.wgt[i] : 1.f,
+                            a.wterm ? a.ph[i] : 0u, a.wterm != 0);
   }
 }
 

@@ -74,6 +74,24 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   return *reinterpret_cast<float2*>(&r);
 }
 
+// Gridding input of the visibility at sorted position i with user-order value vis[pm & 0x7fffffff]
+// (vis null: ones): conjugated when the conjugate-flip bit is set, times the weight `w`, times
+// exp(+2 pi i w t_c) with frac(w t_c) = ph / 2^32 when `wterm`.
+__device__ __forceinline__ float2 gridding_input(const float2* vis, uint32_t pm, float w,
+                                                 uint32_t ph, bool wterm) {
+  float2 v = vis ? vis[pm & 0x7fffffffu] : make_float2(1.f, 0.f);
+  if (pm >> 31) v.y = -v.y;
+  v.x *= w;
+  v.y *= w;
+  if (wterm) {
+    const float f = (float)(int)ph * 2.3283064365386963e-10f;
+    float s, c;
+    sincospif(2.f * f, &s, &c);
+    v = make_float2(v.x * c - v.y * s, v.x * s + v.y * c);
+  }
+  return v;
+}
+
 #define FR_W_DISPATCH(W, F, ...)                           \
   switch (W) {                                             \
     case 4: return F<4>(__VA_ARGS__);                      \

@@ -54,14 +54,29 @@ __global__ void __launch_bounds__(256) degrid_terms_kernel(const __grid_constant
     return;
   }
   const int end = it.x + it.y;
+  // the next visibility's metadata is loaded while the current one is interpolated
+  uint32_t n_cell = 0, n_ph = 0, n_pm = 0;
+  float n_du = 0.f, n_dv = 0.f, n_a = 0.f;
+  auto fetch = [&](int j) {
+    if (j < end) {
+      n_cell = m.cell[j];
+      n_du = m.du[j];
+      n_dv = m.dv[j];
+      n_a = m.dw[j];
+      n_ph = m.ph[j];
+      n_pm = m.perm[j];
+    }
+  };
+  fetch(it.x + threadIdx.x);
   for (int i = it.x + threadIdx.x; i < end; i += blockDim.x) {
-    const uint32_t cell = m.cell[i];
+    const uint32_t cell = n_cell, ph = n_ph, pm = n_pm;
+    const float du = n_du, dv = n_dv, a = n_a;
+    fetch(i + blockDim.x);
     const int ru = (int)(cell >> 18) - tu * TILE;
     const int rv = (int)((cell >> 4) & 0x3fff) - tv * TILE;
     float ku[W], kv[W];
-    kernel_weights<W>(kern, m.du[i], ku);
-    kernel_weights<W>(kern, m.dv[i], kv);
-    const float a = m.dw[i];
+    kernel_weights<W>(kern, du, ku);
+    kernel_weights<W>(kern, dv, kv);
     float2 sn[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) sn[t] = make_float2(0.f, 0.f);
@@ -91,11 +106,10 @@ __global__ void __launch_bounds__(256) degrid_terms_kernel(const __grid_constant
     for (int t = T - 2; t >= 0; --t)
       acc = make_float2(fmaf(a, acc.y, sn[t].x), fmaf(-a, acc.x, sn[t].y));
     // exp(-2 pi i w t_c)
-    const float f = (float)(int)m.ph[i] * 2.3283064365386963e-10f;
+    const float f = (float)(int)ph * 2.3283064365386963e-10f;
     float s, c;
     sincospif(2.f * f, &s, &c);
     acc = make_float2(acc.x * c + acc.y * s, acc.y * c - acc.x * s);
-    const uint32_t pm = m.perm[i];
     if (pm >> 31) acc.y = -acc.y;
     vis_out[pm & 0x7fffffffu] = acc;
   }
@@ -162,8 +176,9 @@ constexpr size_t grid_terms_smem_bytes(int nc) {
 
 template <int W, int NC>
 __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
-    const int4* __restrict__ items, MetaPtrs m, EsKernel kern, int t0,
-    const float2* __restrict__ y, float2* __restrict__ grid_terms, int Nu, int Nv) {
+    const int4* __restrict__ items, MetaPtrs m, const float* __restrict__ wgt, EsKernel kern,
+    int t0, const float2* __restrict__ vis, int apply_weights, float2* __restrict__ grid_terms,
+    int Nu, int Nv) {
   using L = TermsLanes<W>;
   constexpr int BU = TILE + W - 1;
   constexpr int BV = (TILE + W - 1 + 1) & ~1;
@@ -243,10 +258,10 @@ __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
       for (int t = 0; t < NC; ++t) acc[t][k] = ffma2(gg, vt[t], acc[t][k]);
     }
   };
-  // the next batch's metadata is loaded while the current batch is processed
-  uint32_t n_cell = 0;
-  float n_du = 0.f, n_dv = 0.f, n_a = 0.f;
-  float2 n_y = make_float2(0.f, 0.f);
+  // the next batch's metadata is loaded while the current batch is processed; the gridding
+  // input (weight, conjugate flip, centring phase) is formed here from the user-order values
+  uint32_t n_cell = 0, n_pm = 0, n_ph = 0;
+  float n_du = 0.f, n_dv = 0.f, n_a = 0.f, n_w = 1.f;
   auto fetch = [&](int base) {
     if (base + lane < s1) {
       const int i = it.x + base + lane;
@@ -254,18 +269,20 @@ __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
       n_du = m.du[i];
       n_dv = m.dv[i];
       n_a = m.dw[i];
-      n_y = y[i];
+      n_pm = m.perm[i];
+      n_ph = m.ph[i];
+      if (apply_weights) n_w = wgt[i];
     }
   };
   fetch(s0);
   for (int base = s0; base < s1; base += 32) {
     const int nb = min(32, s1 - base);
-    const uint32_t cell = n_cell;
-    const float du = n_du, dv = n_dv, a = n_a;
-    const float2 yv = n_y;
+    const uint32_t cell = n_cell, pm = n_pm, ph = n_ph;
+    const float du = n_du, dv = n_dv, a = n_a, wv = n_w;
     fetch(base + 32);
     int org = -2;
     if (lane < nb) {
+      const float2 yv = gridding_input(vis, pm, wv, ph, true);
       float2 val = rot_pow(yv, t0, a, 1);  // y (i a)^t0, then one factor i a per term
 #pragma unroll
       for (int t = 0; t < NC; ++t) {
@@ -361,7 +378,8 @@ static int launch_degrid_terms(const Geometry& geo, const VisLayout& lay, int64_
 
 template <int W, int NC>
 static int launch_grid_terms_nc(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
-                                int t0, const float2* y, float2* grid_terms, cudaStream_t s) {
+                                int t0, const float2* vis, int apply_weights, float2* grid_terms,
+                                cudaStream_t s) {
   MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
   constexpr size_t smem = grid_terms_smem_bytes<W>(NC);
   static bool attr = false;
@@ -371,19 +389,20 @@ static int launch_grid_terms_nc(const Geometry& geo, const VisLayout& lay, int64
     attr = true;
   }
   grid_terms_kernel<W, NC><<<(unsigned)n, TERMS_WARPS * 32, smem, s>>>(
-      lay.items + i0, m, geo.kern, t0, y, grid_terms, geo.Nu, geo.Nv);
+      lay.items + i0, m, lay.wgt, geo.kern, t0, vis, apply_weights, grid_terms, geo.Nu, geo.Nv);
   FR_LAUNCHED();
   return FR_OK;
 }
 
 template <int W>
 static int launch_grid_terms(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
-                             int t0, int nc, const float2* y, float2* grid_terms, cudaStream_t s) {
+                             int t0, int nc, const float2* vis, int apply_weights,
+                             float2* grid_terms, cudaStream_t s) {
   switch (nc) {
-    case 1: return launch_grid_terms_nc<W, 1>(geo, lay, i0, n, t0, y, grid_terms, s);
-    case 2: return launch_grid_terms_nc<W, 2>(geo, lay, i0, n, t0, y, grid_terms, s);
-    case 3: return launch_grid_terms_nc<W, 3>(geo, lay, i0, n, t0, y, grid_terms, s);
-    default: return launch_grid_terms_nc<W, 4>(geo, lay, i0, n, t0, y, grid_terms, s);
+    case 1: return launch_grid_terms_nc<W, 1>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, s);
+    case 2: return launch_grid_terms_nc<W, 2>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, s);
+    case 3: return launch_grid_terms_nc<W, 3>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, s);
+    default: return launch_grid_terms_nc<W, 4>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, s);
   }
 }
 
@@ -408,8 +427,8 @@ int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtenso
   FR_W_DISPATCH(geo.kern.W, launch_degrid_terms, geo, lay, i0, i1 - i0, tmap, vis_out, status, s);
 }
 
-int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* ysorted,
-               float2* grid_terms, cudaStream_t s) {
+int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* vis,
+               int apply_weights, float2* grid_terms, cudaStream_t s) {
   if (!lay.presorted) {
     set_error("internal: the multi-term gridder needs origin-ordered work items");
     return FR_EUNSUPPORTED;
@@ -419,12 +438,16 @@ int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* y
   if (i1 <= i0) return FR_OK;
   for (int t0 = 0; t0 < geo.nterms; t0 += TERMS_PER_PASS) {
     const int nc = std::min(TERMS_PER_PASS, geo.nterms - t0);
-    // each band cell of every term written once; per visit: metadata + weighted visibility
+    // each band cell of every term written once; per visit: metadata, perm, phase, weight and
+    // the user-order visibility
     ProfScope ps(PC_GRID, s,
-                 nc * band_cells(lay) * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 8.0));
+                 nc * band_cells(lay) * 8.0 +
+                     (double)lay.plane_visits[q] *
+                         (meta_bytes(geo) + 16.0 + (apply_weights ? 4.0 : 0.0)));
     int r;
     auto launch = [&](int W) -> int {
-      FR_W_DISPATCH(W, launch_grid_terms, geo, lay, i0, i1 - i0, t0, nc, ysorted, grid_terms, s);
+      FR_W_DISPATCH(W, launch_grid_terms, geo, lay, i0, i1 - i0, t0, nc, vis, apply_weights,
+                    grid_terms, s);
     };
     if ((r = launch(geo.kern.W))) return r;
   }
