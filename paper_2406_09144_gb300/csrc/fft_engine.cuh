@@ -22,7 +22,9 @@ struct FftCfg {
   static constexpr int NT = (B * L) / 16;     // threads: 16 points each
   static constexpr int LP = spad_len(L) + 1;  // odd stride between sequences
   static constexpr size_t SMEM = size_t(B) * LP * sizeof(float2);
-  static constexpr int MINB = NT >= 1024 ? 1 : 2;
+  // CTAs per SM the register budget is sized for: four at L = 2048 (64 registers, no spills)
+  static constexpr int MINB = NT >= 1024 ? 1 : (NT >= 512 || LOG2L < 11 ? 2 : 4);
+  static constexpr int MINB_SUM = NT >= 1024 ? 1 : 2;  // summing and two-transform passes
 };
 
 constexpr int ns_before(int log2l, int st) {
@@ -101,7 +103,8 @@ struct SeqView {
 //   double store(int seq, int o, SeqView v)   o < nout(); per-thread results are summed
 //   void finish(int seq0, double acc)
 template <int LOG2L, int DIR, int DIR2, class Op>
-__global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB)
+__global__ void __launch_bounds__(FftCfg<LOG2L>::NT,
+                                  Op::TWO ? FftCfg<LOG2L>::MINB_SUM : FftCfg<LOG2L>::MINB)
     fft_pass_kernel(Op op, const float2* __restrict__ tw) {
   using C = FftCfg<LOG2L>;
   constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
@@ -168,7 +171,7 @@ int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
 //   float2 load(int t, int seq, int i); float value(int t, int seq, int o, SeqView v);
 //   void store(int seq, int o, float sum)
 template <int LOG2L, int DIR, class Op>
-__global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB)
+__global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB_SUM)
     fft_pass_sum_kernel(Op op, const float2* __restrict__ tw) {
   using C = FftCfg<LOG2L>;
   constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
