@@ -105,6 +105,29 @@ def test_small_w_expansion_matches_oracle(wc, nchan, per):
     assert rel(plan.degrid(dev(pt)).cpu().numpy(), refp) <= EPS
 
 
+@pytest.mark.parametrize("wc,eps,min_terms,W", [(0.12, 1e-5, 5, 7), (0.02, 1e-3, 1, 5),
+                                                 (0.02, 1e-6, 1, 8)])
+def test_small_w_expansion_term_counts_and_supports(wc, eps, min_terms, W):
+    """Expansions that need two gridding passes (more than 4 terms, padded interleaved term
+    grids when the count is odd), and the smallest and largest kernel supports."""
+    obs = synth.random_observation(1100, 1, 64, 32, 2e-3, seed=46, wmax_cycles=wc)
+    plan = make_plan(obs, eps=eps)
+    info = plan.info()
+    assert info["dw"] == 0.0 and info["support"] == W
+    assert min_terms <= info["wplanes_max"] < W + 1
+    tol = max(eps, 2e-6)  # FP32 arithmetic floors the achievable error near 1e-6
+    sky = synth.random_skies(1, 64, 32, seed=14)
+    ref = oracle.degrid(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize)
+    assert rel(plan.degrid(dev(sky)).cpu().numpy(), ref) <= tol
+    vis = synth.complex_gaussian(plan.vis_shape, seed=15)
+    refd = oracle.grid(vis, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, 64, 32,
+                       weights=obs.weights.astype(np.float32), nsky=1)
+    got = plan.grid(dev(vis, torch.complex64)).cpu().numpy()
+    assert rel(got, refd) <= tol
+    # a second call leaves the same result (the term grids are cleared by the post-pass)
+    assert rel(plan.grid(dev(vis, torch.complex64)).cpu().numpy(), got) <= 1e-6
+
+
 def test_grid_twice_is_identical_workspace_stays_clean():
     obs = synth.random_observation(900, 1, 32, 32, 2e-3, seed=33, wmax_cycles=2.0)
     plan = make_plan(obs)
