@@ -37,6 +37,12 @@ __constant__ float c_inv_fact[MAX_TERMS] = {
     1.f / 3628800.f, 1.f / 39916800.f, 1.f / 479001600.f, 1.f / 6227020800.f, 1.f / 87178291200.f,
     1.f / 1307674368000.f};
 
+// 1 / k
+__constant__ float c_recip[MAX_TERMS] = {0.f,       1.f,        1.f / 2.f,  1.f / 3.f,
+                                         1.f / 4.f, 1.f / 5.f,  1.f / 6.f,  1.f / 7.f,
+                                         1.f / 8.f, 1.f / 9.f,  1.f / 10.f, 1.f / 11.f,
+                                         1.f / 12.f, 1.f / 13.f, 1.f / 14.f, 1.f / 15.f};
+
 // tau^n / n! for the small-w expansion, tau = tq * 2^-30 = (t - t_c) / t_half
 __device__ __forceinline__ float taylor_factor(int32_t tq, int n, float inv_fact) {
   const float tau = (float)tq * 9.313225746154785e-10f;
@@ -107,6 +113,45 @@ struct D2Op : OpBase {
   __device__ double store(int q, int o, SeqView s) const {
     const int u = ub0 + o;
     grid[blockIdx.y * grid_stride + (size_t)(vb0 + q) * Nu + u] = s[u];
+    return 0.0;
+  }
+};
+
+// D1 for all expansion terms from one load: raw element (sky * corr, tau), term t's input
+// sky * corr * tau^t / t! built by one multiply per term, half plane of term t at
+// b1t + t * b1t_stride.
+struct D1TermsOp {
+  static constexpr bool TRANSPOSED = true;
+  const float* sky;
+  const float* corr;
+  const int32_t* tq;
+  float2* b1t;  // [band v][nx] per term
+  size_t b1t_stride;
+  int nterm;
+  int nx, ny, Nv;
+  int vb0, nvb;
+  __host__ __device__ int nseq() const { return nx; }
+  __host__ __device__ int nout() const { return nvb; }
+  __device__ int nterms() const { return nterm; }
+  __device__ float2 load(int jx, int i) const {
+    const int hy = ny >> 1;
+    int jy;
+    if (i < hy)
+      jy = i + hy;
+    else if (i >= Nv - hy)
+      jy = i - Nv + hy;
+    else
+      return make_float2(0.f, 0.f);
+    const int pix = jx * ny + jy;
+    return make_float2(__ldg(&sky[pix]) * __ldg(&corr[pix]),
+                       (float)__ldg(&tq[pix]) * 9.313225746154785e-10f);
+  }
+  __device__ float2 prep(int t, float2& raw) const {
+    if (t > 0) raw.x *= raw.y * c_recip[t];
+    return make_float2(raw.x, 0.f);
+  }
+  __device__ double store(int t, int jx, int o, SeqView s) const {
+    b1t[t * b1t_stride + (size_t)o * nx + jx] = s[vb0 + o];
     return 0.0;
   }
 };
@@ -247,7 +292,8 @@ static int d2(int lg, const D2Op& op, const float2* tw, cudaStream_t s) { FR_LOG
 static int g1(int lg, const G1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1, op, tw, s); }
 static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2, op, tw, s); }
 template <int LG>
-static int run_d1t(const D1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, nt, tw, s); }
+static int run_d1m(const D1TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass_multi<LG, -1>(op, tw, s); }
+static int d1m(int lg, const D1TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1m, op, tw, s); }
 template <int LG>
 static int run_d2i(const D2TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, 1, tw, s); }
 static int d2i(int lg, const D2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2i, op, tw, s); }
@@ -255,7 +301,6 @@ template <int LG>
 static int run_g1t(const G1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, nt, tw, s); }
 template <int LG>
 static int run_g2t(const G2TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass_sum<LG, 1>(op, tw, s); }
-static int d1t(int lg, const D1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1t, op, nt, tw, s); }
 static int g1t(int lg, const G1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1t, op, nt, tw, s); }
 static int g2t(int lg, const G2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2t, op, tw, s); }
 
@@ -348,25 +393,22 @@ int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float
   const int nvb = a.bv1 - a.bv0 + 1, nub = a.bu1 - a.bu0 + 1;
   if (nvb <= 0 || nub <= 0 || nterms <= 0) return FR_OK;
   const double img = (double)a.nx * a.ny, half = (double)a.nx * nvb, full = (double)nvb * nub;
-  D1Op o1;
+  D1TermsOp o1;
   o1.vb0 = a.bv0;
   o1.nvb = nvb;
   o1.sky = sky;
   o1.corr = a.corr;
   o1.tq = a.tq;
-  o1.k64 = 0;
-  o1.wterm = 1;
-  o1.taylor = 1;
-  o1.n = 0;
   o1.b1t = b1;
   o1.b1t_stride = b1_stride;
+  o1.nterm = nterms;
   o1.nx = a.nx;
   o1.ny = a.ny;
   o1.Nv = a.Nv;
   {
-    // per term: sky + corr + tq in (cached after the first term), half plane out
+    // sky + corr + tq in once, one half plane out per term
     ProfScope ps(PC_FFT_ROWS, s, img * 12.0 + nterms * half * 8.0);
-    FR_TRY(d1t(ilog2(a.Nv), o1, nterms, twv, s));
+    FR_TRY(d1m(ilog2(a.Nv), o1, twv, s));
   }
   D2TermsOp o2;
   o2.b1t = b1;
