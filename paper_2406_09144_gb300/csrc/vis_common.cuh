@@ -74,12 +74,11 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   return *reinterpret_cast<float2*>(&r);
 }
 
-// Gridding input of the visibility at sorted position i with user-order value vis[pm & 0x7fffffff]
-// (vis null: ones): conjugated when the conjugate-flip bit is set, times the weight `w`, times
-// exp(+2 pi i w t_c) with frac(w t_c) = ph / 2^32 when `wterm`.
-__device__ __forceinline__ float2 gridding_input(const float2* vis, uint32_t pm, float w,
-                                                 uint32_t ph, bool wterm) {
-  float2 v = vis ? vis[pm & 0x7fffffffu] : make_float2(1.f, 0.f);
+// Gridding input from the user-order value v of a visibility: conjugated when the conjugate-flip
+// bit of pm is set, times the weight `w`, times exp(+2 pi i w t_c) with frac(w t_c) = ph / 2^32
+// when `wterm`.
+__device__ __forceinline__ float2 gridding_input_of(float2 v, uint32_t pm, float w, uint32_t ph,
+                                                    bool wterm) {
   if (pm >> 31) v.y = -v.y;
   v.x *= w;
   v.y *= w;
@@ -90,6 +89,12 @@ __device__ __forceinline__ float2 gridding_input(const float2* vis, uint32_t pm,
     v = make_float2(v.x * c - v.y * s, v.x * s + v.y * c);
   }
   return v;
+}
+
+// The same for the visibility vis[pm & 0x7fffffff] (vis null: ones).
+__device__ __forceinline__ float2 gridding_input(const float2* vis, uint32_t pm, float w,
+                                                 uint32_t ph, bool wterm) {
+  return gridding_input_of(vis ? vis[pm & 0x7fffffffu] : make_float2(1.f, 0.f), pm, w, ph, wterm);
 }
 
 #define FR_W_DISPATCH(W, F, ...)                           \
