@@ -231,7 +231,11 @@ struct G2Op : OpBase {
   int nx, ny, Nv;
   __host__ __device__ int nseq() const { return nx; }
   __host__ __device__ int nout() const { return ny; }
-  __device__ float2 load(int jx, int i) const { return b1[(size_t)jx * Nv + i]; }
+  int vb0, nvb;  // the half plane is zero outside the band columns: no loads there
+  __device__ float2 load(int jx, int i) const {
+    if (i < vb0 || i >= vb0 + nvb) return make_float2(0.f, 0.f);
+    return b1[(size_t)jx * Nv + i];
+  }
   __device__ double store(int jx, int jy, SeqView s) const {
     const int i = (jy - (ny >> 1) + Nv) & (Nv - 1);
     const float2 z = s[i];
@@ -265,7 +269,9 @@ struct G2TermsOp {
   __host__ __device__ int nseq() const { return nx; }
   __host__ __device__ int nout() const { return ny; }
   __device__ int nterms() const { return nterm; }
+  int vb0, nvb;  // the half planes are zero outside the band columns: no loads there
   __device__ float2 load(int t, int jx, int i) const {
+    if (i < vb0 || i >= vb0 + nvb) return make_float2(0.f, 0.f);
     return b1[t * b1_stride + (size_t)jx * Nv + i];
   }
   __device__ float value(int t, int jx, int jy, SeqView s) const {
@@ -382,8 +388,11 @@ int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, in
   o2.nx = a.nx;
   o2.ny = a.ny;
   o2.Nv = a.Nv;
+  o2.vb0 = a.bv0;
+  o2.nvb = nvb;
   ProfScope ps(PC_FFT_ROWS, s,
-               half * 8.0 + img * (4.0 + (a.wterm ? 4.0 : 0.0) + (accumulate ? 8.0 : 4.0)));
+               (double)a.nx * nvb * 8.0 +
+                   img * (4.0 + (a.wterm ? 4.0 : 0.0) + (accumulate ? 8.0 : 4.0)));
   return g2(ilog2(a.Nv), o2, twv, s);
 }
 
@@ -460,8 +469,10 @@ int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t gri
   o2.nx = a.nx;
   o2.ny = a.ny;
   o2.Nv = a.Nv;
-  // per term a half plane in; corr + tq in and the image out once
-  ProfScope ps(PC_FFT_ROWS, s, nterms * half * 8.0 + img * 12.0);
+  o2.vb0 = a.bv0;
+  o2.nvb = nvb;
+  // per term the band of a half plane in; corr + tq in and the image out once
+  ProfScope ps(PC_FFT_ROWS, s, nterms * (double)a.nx * nvb * 8.0 + img * 12.0);
   return g2t(ilog2(a.Nv), o2, twv, s);
 }
 
