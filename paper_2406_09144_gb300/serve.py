@@ -163,6 +163,61 @@ def summarize(reqs, wall_s: float) -> dict:
 
 
 # ------------------------------------------------------------------------------ GPU executor
+class CaptureGate:
+    """Keeps device-synchronising cleanup (freeing plans and graphs) apart from stream captures.
+
+    Freeing device memory synchronises the whole device, and a synchronisation while another
+    thread is capturing a CUDA graph invalidates that capture. Captures enter shared; cleanup
+    enters exclusive, waits for the captures in progress and holds new ones back meanwhile.
+    """
+
+    def __init__(self):
+        import threading
+        self._cv = threading.Condition()
+        self._capturing = 0
+        self._exclusive = False
+
+    def capture(self):
+        return _GateSection(self, exclusive=False)
+
+    def exclusive(self):
+        return _GateSection(self, exclusive=True)
+
+    def _enter(self, exclusive: bool):
+        with self._cv:
+            if exclusive:
+                while self._exclusive:
+                    self._cv.wait()
+                self._exclusive = True
+                while self._capturing:
+                    self._cv.wait()
+            else:
+                while self._exclusive:
+                    self._cv.wait()
+                self._capturing += 1
+
+    def _exit(self, exclusive: bool):
+        with self._cv:
+            if exclusive:
+                self._exclusive = False
+            else:
+                self._capturing -= 1
+            self._cv.notify_all()
+
+
+class _GateSection:
+    def __init__(self, gate: CaptureGate, exclusive: bool):
+        self.gate, self.ex = gate, exclusive
+
+    def __enter__(self):
+        self.gate._enter(self.ex)
+        return self
+
+    def __exit__(self, *exc):
+        self.gate._exit(self.ex)
+        return False
+
+
 class GpuExecutor:
     """Runs admitted jobs on their own CUDA streams; one captured CUDA graph per job call."""
 
@@ -184,6 +239,7 @@ class GpuExecutor:
         self.graveyard = []
         self.graveyard_bytes = 0
         self.graveyard_limit = 32 << 30
+        self.gate = CaptureGate()
 
     def _stream(self):
         with self.lock:
@@ -220,10 +276,14 @@ class GpuExecutor:
             call()  # eager: sizes the per-stream workspace before any capture
             if self.graphs:
                 g = torch.cuda.CUDAGraph()
-                # thread-local capture: other threads keep allocating and synchronising
-                g.capture_begin(capture_error_mode="thread_local")
-                call()
-                g.capture_end()
+                # thread-local capture: other threads keep building plans meanwhile; plan and
+                # graph destruction (device-synchronising) waits for the capture to end
+                with self.gate.capture():
+                    g.capture_begin(capture_error_mode="thread_local")
+                    try:
+                        call()
+                    finally:
+                        g.capture_end()
                 h["graph"] = g
         h.update(plan=plan, sky=sky, out=out, call=call)
         ev = torch.cuda.Event()
@@ -271,10 +331,11 @@ class GpuExecutor:
             self.streams.append(h["stream"])
 
     def close_finished(self):
-        for plan, _ in self.graveyard:
-            plan.close()
-        self.graveyard = []
-        self.graveyard_bytes = 0
+        with self.gate.exclusive():
+            for plan, _ in self.graveyard:
+                plan.close()
+            self.graveyard = []  # the graphs are released here too, inside the exclusive section
+            self.graveyard_bytes = 0
 
 
 def run_sequential(requests, device="cuda", eps=1e-5):

@@ -72,3 +72,61 @@ def test_request_larger_than_budget_is_refused():
     import pytest
     with pytest.raises(ValueError):
         Scheduler(FakeExecutor(), 1000, 2).run([_req(0, 256, 0.0)])
+
+
+def test_capture_gate_keeps_cleanup_apart_from_captures():
+    """Plan and graph destruction (device-synchronising) never overlaps a graph capture: the
+    exclusive section waits for captures in progress and holds new captures back."""
+    import threading
+    import time as _time
+    from paper_2406_09144_gb300.serve import CaptureGate
+
+    gate = CaptureGate()
+    log = []
+    lock = threading.Lock()
+
+    def note(x):
+        with lock:
+            log.append(x)
+
+    def capture(i, hold):
+        with gate.capture():
+            note(("cap+", i))
+            _time.sleep(hold)
+            note(("cap-", i))
+
+    def cleanup():
+        with gate.exclusive():
+            note(("free+", 0))
+            _time.sleep(0.05)
+            note(("free-", 0))
+
+    a = threading.Thread(target=capture, args=(1, 0.2))
+    b = threading.Thread(target=capture, args=(2, 0.2))
+    a.start()
+    b.start()
+    _time.sleep(0.05)  # both captures are in progress
+    c = threading.Thread(target=cleanup)
+    c.start()
+    _time.sleep(0.05)  # cleanup is now waiting; a new capture must wait behind it
+    d = threading.Thread(target=capture, args=(3, 0.01))
+    d.start()
+    for t in (a, b, c, d):
+        t.join(5)
+    active = 0
+    freeing = False
+    for kind, _ in log:
+        if kind == "cap+":
+            assert not freeing
+            active += 1
+        elif kind == "cap-":
+            active -= 1
+        elif kind == "free+":
+            assert active == 0
+            freeing = True
+        else:
+            freeing = False
+    assert [k for k, i in log if i == 3] == ["cap+", "cap-"]
+    assert log.index(("cap+", 3)) > log.index(("free-", 0))
+    # two captures ran concurrently
+    assert log.index(("cap+", 2)) < log.index(("cap-", 1)) or log.index(("cap+", 1)) < log.index(("cap-", 2))
