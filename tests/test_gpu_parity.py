@@ -275,6 +275,24 @@ def test_dropped_and_flagged_visibilities():
     assert rel(g, rg) <= EPS
 
 
+def test_all_visibilities_dropped():
+    """Degenerate plan: every footprint leaves the grid and is dropped. R gives zeros, R^dagger
+    a zero image, and the PSF (no weight) is zero."""
+    obs = synth.random_observation(64, 1, 32, 32, 2e-3, seed=47, wmax_cycles=1.0)
+    uvw = obs.uvw.copy()
+    lam = oracle.C_LIGHT / obs.freqs[0]
+    uvw[:, 0] = 0.499 / obs.pixsize * lam
+    from paper_2406_09144_gb300.binding import Plan
+    plan = Plan(uvw, obs.freqs, 32, 32, obs.pixsize, weights=obs.weights, eps=EPS, drop_oob=True)
+    assert plan.info()["nvis_dropped"] == 64
+    sky = synth.random_skies(1, 32, 32, seed=8)
+    assert np.all(plan.degrid(dev(sky)).cpu().numpy() == 0)
+    vis = dev(synth.complex_gaussian((64, 1), seed=9), torch.complex64)
+    assert np.all(plan.grid(vis).cpu().numpy() == 0)
+    _, psf, norm = plan.dirty_psf(want_dirty=False)
+    assert np.all(psf.cpu().numpy() == 0) and np.all(norm == 0)
+
+
 def test_single_visibility_at_origin():
     """A single visibility y at u = v = w = 0 grids to D_j = Re(y) / n_j (closed form)."""
     from paper_2406_09144_gb300.binding import Plan
@@ -317,4 +335,28 @@ def test_vla_full_size_sampled():
     w32 = obs.weights.astype(np.float32)
     refd = cdft.grid_at(y, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, 1024, 1024,
                         np.zeros(40, int), pix, weights=w32)
+    assert rel(d.reshape(-1)[pix], refd) <= 2 * EPS
+
+
+@pytest.mark.slow
+def test_meerkat_top_channel_full_size_sampled():
+    """Largest image the API takes (4096^2, 8192^2 grid) with the MeerKAT-like top channel:
+    w-stacking over 30 planes, 7,257,600 visibilities; sampled outputs against the FP64 direct
+    sums in the benchmark's launch configuration."""
+    obs = synth.observation("meerkat1")
+    plan = make_plan(obs, mfs=not obs.per_channel_sky)
+    assert plan.info()["wplanes_total"] > plan.info()["support"]
+    rng = np.random.default_rng(2)
+    sky = synth.sky_image(4096, 4096, seed=3)[None]
+    vis = plan.degrid(dev(sky)).cpu().numpy()
+    rows = rng.integers(0, obs.nrow, 120)
+    ref = cdft.degrid_at(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, rows,
+                         np.zeros(120, int))
+    assert rel(vis[rows, 0], ref) <= 2 * EPS
+    y = synth.complex_gaussian((obs.nrow, 1), seed=4)
+    d = plan.grid(dev(y, torch.complex64)).cpu().numpy()
+    pix = rng.integers(0, 4096 * 4096, 24)
+    w32 = obs.weights.astype(np.float32)
+    refd = cdft.grid_at(y, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, 4096, 4096,
+                        np.zeros(24, int), pix, weights=w32)
     assert rel(d.reshape(-1)[pix], refd) <= 2 * EPS

@@ -57,6 +57,16 @@ def test_plan_create_rejects_bad_sizes_without_gpu(lib):
     r = lib.fr_plan_create(bad.ctypes.data, 4, f.ctypes.data, 1, None, 64, 64, 1e-5, 1e-5, 1e-5,
                            0, None, ctypes.byref(h))
     assert r == -1 and b"not finite" in lib.fr_last_error()
+    # empty input: no rows, no channels, or an image below the 16-pixel minimum
+    r = lib.fr_plan_create(uvw.ctypes.data, 0, f.ctypes.data, 1, None, 64, 64, 1e-5, 1e-5, 1e-5,
+                           0, None, ctypes.byref(h))
+    assert r == -1 and not h.value
+    r = lib.fr_plan_create(uvw.ctypes.data, 4, f.ctypes.data, 0, None, 64, 64, 1e-5, 1e-5, 1e-5,
+                           0, None, ctypes.byref(h))
+    assert r == -1
+    r = lib.fr_plan_create(uvw.ctypes.data, 4, f.ctypes.data, 1, None, 8, 64, 1e-5, 1e-5, 1e-5,
+                           0, None, ctypes.byref(h))
+    assert r == -4
 
 
 @pytest.mark.parametrize("lg", list(range(1, 15)))
