@@ -10,7 +10,7 @@
  *              V_k = sum_j I_j / n_j exp(-2 pi i (u_k l_j + v_k m_j + w_k (n_j - 1)))
  *   R^dag N^-1 Eq. (clean), Sec. 3.2: weighted back-projection (dirty image), N^-1 = weights
  *              (Sec. 3.1.2), the adjoint of R under the real inner product (the sky is real)
- *   PSF *      Sec. 3.3.1: R^dag N^-1 R ~ convolution with the PSF, evaluated exactly (linear,
+ *   PSF *      Sec. 3.3.2: R^dag N^-1 R ~ convolution with the PSF, evaluated exactly (linear,
  *              not circular) by zero padding to 2nx x 2ny
  *   likelihood Eq. (ham) expanded with Eq. (clean): L(s) = 1/2 s^T (PSF * s) - s^T d,
  *              grad = PSF * s - d; the exact variant uses R^dag N^-1 R (Algorithm 1 major cycle)
@@ -63,7 +63,7 @@ typedef struct {
 #define FR_DROP_OOB 8u       /* drop visibilities whose kernel footprint leaves the grid instead of failing */
 #define FR_NO_PSF 16u        /* skip building the PSF (fr_psf_apply / approximate likelihood unavailable) */
 
-/* Build a plan (plan time, Sec. 3.3.3: done once per observation).
+/* Build a plan (plan time, Sec. 3.3.4: done once per observation).
  *   uvw      host float64 [nrow][3] metres
  *   freqs    host float64 [nchan] Hz, all > 0
  *   weights  host float32 [nrow][nchan] (N^-1 as visibility weights, Sec. 3.1.2), >= 0;
@@ -89,7 +89,7 @@ int fr_degrid(fr_plan_t plan, const float *sky, fr_cf32 *vis, void *stream);
  * dirty [nsky][nx][ny] (device, overwritten): D_j = Re sum_k w_k y_k exp(+2 pi i phase_kj) / n_j. */
 int fr_grid(fr_plan_t plan, const fr_cf32 *vis, int32_t apply_weights, float *dirty, void *stream);
 
-/* Dirty image I^D = R^dag N^-1 V (Algorithm 1, first step) and the PSF (Sec. 3.3.1).
+/* Dirty image I^D = R^dag N^-1 V (Algorithm 1, first step) and the PSF (Sec. 3.3.2).
  *   dirty    device [nsky][nx][ny] or NULL
  *   psf      device [nsky][2nx][2ny] or NULL; unnormalised PSF(a, b) = sum_k w_k
  *            cos(2 pi (u_k a dx + v_k b dy)) at w = 0, offset (a, b) stored at (a + nx, b + ny);
@@ -99,7 +99,7 @@ int fr_grid(fr_plan_t plan, const fr_cf32 *vis, int32_t apply_weights, float *di
 int fr_dirty_psf(fr_plan_t plan, const fr_cf32 *vis, float *dirty, float *psf, double *psf_norm,
                  void *stream);
 
-/* PSF convolution (Sec. 3.3.1): out = P^dag FFT^-1[FFT[PSF] . FFT[P sky]], i.e. the linear
+/* PSF convolution (Sec. 3.3.2): out = P^dag FFT^-1[FFT[PSF] . FFT[P sky]], i.e. the linear
  * convolution out(p) = sum_q PSF(p - q) sky(q) cropped to the image.
  *   sky, out  device [batch][nsky][nx][ny]; image b*nsky + s uses the PSF of image s.
  *   batch     >= 1 */
@@ -107,7 +107,7 @@ int fr_psf_apply(fr_plan_t plan, const float *sky, int32_t batch, float *out, vo
 
 /* Likelihood value and gradient (Eq. ham with Eq. clean, constants dropped):
  *   L_b = 1/2 s_b^T (A s_b) - s_b^T d_b,  grad_b = A s_b - d_b
- * with A = PSF * (exact == 0, Sec. 3.3.1) or A = R^dag N^-1 R (exact != 0, Algorithm 1).
+ * with A = PSF * (exact == 0, Sec. 3.3.2) or A = R^dag N^-1 R (exact != 0, Algorithm 1).
  *   sky, dirty, grad  device [batch][nsky][nx][ny]; grad may alias neither input
  *   value             host float64 [batch] (sum over the nsky images of element b); may be NULL
  * Reductions are FP64. Synchronises `stream` when value != NULL. */

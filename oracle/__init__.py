@@ -13,7 +13,7 @@ Sections and equations cited:
   Eq. (rime), Sec. 2       - measurement equation R
   Eq. (ham), Sec. 3.1.2    - likelihood Hamiltonian, N^-1 = visibility weights
   Eq. (clean), Sec. 3.2    - R^dagger N^-1 R I = R^dagger N^-1 V, dirty image, PSF
-  Sec. 3.3.1               - PSF convolution on a 2x padded grid
+  Sec. 3.3.2               - PSF convolution on a 2x padded grid
   Algorithm 1              - major-cycle residual d = I^D - R^dagger N^-1 R I
 
 Parity: every function is pinned by tests in tests/test_oracle_pins.py (closed

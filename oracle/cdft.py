@@ -89,7 +89,7 @@ def grid_at(vis, uvw, freqs, dl, dm, nx, ny, imgs, pix, weights=None, nsky=1, wt
 
 
 def psf_at(uvw, freqs, dl, dm, imgs, a, b, weights=None, nsky=1):
-    """PSF (Sec. 3.3.1, unnormalised, w = 0) at pixel offsets (a[i], b[i]) of image imgs[i]."""
+    """PSF (Sec. 3.3.2, unnormalised, w = 0) at pixel offsets (a[i], b[i]) of image imgs[i]."""
     lib = load()
     u, v, _ = (_f64(x) for x in uvw_to_wavelengths(uvw, freqs))
     wt = _f64(np.ones(u.shape) if weights is None else weights)

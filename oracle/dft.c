@@ -9,7 +9,7 @@
  *
  *   R       (Eq. rime, G = 1):  V_k = sum_j I_j / n_j exp(-2 pi i (u l + v m + w (n - 1)))
  *   R^dag N^-1 (Eq. clean):     D_j = Re sum_k y_k exp(+2 pi i (u l + v m + w (n - 1))) / n_j
- *   PSF (Sec. 3.2, 3.3.1):      P(a, b) = sum_k w_k cos(2 pi (u a dl + v b dm))
+ *   PSF (Sec. 3.2, 3.3.2):      P(a, b) = sum_k w_k cos(2 pi (u a dl + v b dm))
  *
  * u, v, w are given in wavelengths ([nrow][nchan], row-major), already scaled by nu / c.
  * Pixel (jx, jy) sits at l = (jx - nx/2) dl, m = (jy - ny/2) dm (integer division).

@@ -120,7 +120,7 @@ def grid(vis, uvw, freqs, dl, dm, nx, ny, weights=None, nsky=1, wterm=True, nter
 
 
 def psf(uvw, freqs, dl, dm, nx, ny, weights=None, nsky=1):
-    """Point spread function on the 2x padded grid (Sec. 3.2 and 3.3.1), neglecting wide-field
+    """Point spread function on the 2x padded grid (Sec. 3.2 and 3.3.2), neglecting wide-field
     effects (w = 0, 1/n = 1), unnormalised so that PSF * I equals R^dagger N^-1 R I at w = 0:
 
         PSF(a, b) = sum_k w_k cos(2 pi (u_k a dl + v_k b dm)),  a in [-nx, nx), b in [-ny, ny)
@@ -153,7 +153,7 @@ def psf(uvw, freqs, dl, dm, nx, ny, weights=None, nsky=1):
 
 def psf_apply(psf_img, sky):
     """Linear (non-circular) convolution of each sky with the PSF, cropped to the sky
-    (Sec. 3.3.1: the padded FFT convolution evaluates exactly this):
+    (Sec. 3.3.2: the padded FFT convolution evaluates exactly this):
 
         out_b(p) = sum_{q in sky} PSF(p - q) s_b(q)
 
@@ -180,7 +180,7 @@ def psf_apply(psf_img, sky):
 
 
 def likelihood(psf_img, sky, dirty):
-    """Likelihood in image space with the PSF approximation R^dagger N^-1 R ~ PSF * (Sec. 3.3.1):
+    """Likelihood in image space with the PSF approximation R^dagger N^-1 R ~ PSF * (Sec. 3.3.2):
     Eq. (ham) expanded with Eq. (clean) and constants dropped,
 
         L(s) = 1/2 s^T (PSF * s) - s^T d,    grad L = PSF * s - d.

@@ -6,7 +6,7 @@ With it:
     gridding kernel without weights;
   * Grid    d = R^dagger (N^-1) y (Eq. clean): grad_y = N^-1 R grad_d, i.e. the degridding kernel
     followed by the weights;
-  * PsfLikelihood / ExactLikelihood  L_b = 1/2 s_b.(A s_b) - s_b.d_b with A = PSF * (Sec. 3.3.1)
+  * PsfLikelihood / ExactLikelihood  L_b = 1/2 s_b.(A s_b) - s_b.d_b with A = PSF * (Sec. 3.3.2)
     or R^dagger N^-1 R: grad_s = (A s - d) * grad_L (A is self-adjoint), grad_d = -s * grad_L.
     The forward kernel already produces A s - d, so backward costs no extra launch.
 All arithmetic runs in the library's CUDA kernels through binding.Plan.

@@ -258,7 +258,7 @@ class Plan:
         return dirty, psf, norm
 
     def psf_apply(self, sky, out=None, stream=None):
-        """PSF convolution (Sec. 3.3.1): sky [batch, nsky, nx, ny] or [nsky, nx, ny]."""
+        """PSF convolution (Sec. 3.3.2): sky [batch, nsky, nx, ny] or [nsky, nx, ny]."""
         torch = _torch()
         batch, shape = self._batch_shape(sky)
         if out is None:

@@ -1,7 +1,7 @@
 // Radix-2/4/8/16 Stockham FFT building blocks shared by every FFT pass kernel.
 //
 // The FFT passes implement the FFT[...] / FFT^-1[...] of the padded PSF convolution
-// (Sec. 3.3.1) and the oversampled-grid transforms of the measurement operator R (Eq. rime)
+// (Sec. 3.3.2) and the oversampled-grid transforms of the measurement operator R (Eq. rime)
 // and its adjoint. Only power-of-two lengths are supported.
 //
 // A Stockham stage with radix R and current sub-transform size Ns maps, for each butterfly

@@ -1,4 +1,4 @@
-// PSF convolution on the 2x padded grid (Sec. 3.3.1):
+// PSF convolution on the 2x padded grid (Sec. 3.3.2):
 //   out = P^dag FFT^-1[ T . FFT[P s] ],  T = FFT[ifftshift(PSF)] / (4 nx ny)  (real: PSF even)
 // in three passes over half spectra (the sky and the PSF are real), each reading contiguous
 // sequences:

@@ -192,7 +192,7 @@ struct fr_plan {
   int nchan = 0, nsky = 0;
   uint32_t flags = 0;
   double eps = 0;
-  // PSF (Sec. 3.3.1)
+  // PSF (Sec. 3.3.2)
   bool has_psf = false;
   std::vector<double> psf_norm;  // [nsky]
   float* psf_img = nullptr;      // [nsky][2nx][2ny]

@@ -2,7 +2,7 @@
 
 Requests are imaging jobs of different image sizes, visibility counts and channel counts, of two
 kinds, matching the two operator calls of the fast-resolve scheme (Algorithm 1):
-  * "psf":   minor-cycle work, the PSF convolution of a batch of skies (Sec. 3.3.1);
+  * "psf":   minor-cycle work, the PSF convolution of a batch of skies (Sec. 3.3.2);
   * "major": major-cycle work, R^dagger N^-1 R of a sky (Eq. clean), degridding then gridding.
 Each job makes `ncalls` operator applications.
 

@@ -187,7 +187,7 @@ def test_psf_apply_matches_direct_convolution(nx, ny, batch):
 
 
 def test_psf_convolution_equals_normal_operator_at_w0():
-    """PSF * s vs R^dagger N^-1 R s at w = 0, 1/n = 1 (Sec. 3.3.1 exact for coplanar arrays)."""
+    """PSF * s vs R^dagger N^-1 R s at w = 0, 1/n = 1 (Sec. 3.3.2 exact for coplanar arrays)."""
     obs = synth.random_observation(3000, 1, 64, 64, 2e-3, seed=38)
     plan = make_plan(obs, nterm=False, wterm=False)
     sky = dev(synth.random_skies(1, 64, 64, seed=11))

@@ -2,7 +2,7 @@
 
 Each test checks the oracle against something other than itself: a library FFT or
 convolution on a special case that reduces to it, a different geometric route to the same
-phase, adjointness, the PSF identity R^dagger N^-1 R = PSF * at w = 0 (Sec. 3.2, 3.3.1),
+phase, adjointness, the PSF identity R^dagger N^-1 R = PSF * at w = 0 (Sec. 3.2, 3.3.2),
 closed forms, invariants, and finite differences. A dropped term, a flipped sign, a shifted
 pixel origin or a transposed axis in the oracle fails at least one of them.
 """
@@ -157,7 +157,7 @@ def test_normal_operator_of_a_delta_is_the_shifted_psf():
 
 
 def test_psf_convolution_equals_normal_operator_at_w0():
-    """PSF * s == R^dagger N^-1 R s for every sky when w = 0 and 1/n = 1 (Sec. 3.3.1, coplanar)."""
+    """PSF * s == R^dagger N^-1 R s for every sky when w = 0 and 1/n = 1 (Sec. 3.3.2, coplanar)."""
     obs = _tiny_w0_obs(nchan=2, seed=9)
     nx, ny, dl = obs.nx, obs.ny, obs.pixsize
     s = np.random.default_rng(10).uniform(0, 1, (1, nx, ny))
@@ -170,7 +170,7 @@ def test_psf_convolution_equals_normal_operator_at_w0():
 
 
 def test_psf_apply_equals_scipy_linear_convolution():
-    """The cropped linear convolution of Sec. 3.3.1 is the centre block of the full 2D convolution."""
+    """The cropped linear convolution of Sec. 3.3.2 is the centre block of the full 2D convolution."""
     rng = np.random.default_rng(11)
     nx, ny = 9, 14
     P = rng.standard_normal((2 * nx, 2 * ny))
