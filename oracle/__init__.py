@@ -5,8 +5,10 @@ TEST INFRASTRUCTURE ONLY. Nothing on the product path imports this package: only
 ``bench.py`` may import, call, link or execute anything under ``oracle/``.
 
 Every function here evaluates a definition from the paper directly (direct sums,
-no NUFFT, no FFT, no blocking or fusion beyond chunking a vectorised sum), so a
-reader can check it against the equations by eye. The oracle shares no code,
+no NUFFT, no blocking or fusion beyond chunking a vectorised sum), so a reader can
+check it against the equations by eye. The measurement operator uses no FFT; the
+noise model (``oracle.noise``) uses numpy's FFT because the paper defines its
+periodic convolutions by FFTs, and solves the kernel fit as a numerical argmin. The oracle shares no code,
 tables or constants with the CUDA path under ``paper_2406_09144_gb300/csrc``.
 
 Sections and equations cited:
@@ -15,10 +17,14 @@ Sections and equations cited:
   Eq. (clean), Sec. 3.2    - R^dagger N^-1 R I = R^dagger N^-1 V, dirty image, PSF
   Sec. 3.3.2               - PSF convolution on a 2x padded grid
   Algorithm 1              - major-cycle residual d = I^D - R^dagger N^-1 R I
+  Eq. (ham_new), Sec. 3.3.1, Sec. 3.3.3 (oracle.noise) - noise kernel K = exp(xi) + eps,
+                             its fit, N'^-1 and the fast-resolve Hamiltonian
 
-Parity: every function is pinned by tests in tests/test_oracle_pins.py (closed
-forms, a special case equal to numpy.fft, adjointness, the PSF identity, a
-library convolution, and finite differences). No function is parity-unpinned.
+Parity: every function is pinned by tests in tests/test_oracle_pins.py and
+tests/test_oracle_noise_pins.py (closed forms, a special case equal to numpy.fft,
+adjointness, the PSF identity, a library convolution, dense circulant algebra, a
+kernel the fit must recover, and finite differences). No function is
+parity-unpinned.
 """
 from .measurement import (  # noqa: F401
     C_LIGHT,
@@ -34,3 +40,4 @@ from .measurement import (  # noqa: F401
     residual_dirty,
     vis_residual_norm2,
 )
+from . import noise  # noqa: E402,F401
