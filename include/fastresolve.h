@@ -123,6 +123,40 @@ int fr_likelihood_grad(fr_plan_t plan, const float *sky, const float *dirty, int
 int fr_major_cycle(fr_plan_t plan, const float *sky, const float *dirty, float *resid,
                    double *resid_norm2, const fr_cf32 *vis, double *vis_chi2, void *stream);
 
+/* Noise model of the fast-resolve likelihood (Sec. 3.3.3, Eq. N_new). Fits, per image, the
+ * transfer function K = exp(xi) + eps_noise of a periodic convolution on the nx x ny image that
+ * stands in for N' = R^dag N^-1 R + eps_noise 1: xi minimises
+ * || N'(I_delta) - FFT^-1[K . FFT(I_delta)] ||^2 with I_delta a unit point source in the centre
+ * pixel (nx/2, ny/2), and N'(I_delta) is evaluated with the exact R and R^dag of the plan. The
+ * minimiser is computed exactly: by Parseval the loss separates per frequency, and
+ * K_k = max(Re(FFT(N' I_delta)_k conj(FFT(I_delta)_k)), eps_noise) (the bound eps_noise is the
+ * limit xi -> -inf where the target is smaller). The kernel stays resident in the plan.
+ *   eps_noise  > 0, the variance of the added white noise (Eq. N_new)
+ *   logdet     host float64 [nsky] or NULL: 1/2 sum_k ln(2 pi K_k), the ln|2 pi N'| / 2 term of
+ *              Eq. ham_new (constant in the sky)
+ * Needs nx, ny >= 32 (FR_EUNSUPPORTED otherwise). Synchronises `stream`. */
+int fr_noise_fit(fr_plan_t plan, double eps_noise, double *logdet, void *stream);
+
+/* The fitted kernel K (not its inverse): device float32 [nsky][nx][ny] in numpy.fft.fft2 order
+ * (kx, ky). FR_EINVAL before fr_noise_fit. */
+int fr_noise_kernel(fr_plan_t plan, float *K, void *stream);
+
+/* N'^-1 x ~ FFT^-1[K^-1 . FFT(x)] per image (periodic boundaries, Sec. 3.3.3).
+ *   x, out  device float32 [batch][nsky][nx][ny]; image (b, k) uses the kernel of sky k.
+ * FR_EINVAL before fr_noise_fit. */
+int fr_noise_apply_inverse(fr_plan_t plan, const float *x, int32_t batch, float *out,
+                           void *stream);
+
+/* The fast-resolve likelihood, Eq. ham_new with R' = PSF * (Sec. 3.3.2) and N'^-1 from the
+ * fitted kernel, for a batch of skies against their dirty images or major-cycle residuals d:
+ *   r = d - PSF * sky,   value_b = 1/2 r_b^T N'^-1 r_b,   grad_b = -PSF * (N'^-1 r_b)
+ * (the ln|2 pi N'| term is constant in the sky and returned by fr_noise_fit).
+ *   sky, dirty, grad  device float32 [batch][nsky][nx][ny]; grad may alias neither input
+ *   value      host float64 [batch] or NULL (synchronises `stream` when given)
+ * FR_EINVAL before fr_noise_fit or for a plan created with FR_NO_PSF. */
+int fr_fast_likelihood_grad(fr_plan_t plan, const float *sky, const float *dirty, int32_t batch,
+                            float *grad, double *value, void *stream);
+
 /* Allocation-free PSF convolution. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory, such as code embedded in an application that owns
  * the whole device-memory budget through its own pool, or code running where a cudaMalloc would

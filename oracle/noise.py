@@ -56,7 +56,9 @@ def fit_noise_kernel(n_delta, eps_noise, maxiter=20000, gtol=1e-14):
 
     n_delta [nsky, nx, ny] = N'(I_delta). The loss is the squared image-space residual; its
     gradient is taken through numpy's FFTs (Parseval: the loss equals (1/N) sum_k
-    |FFT(n_delta)_k - K_k FFT(I_delta)_k|^2). Starts from xi = 0.
+    |FFT(n_delta)_k - K_k FFT(I_delta)_k|^2). The problem is solved for the target and eps
+    divided by s = max|n_delta| (the argmin scales with them: K(target / s, eps / s) = K / s),
+    from xi = 0 and with xi bounded to [-80, 20] so that exp(xi) stays finite.
     """
     from scipy import optimize
 
@@ -67,10 +69,12 @@ def fit_noise_kernel(n_delta, eps_noise, maxiter=20000, gtol=1e-14):
     for s in range(nsky):
         delta = centre_delta(1, nx, ny)[0]
         D = np.fft.fft2(delta)
-        target = n_delta[s]
+        scale = float(np.max(np.abs(n_delta[s]))) or 1.0
+        target = n_delta[s] / scale
+        eps = eps_noise / scale
 
         def loss(xi):
-            K = np.exp(xi.reshape(nx, ny)) + eps_noise
+            K = np.exp(xi.reshape(nx, ny)) + eps
             r = target - np.fft.ifft2(K * D)
             val = float(np.sum(np.abs(r) ** 2))
             # dL/dK_k = (2/N) Re(conj(FFT(model - target))_k D_k); dK/dxi = exp(xi)
@@ -79,9 +83,10 @@ def fit_noise_kernel(n_delta, eps_noise, maxiter=20000, gtol=1e-14):
             return val, g.ravel()
 
         res = optimize.minimize(loss, np.zeros(N), jac=True, method="L-BFGS-B",
+                                bounds=[(-80.0, 20.0)] * N,
                                 options={"maxiter": maxiter, "gtol": gtol, "ftol": 1e-16,
                                          "maxcor": 30})
-        out[s] = np.exp(res.x.reshape(nx, ny)) + eps_noise
+        out[s] = (np.exp(res.x.reshape(nx, ny)) + eps) * scale
     return out
 
 

@@ -20,7 +20,8 @@ ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EUNSUPPORTED
 EXPORTS = ["fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
            "fr_likelihood_grad", "fr_major_cycle", "fr_plan_get_info", "fr_plan_footprint",
            "fr_plan_check", "fr_plan_destroy", "fr_strerror", "fr_last_error", "fr_launch_count",
-           "fr_selftest_fft_host", "fr_psf_convolve_noalloc"]
+           "fr_selftest_fft_host", "fr_psf_convolve_noalloc", "fr_noise_fit", "fr_noise_kernel",
+           "fr_noise_apply_inverse", "fr_fast_likelihood_grad"]
 
 
 class FastResolveError(RuntimeError):
@@ -62,6 +63,10 @@ def load(path: str = LIB_PATH):
     lib.fr_psf_apply.argtypes = [P, P, I32, P, P]
     lib.fr_likelihood_grad.argtypes = [P, P, P, I32, I32, P, P, P]
     lib.fr_major_cycle.argtypes = [P, P, P, P, P, P, P, P]
+    lib.fr_noise_fit.argtypes = [P, D, P, P]
+    lib.fr_noise_kernel.argtypes = [P, P, P]
+    lib.fr_noise_apply_inverse.argtypes = [P, P, I32, P, P]
+    lib.fr_fast_likelihood_grad.argtypes = [P, P, P, I32, P, P, P]
     lib.fr_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
     lib.fr_plan_footprint.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
     lib.fr_plan_check.argtypes = [P, P]
@@ -294,6 +299,43 @@ class Plan:
             _dev(vis, torch.complex64, self.vis_shape, "vis") if vis is not None else None,
             ctypes.byref(chi) if vis is not None else None, _stream_ptr(stream)))
         return resid, rn.value, (chi.value if vis is not None else None)
+
+    def noise_fit(self, eps_noise, stream=None):
+        """Fit the noise kernel K = exp(xi) + eps_noise (Sec. 3.3.3); returns 1/2 sum ln(2 pi K)
+        per image (the constant ln|2 pi N'| / 2 of Eq. ham_new)."""
+        logdet = np.zeros(self.nsky, dtype=np.float64)
+        check(load().fr_noise_fit(self._h, float(eps_noise), logdet.ctypes.data, _stream_ptr(stream)))
+        return logdet
+
+    def noise_kernel(self, device="cuda", stream=None):
+        """The fitted K [nsky, nx, ny] (numpy.fft.fft2 frequency order)."""
+        torch = _torch()
+        K = torch.empty((self.nsky, self.nx, self.ny), dtype=torch.float32, device=device)
+        check(load().fr_noise_kernel(self._h, _dev(K, torch.float32, K.shape, "K"), _stream_ptr(stream)))
+        return K
+
+    def noise_apply_inverse(self, x, out=None, stream=None):
+        """N'^-1 x = FFT^-1[K^-1 FFT(x)] per image (periodic): x [batch, nsky, nx, ny] or [nsky, nx, ny]."""
+        torch = _torch()
+        batch, shape = self._batch_shape(x)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=x.device)
+        check(load().fr_noise_apply_inverse(self._h, _dev(x, torch.float32, shape, "x"), batch,
+                                            _dev(out, torch.float32, shape, "out"), _stream_ptr(stream)))
+        return out
+
+    def fast_likelihood_grad(self, sky, dirty, grad=None, want_value=True, stream=None):
+        """Eq. ham_new: value = 1/2 r.(N'^-1 r), grad = -PSF * (N'^-1 r), r = d - PSF * sky."""
+        torch = _torch()
+        batch, shape = self._batch_shape(sky)
+        if grad is None:
+            grad = torch.empty(shape, dtype=torch.float32, device=sky.device)
+        val = np.zeros(batch, dtype=np.float64)
+        check(load().fr_fast_likelihood_grad(
+            self._h, _dev(sky, torch.float32, shape, "sky"), _dev(dirty, torch.float32, shape, "dirty"),
+            batch, _dev(grad, torch.float32, shape, "grad"),
+            val.ctypes.data if want_value else None, _stream_ptr(stream)))
+        return (val if want_value else None), grad
 
     def _batch_shape(self, sky):
         if sky.dim() == 3:

@@ -230,6 +230,8 @@ static void free_ws(Workspace* w) {
   cudaFree(w->grid_terms_g);
   cudaFree(w->b1_terms);
   cudaFree(w->b1g_terms);
+  cudaFree(w->img_a);
+  cudaFree(w->img_b);
   cudaFree(w->vbuf);
   cudaFree(w->h);
   cudaFree(w->tmp_img);
@@ -329,6 +331,19 @@ static int ws_reserve_terms_g(const Geometry& g, Workspace* w, cudaStream_t s) {
 static bool use_term_grids(const Geometry& g) {
   return g.wterm && g.taylor && degrid_terms_fits(g) &&
          (size_t)term_grid_count(g) * g.Nu * g.Nv * sizeof(float2) <= TERM_GRIDS_MAX_BYTES;
+}
+
+static int ws_reserve_imgs(Workspace* w, size_t n) {
+  if (w->img_n >= n) return FR_OK;
+  cudaFree(w->img_a);
+  cudaFree(w->img_b);
+  w->bytes -= 2 * w->img_n * sizeof(float);
+  w->img_a = w->img_b = nullptr;
+  w->img_n = 0;
+  FR_TRY(ws_alloc(&w->img_a, n, w));
+  FR_TRY(ws_alloc(&w->img_b, n, w));
+  w->img_n = n;
+  return FR_OK;
 }
 
 static int ws_reserve_h(Workspace* w, size_t n) {
@@ -719,6 +734,7 @@ static void plan_free(fr_plan* p) {
   cudaFree(p->geo.tq);
   cudaFree(p->psf_img);
   cudaFree(p->transfer);
+  cudaFree(p->noise_kinv);
   cudaFree(p->status);
   for (float2*& t : p->tw) cudaFree(t);
   delete p;
@@ -944,6 +960,146 @@ int fr_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, int32_
     }
     FR_LAUNCHED();
   }
+  if (value) {
+    FR_CUDA_TRY(cudaMemcpyAsync(value, w->red, batch * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return FR_OK;
+}
+
+// ------------------------------------------------------------ noise model (Sec. 3.3.3)
+__global__ void add_centre_kernel(float* img, int nsky, int nx, int ny, float v) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nsky) img[((size_t)k * nx + nx / 2) * ny + ny / 2] += v;
+}
+
+__global__ void kernel_from_inverse(const float* kinv, int nsky, int nx, int ny, float* K) {
+  const size_t n = (size_t)nsky * nx * ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t img = i / ((size_t)nx * ny), r = i % ((size_t)nx * ny);
+    const int kx = (int)(r / ny), ky = (int)(r % ny);
+    K[i] = 1.f / kinv[(img * ny + ky) * nx + kx];
+  }
+}
+
+static int noise_sizes_ok(const fr_plan* p) {
+  const int lx = ilog2(p->geo.nx), ly = ilog2(p->geo.ny);
+  if (lx < fft_min_log2() || ly < fft_min_log2()) {
+    set_error("the noise model needs nx, ny >= %d", 1 << fft_min_log2());
+    return FR_EUNSUPPORTED;
+  }
+  return FR_OK;
+}
+
+int fr_noise_fit(fr_plan_t p, double eps_noise, double* logdet, void* stream) {
+  if (!p || !(eps_noise > 0.0) || !std::isfinite(eps_noise)) {
+    set_error("plan must be non-null and eps_noise positive");
+    return FR_EINVAL;
+  }
+  FR_TRY(noise_sizes_ok(p));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geometry& g = p->geo;
+  FR_TRY(ensure_twiddles(p, ilog2(g.nx), s));
+  FR_TRY(ensure_twiddles(p, ilog2(g.ny), s));
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  FR_TRY(ws_reserve_tmp(p, w));
+  const size_t n = (size_t)p->nsky * g.nx * g.ny;
+  FR_TRY(ws_reserve_imgs(w, n));
+  FR_TRY(ws_reserve_h(w, n));
+  FR_TRY(ws_reserve_red(w, (size_t)std::max(p->nsky, 4)));
+  if (!p->noise_kinv) {
+    FR_CUDA_TRY(cudaMalloc(&p->noise_kinv, n * sizeof(float)));
+    p->resident += n * sizeof(float);
+  }
+  // N'(I_delta) = R^dag N^-1 R I_delta + eps I_delta with the exact operators (Eq. N_new)
+  FR_CUDA_TRY(cudaMemsetAsync(w->img_a, 0, n * sizeof(float), s));
+  add_centre_kernel<<<1, 32, 0, s>>>(w->img_a, p->nsky, g.nx, g.ny, 1.f);
+  FR_LAUNCHED();
+  FR_TRY(run_degrid(p, g, p->lay, w, w->img_a, w->tmp_vis, s));
+  FR_TRY(run_grid(p, g, p->lay, w, w->tmp_vis, 1, w->img_b, w->grid, w->b1g, w->vbuf, s,
+                  &w->grid_zero));
+  add_centre_kernel<<<1, 32, 0, s>>>(w->img_b, p->nsky, g.nx, g.ny, (float)eps_noise);
+  FR_LAUNCHED();
+  FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, p->nsky * sizeof(double), s));
+  FR_TRY(noise_kernel_passes(w->img_b, g.nx, g.ny, p->nsky, (float)eps_noise, w->h,
+                             p->noise_kinv, w->red, p->tw[ilog2(g.ny)], p->tw[ilog2(g.nx)], s));
+  p->noise_logdet.assign(p->nsky, 0.0);
+  FR_CUDA_TRY(cudaMemcpyAsync(p->noise_logdet.data(), w->red, p->nsky * sizeof(double),
+                              cudaMemcpyDeviceToHost, s));
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  p->noise_eps = eps_noise;
+  p->has_noise = true;
+  if (logdet) std::copy(p->noise_logdet.begin(), p->noise_logdet.end(), logdet);
+  return FR_OK;
+}
+
+int fr_noise_kernel(fr_plan_t p, float* K, void* stream) {
+  if (!p || !K) {
+    set_error("plan and K must be non-null");
+    return FR_EINVAL;
+  }
+  if (!p->has_noise) {
+    set_error("no noise kernel: call fr_noise_fit first");
+    return FR_EINVAL;
+  }
+  const size_t n = (size_t)p->nsky * p->geo.nx * p->geo.ny;
+  kernel_from_inverse<<<nblocks(n), RED_T, 0, (cudaStream_t)stream>>>(p->noise_kinv, p->nsky,
+                                                                       p->geo.nx, p->geo.ny, K);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+int fr_noise_apply_inverse(fr_plan_t p, const float* x, int32_t batch, float* out, void* stream) {
+  if (!p || !x || !out || batch < 1) {
+    set_error("plan, x, out must be non-null and batch >= 1");
+    return FR_EINVAL;
+  }
+  if (!p->has_noise) {
+    set_error("no noise kernel: call fr_noise_fit first");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geometry& g = p->geo;
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  const int nimg = batch * p->nsky;
+  const size_t n = (size_t)nimg * g.nx * g.ny;
+  FR_TRY(ws_reserve_h(w, 2 * n));
+  return noise_inverse_passes(x, g.nx, g.ny, nimg, p->nsky, p->noise_kinv, w->h, w->h + n, out,
+                              1.f, nullptr, nullptr, p->tw[ilog2(g.ny)], p->tw[ilog2(g.nx)], s);
+}
+
+int fr_fast_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, int32_t batch,
+                            float* grad, double* value, void* stream) {
+  if (!p || !sky || !dirty || !grad || batch < 1) {
+    set_error("plan, sky, dirty, grad must be non-null and batch >= 1");
+    return FR_EINVAL;
+  }
+  if (!p->has_noise) {
+    set_error("no noise kernel: call fr_noise_fit first");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geometry& g = p->geo;
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  const int nimg = batch * p->nsky;
+  const size_t n = (size_t)nimg * g.nx * g.ny;
+  FR_TRY(ws_reserve_imgs(w, n));
+  // spectra scratch for both the PSF passes and the noise passes (the PSF's is the larger)
+  FR_TRY(ws_reserve_h(w, (size_t)nimg * g.nx * (2 * (size_t)g.ny + 3)));
+  FR_TRY(ws_reserve_red(w, (size_t)std::max(batch, 4)));
+  // t = PSF * sky - dirty = -r (Sec. 3.3.2 response)
+  FR_TRY(psf_common(p, sky, batch, w->img_a, dirty, nullptr, s));
+  FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, batch * sizeof(double), s));
+  // u = N'^-1 t = -N'^-1 r and H = 1/2 t . u = 1/2 r^T N'^-1 r (Eq. ham_new)
+  FR_TRY(noise_inverse_passes(w->img_a, g.nx, g.ny, nimg, p->nsky, p->noise_kinv, w->h,
+                              w->h + n, w->img_b, 1.f, w->img_a, w->red, p->tw[ilog2(g.ny)],
+                              p->tw[ilog2(g.nx)], s));
+  // grad = -PSF * (N'^-1 r) = PSF * u (the PSF passes without a dirty image leave red alone)
+  FR_TRY(psf_common(p, w->img_b, batch, grad, nullptr, nullptr, s));
   if (value) {
     FR_CUDA_TRY(cudaMemcpyAsync(value, w->red, batch * sizeof(double), cudaMemcpyDeviceToHost, s));
     FR_CUDA_TRY(cudaStreamSynchronize(s));

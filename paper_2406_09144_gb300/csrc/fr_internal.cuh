@@ -178,6 +178,9 @@ struct Workspace {
   CUtensorMap tmap_terms;        // 3-D TMA descriptor of `grid_terms`
   float2* grid_terms_g = nullptr;  // [nterms][Nv][Nu] gridding term grids (kept zero)
   bool terms_g_zero = false;
+  float* img_a = nullptr;  // [n] image scratch of the fast-resolve likelihood
+  float* img_b = nullptr;
+  size_t img_n = 0;
   float2* b1_terms = nullptr;   // [nterms][band v][nx] degridding half planes
   float2* b1g_terms = nullptr;  // [nterms][nx][Nv] gridding half planes (zero off-band)
   size_t bytes = 0;
@@ -197,6 +200,11 @@ struct fr_plan {
   std::vector<double> psf_norm;  // [nsky]
   float* psf_img = nullptr;      // [nsky][2nx][2ny]
   float* transfer = nullptr;     // [nsky][2nx][ny+1], includes 1 / (4 nx ny)
+  // noise model of the fast-resolve likelihood (Sec. 3.3.3): 1 / K_xi, [nsky][ny][nx]
+  bool has_noise = false;
+  float* noise_kinv = nullptr;
+  double noise_eps = 0;
+  std::vector<double> noise_logdet;  // [nsky] 1/2 sum ln(2 pi K)
   // twiddle tables by log2 length
   float2* tw[16] = {nullptr};
   int* status = nullptr;         // device status word
@@ -256,6 +264,16 @@ int build_transfer(int nx, int ny, int nsky, const float* psf, float2* ht, float
                    const float2* tw_rows, const float2* tw_cols, cudaStream_t s);
 int fft_max_log2();
 int fft_min_log2();
+// noise model passes (noise.cu): n_delta [nsky][nx][ny] -> kinv [nsky][ny][nx], logdet [nsky]
+// (accumulated); ht scratch [nsky][ny][nx]
+int noise_kernel_passes(const float* n_delta, int nx, int ny, int nsky, float eps, float2* ht,
+                        float* kinv, double* logdet, const float2* tw_y, const float2* tw_x,
+                        cudaStream_t s);
+// out = sgn N'^-1 x for nimg images (image i uses kernel i % nsky); with t non-null,
+// value[i / nsky] += 1/2 t . N'^-1 x; ht, h scratch [nimg][nx][ny] complex each
+int noise_inverse_passes(const float* x, int nx, int ny, int nimg, int nsky, const float* kinv,
+                         float2* ht, float2* h, float* out, float sgn, const float* t,
+                         double* value, const float2* tw_y, const float2* tw_x, cudaStream_t s);
 
 // -------- gridding kernels (gridder.cu) --------
 int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const double* h_freqs,
