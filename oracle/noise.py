@@ -11,7 +11,8 @@ with xi fitted to the exact N' applied to a centre delta:
     xi = argmin_xi || N'(I_delta) - FFT^-1[(exp xi + eps) . FFT(I_delta)] ||^2.
 
 The FFTs are the paper's own definition of these operators (numpy.fft, unnormalised forward,
-1/N inverse). The fit is the argmin itself, solved numerically (L-BFGS on xi in FP64).
+1/N inverse). The fit is the argmin itself, solved numerically as a bound-constrained linear
+least-squares problem on the dense operator.
 """
 import numpy as np
 
@@ -51,42 +52,32 @@ def noise_inverse(x, K):
     return periodic_convolve(x, 1.0 / np.asarray(K))
 
 
-def fit_noise_kernel(n_delta, eps_noise, maxiter=20000, gtol=1e-14):
+def fit_noise_kernel(n_delta, eps_noise):
     """K = exp(xi) + eps with xi the argmin of Sec. 3.3.3, one kernel per image.
 
-    n_delta [nsky, nx, ny] = N'(I_delta). The loss is the squared image-space residual; its
-    gradient is taken through numpy's FFTs (Parseval: the loss equals (1/N) sum_k
-    |FFT(n_delta)_k - K_k FFT(I_delta)_k|^2). The problem is solved for the target and eps
-    divided by s = max|n_delta| (the argmin scales with them: K(target / s, eps / s) = K / s),
-    from xi = 0 and with xi bounded to [-80, 20] so that exp(xi) stays finite.
+    n_delta [nsky, nx, ny] = N'(I_delta). The model FFT^-1[K . FFT(I_delta)] is linear in K, so
+    the loss is a linear least-squares problem in K over K > eps; its argmin over xi is the
+    bound-constrained minimiser with K >= eps (K = eps being the limit xi -> -inf). It is
+    solved on the dense operator (columns FFT^-1[e_k . FFT(I_delta)], real and imaginary parts
+    stacked) by scipy.optimize.lsq_linear, after dividing the target and eps by
+    s = max|n_delta| (the argmin scales with them).
     """
     from scipy import optimize
 
     n_delta = np.asarray(n_delta, dtype=np.float64)
     nsky, nx, ny = n_delta.shape
     N = nx * ny
+    D = np.fft.fft2(centre_delta(1, nx, ny)[0])
+    cols = np.fft.ifft2(np.eye(N).reshape(N, nx, ny) * D[None], axes=(1, 2)).reshape(N, N).T
+    A = np.concatenate([cols.real, cols.imag])  # [2N, N]: image residual (re, im) per K_k
     out = np.empty_like(n_delta)
     for s in range(nsky):
-        delta = centre_delta(1, nx, ny)[0]
-        D = np.fft.fft2(delta)
         scale = float(np.max(np.abs(n_delta[s]))) or 1.0
-        target = n_delta[s] / scale
+        b = np.concatenate([n_delta[s].ravel() / scale, np.zeros(N)])
         eps = eps_noise / scale
-
-        def loss(xi):
-            K = np.exp(xi.reshape(nx, ny)) + eps
-            r = target - np.fft.ifft2(K * D)
-            val = float(np.sum(np.abs(r) ** 2))
-            # dL/dK_k = (2/N) Re(conj(FFT(model - target))_k D_k); dK/dxi = exp(xi)
-            R = np.fft.fft2(-r)
-            g = (2.0 / N) * np.real(np.conj(R) * D) * np.exp(xi.reshape(nx, ny))
-            return val, g.ravel()
-
-        res = optimize.minimize(loss, np.zeros(N), jac=True, method="L-BFGS-B",
-                                bounds=[(-80.0, 20.0)] * N,
-                                options={"maxiter": maxiter, "gtol": gtol, "ftol": 1e-16,
-                                         "maxcor": 30})
-        out[s] = (np.exp(res.x.reshape(nx, ny)) + eps) * scale
+        res = optimize.lsq_linear(A, b, bounds=(eps, np.inf), method="bvls", tol=1e-15,
+                                  lsmr_tol="auto")
+        out[s] = res.x.reshape(nx, ny) * scale
     return out
 
 

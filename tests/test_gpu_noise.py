@@ -1,9 +1,9 @@
 """GPU parity of the fast-resolve noise model and likelihood (Sec. 3.3.1 Eq. ham_new, Sec. 3.3.3)
 against the FP64 oracle (oracle/noise.py), through the C ABI.
 
-Tolerances: the kernel K inherits the NUFFT error of the exact N'(I_delta) (relative L2
-<= 2e-5 against the oracle's numerical argmin); N'^-1 and the likelihood with a given kernel
-are FP32 FFT arithmetic (<= 2e-6 and 1e-5 relative)."""
+Tolerances: the kernel K inherits the NUFFT error of the exact N'(I_delta), one R and one
+R^dagger at eps = 1e-5 (relative L2 <= 5 eps against the oracle's argmin); N'^-1 and the
+likelihood with a given kernel are FP32 FFT arithmetic (<= 2e-6 and 1e-5 relative)."""
 import numpy as np
 import pytest
 
@@ -51,7 +51,7 @@ def test_noise_kernel_fit_matches_oracle_argmin(wc, nchan, per, nx, ny):
     n_delta = noise.noise_cov_of_delta(obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, nx, ny,
                                        eps_noise, weights=w, nsky=plan.nsky, wterm=obs.wterm)
     K_ref = noise.fit_noise_kernel(n_delta, eps_noise)
-    assert rel(K, K_ref) <= 2e-5, rel(K, K_ref)
+    assert rel(K, K_ref) <= 5e-5, rel(K, K_ref)
     assert np.all(K >= np.float32(eps_noise) * (1 - 1e-6))
     ref_logdet = 0.5 * np.log(2 * np.pi * K_ref).reshape(plan.nsky, -1).sum(1)
     assert np.allclose(logdet, ref_logdet, rtol=1e-5)
