@@ -335,6 +335,32 @@ def main():
                    "GBps": (v[1] / (v[0] * 1e-3) / 1e9) if v[0] > 0 else None}
                for k, v in cats.items() if v[2]}
 
+    # the fast-resolve minor-cycle likelihood (Eq. ham_new): noise kernel fitted once (untimed),
+    # then value + gradient per call; and one exact major cycle (Alg. 1) for comparison
+    eps_noise = 1e-4 * float(w32.astype(np.float64).sum()) / obs.nchan
+    plan.noise_fit(eps_noise)
+    fgrad = torch.empty_like(dirty)
+    for _ in range(2):
+        plan.fast_likelihood_grad(sky, dirty, grad=fgrad, want_value=False)
+        plan.major_cycle(sky, dirty, want_resid=True)
+    torch.cuda.synchronize()
+    t_fast = t_major = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        plan.fast_likelihood_grad(sky, dirty, grad=fgrad, want_value=False)
+        b.record(stream)
+        plan.major_cycle(sky, dirty, want_resid=True)
+        c.record(stream)
+        c.synchronize()
+        t_fast += a.elapsed_time(b)
+        t_major += b.elapsed_time(c)
+    minor_major = {"fast_likelihood_ms": t_fast / args.steps,
+                   "fast_likelihood_mpix_s": obs.nsky * obs.nx * obs.ny / (t_fast / args.steps * 1e-3) / 1e6,
+                   "major_cycle_ms": t_major / args.steps,
+                   "eps_noise": eps_noise}
+
     # end to end through the C ABI with host buffers: H2D sky + vis, R and R^dag, D2H results
     e2e = None
     if True:
@@ -395,6 +421,7 @@ def main():
             "psf_likelihood_ms": t_psf / args.steps,
             "plan_s": plan_s,
             "plan": {k: info[k] for k in ("support", "wplanes_total", "work_items", "grid_nu")},
+            "minor_major": minor_major,
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
         }

@@ -1,0 +1,59 @@
+"""Alg. 1 major/minor loop (paper_2406_09144_gb300/driver.py) on a small synthetic observation:
+each major cycle's residual matches the oracle's for the same sky, the residual shrinks from
+cycle to cycle, and the reconstruction explains the visibilities far better than no sky does
+(chi^2 below 30 % of the empty sky's)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_09144_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2406_09144_gb300 import build, binding
+    build.build()
+    binding.load()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def test_major_minor_loop():
+    from paper_2406_09144_gb300.binding import Plan
+    from paper_2406_09144_gb300.driver import reconstruct
+    nx = ny = 64
+    obs = synth.random_observation(3000, 1, nx, ny, 2e-3, seed=70, wmax_cycles=0.3)
+    truth = np.clip(synth.sky_image(nx, ny, seed=71), 0.0, None)[None]
+    sigma = 1e-2
+    vis_true = oracle.degrid(truth, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize)
+    vis = vis_true + sigma * synth.complex_gaussian(vis_true.shape, seed=72)
+    w = np.full(vis.shape, 1.0 / sigma ** 2, dtype=np.float32)
+    plan = Plan(obs.uvw, obs.freqs, nx, ny, obs.pixsize, weights=w, eps=1e-5, mfs=True)
+    vis_d = torch.as_tensor(vis).to("cuda", torch.complex64)
+    sky, hist = reconstruct(plan, vis_d, n_major=4, n_minor=300, prior_sigma=10.0)
+    s = sky.cpu().numpy().astype(np.float64)
+    assert np.all(s > 0)
+    rn = [h["resid_norm2"] for h in hist]
+    assert all(b < a for a, b in zip(rn, rn[1:])), rn
+    # the major-cycle residual is the exact one: same sky through the oracle
+    dirty = oracle.grid(vis.astype(np.complex64), obs.uvw, obs.freqs, obs.pixsize, obs.pixsize,
+                        nx, ny, weights=w)
+    d_ref = oracle.residual_dirty(dirty, s, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize,
+                                  weights=w)
+    d_gpu, rn2, _ = plan.major_cycle(sky, torch.as_tensor(dirty).to("cuda", torch.float32))
+    assert rel(d_gpu.cpu().numpy(), d_ref) <= 1e-4
+    assert abs(rn2 - float(np.sum(d_ref ** 2))) <= 2e-4 * float(np.sum(d_ref ** 2))
+    # the data fit: chi^2 of the visibilities falls far below that of an empty sky
+    dirty_d = torch.as_tensor(dirty).to("cuda", torch.float32)
+    chi_sky = plan.major_cycle(sky, dirty_d, vis=vis_d)[2]
+    chi_zero = plan.major_cycle(torch.zeros_like(sky), dirty_d, vis=vis_d)[2]
+    # (the stand-in MAP minor cycle converges slowly on this ill-conditioned problem; four major
+    # cycles of 300 L-BFGS steps measured 0.22)
+    assert chi_sky < 0.3 * chi_zero, (chi_sky, chi_zero)
