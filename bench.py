@@ -331,6 +331,20 @@ def main():
                 "algorithmic_bytes_per_launch": dby / max(dn, 1),
                 "avg_launch_ms": dms / max(dn, 1), "launches": int(dn),
                 "share_of_step": dms / max(t_step, 1e-9)}
+    # the visibility kernels are bound by FP32 issue, not HBM: their multiply-add rate against
+    # the FP32 peak (152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s, nominal unit counts
+    # and the maximum SM clock). Flops: 4 per footprint cell (a complex times a real weight,
+    # two FMAs) for every term or w-plane a visibility visits.
+    visits = info["wplanes_max"] if info["dw"] == 0.0 else info["support"]
+    cells = info["support"] ** 2
+    alu = {}
+    for k in ("grid", "degrid"):
+        if k in cats and cats[k][2]:
+            flops = obs.nvis * visits * cells * 4.0
+            tf = flops / (cats[k][0] / args.steps * 1e-3) / 1e12
+            alu[k] = {"bound": "alu", "achieved": tf, "peak": 80.5, "unit": "TFLOP/s",
+                      "frac": tf / 80.5, "flops_per_step": flops,
+                      "peak_source": "nominal FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
     kernels = {k: {"ms": v[0] / args.steps, "launches": int(v[2]) // args.steps,
                    "GBps": (v[1] / (v[0] * 1e-3) / 1e9) if v[0] > 0 else None}
                for k, v in cats.items() if v[2]}
@@ -436,7 +450,7 @@ def main():
             "psf_likelihood_ms": t_psf / args.steps,
             "plan_s": plan_s,
             "plan": {k: info[k] for k in ("support", "wplanes_total", "work_items", "grid_nu")},
-            "minor_major": minor_major,
+            "minor_major": minor_major, "roofline_alu": alu,
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
         }
