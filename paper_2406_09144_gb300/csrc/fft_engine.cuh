@@ -93,6 +93,40 @@ struct SeqView {
   __device__ __forceinline__ float2 operator[](int i) const { return p[spad(i)]; }
 };
 
+// Transposed stores write each output index o as a run of consecutive sequences. With few
+// sequences per CTA that run is short (8 bytes at B = 1), so ops that support it (Op::GROUP)
+// gather the run of a thread-block cluster instead: CL = 4 / B CTAs (B < 4) hold 4 consecutive
+// sequences, and after a cluster barrier each CTA writes 1/CL of the outputs as 32-byte groups,
+// reading the other CTAs' sequences through distributed shared memory (8 sequences in 64-byte
+// groups measured slower). Such ops add
+//   float2 pick(int seq, int o, SeqView v)            the value store() would write
+//   void store_group(int seq0, int o, const float2* v, int n)   n <= 4 consecutive sequences
+constexpr int GROUP_SEQ = 4;  // consecutive sequences per output run (32 bytes)
+
+template <int B, class Op>
+constexpr int cluster_size() {
+  if constexpr (Op::TRANSPOSED && Op::GROUP) return B >= GROUP_SEQ ? 1 : GROUP_SEQ / B;
+  return 1;
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// generic address of the same shared-memory location in cluster CTA `rank`
+__device__ __forceinline__ const float2* cluster_map(const float2* p, uint32_t rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"((uint64_t)p), "r"(rank));
+  return reinterpret_cast<const float2*>(out);
+}
+
 // Generic pass. blockIdx.x selects B consecutive sequences, blockIdx.y an image (ops that batch
 // images use it). Op provides:
 //   static constexpr bool TRANSPOSED   store mapping (see above)
@@ -135,7 +169,33 @@ __global__ void __launch_bounds__(FftCfg<LOG2L>::NT,
   }
   const int nout = op.nout();
   double acc = 0.0;
-  if constexpr (Op::TRANSPOSED) {
+  constexpr int CL = cluster_size<B, Op>();
+  if constexpr (CL > 1) {
+    // every CTA of the cluster has transformed its sequences: gather 4 per output index
+    cluster_barrier();
+    const uint32_t rank = cluster_rank();
+    const int g0 = seq0 - (int)rank * B;  // first sequence of the cluster
+    const int per = (nout + CL - 1) / CL;
+    const int o0 = (int)rank * per, o1 = min(nout, o0 + per);
+    const int n = min(CL * B, nseq - g0);
+    if (n > 0) {
+      const float2* views[CL];
+#pragma unroll
+      for (int c = 0; c < CL; ++c) views[c] = cluster_map(smem, (uint32_t)c);
+      for (int o = o0 + threadIdx.x; o < o1; o += NT) {
+        float2 v[CL * B];
+#pragma unroll
+        for (int c = 0; c < CL; ++c)
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const int q = c * B + b;
+            v[q] = q < n ? op.pick(g0 + q, o, SeqView{views[c] + b * LP}) : make_float2(0.f, 0.f);
+          }
+        op.store_group(g0, o, v, n);
+      }
+    }
+    cluster_barrier();  // the other CTAs have read this CTA's shared memory
+  } else if constexpr (Op::TRANSPOSED) {
     for (int idx = threadIdx.x; idx < B * nout; idx += NT) {
       const int o = idx / B, b = idx % B;
       if (seq0 + b < nseq) acc += op.store(seq0 + b, o, SeqView{smem + b * LP});
@@ -161,7 +221,25 @@ int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
     FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr = true;
   }
-  kern<<<dim3(nblk, nimg), C::NT, C::SMEM, s>>>(op, tw);
+  constexpr int CL = cluster_size<C::B, Op>();
+  if constexpr (CL > 1) {
+    // whole clusters: the CTAs past the last sequence transform zeros and store nothing
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((nblk + CL - 1) / CL * CL, nimg);
+    cfg.blockDim = dim3(C::NT);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FR_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, op, tw));
+  } else {
+    kern<<<dim3(nblk, nimg), C::NT, C::SMEM, s>>>(op, tw);
+  }
   FR_LAUNCHED();
   return FR_OK;
 }
@@ -303,10 +381,23 @@ int launch_pass_multi(const Op& op, const float2* tw, cudaStream_t s) {
   return FR_OK;
 }
 
+// group store helper: n <= GROUP_SEQ consecutive complex values at dst (16-byte vector stores
+// when the group is whole and aligned)
+__device__ __forceinline__ void store_run(float2* dst, const float2* v, int n) {
+  if (n == GROUP_SEQ && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+    for (int g = 0; g < GROUP_SEQ; g += 2)
+      reinterpret_cast<float4*>(dst)[g / 2] = make_float4(v[g].x, v[g].y, v[g + 1].x, v[g + 1].y);
+  } else {
+    for (int g = 0; g < n; ++g) dst[g] = v[g];
+  }
+}
+
 // Defaults for the optional parts of an op.
 struct OpBase {
   static constexpr bool TRANSPOSED = false;
   static constexpr bool TWO = false;
+  static constexpr bool GROUP = false;
   __device__ void after_load(int, int) const {}
   template <int B, int NT, int L, int LP>
   __device__ void mid(float2*, int) const {}

@@ -89,6 +89,11 @@ struct D1Op : OpBase {
     b1t[blockIdx.y * b1t_stride + (size_t)o * nx + jx] = s[vb0 + o];
     return 0.0;
   }
+  static constexpr bool GROUP = true;
+  __device__ float2 pick(int, int o, SeqView s) const { return s[vb0 + o]; }
+  __device__ void store_group(int jx0, int o, const float2* v, int n) const {
+    store_run(b1t + blockIdx.y * b1t_stride + (size_t)o * nx + jx0, v, n);
+  }
 };
 
 struct D2Op : OpBase {
@@ -216,6 +221,13 @@ struct G1Op : OpBase {
     const int i = (o - (nx >> 1) + Nu) & (Nu - 1);
     b1[blockIdx.y * b1_stride + (size_t)o * Nv + vb0 + q] = s[i];
     return 0.0;
+  }
+  static constexpr bool GROUP = true;
+  __device__ float2 pick(int, int o, SeqView s) const {
+    return s[(o - (nx >> 1) + Nu) & (Nu - 1)];
+  }
+  __device__ void store_group(int q0, int o, const float2* v, int n) const {
+    store_run(b1 + blockIdx.y * b1_stride + (size_t)o * Nv + vb0 + q0, v, n);
   }
 };
 

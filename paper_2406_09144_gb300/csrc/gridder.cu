@@ -680,7 +680,7 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
     if (N > 0) {
       lay->bu0 = hb[0];
       lay->bu1 = std::min(geo.Nu - 1, hb[1] + W - 1);
-      lay->bv0 = hb[2];
+      lay->bv0 = hb[2] & ~3;  // a multiple of 4: whole 32-byte groups in the post-pass stores
       lay->bv1 = std::min(geo.Nv - 1, hb[3] + W - 1);
     } else {
       lay->bu0 = lay->bv0 = 0;

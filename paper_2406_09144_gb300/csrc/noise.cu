@@ -30,6 +30,11 @@ struct NK1Op : OpBase {
     ht[((size_t)blockIdx.y * ny + ky) * nx + jx] = s[ky];
     return 0.0;
   }
+  static constexpr bool GROUP = true;
+  __device__ float2 pick(int, int ky, SeqView s) const { return s[ky]; }
+  __device__ void store_group(int jx0, int ky, const float2* v, int n) const {
+    store_run(ht + ((size_t)blockIdx.y * ny + ky) * nx + jx0, v, n);
+  }
 };
 
 struct NK2Op : OpBase {
@@ -60,6 +65,11 @@ struct NK2Op : OpBase {
   __device__ double store(int ky, int jx, SeqView s) const {
     h[((size_t)blockIdx.y * nx + jx) * ny + ky] = s[jx];
     return 0.0;
+  }
+  static constexpr bool GROUP = true;
+  __device__ float2 pick(int, int jx, SeqView s) const { return s[jx]; }
+  __device__ void store_group(int ky0, int jx, const float2* v, int n) const {
+    store_run(h + ((size_t)blockIdx.y * nx + jx) * ny + ky0, v, n);
   }
 };
 
