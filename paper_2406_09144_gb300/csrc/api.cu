@@ -898,7 +898,7 @@ static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, 
   Workspace* w;
   FR_TRY(get_ws(p, s, &w));
   const int nimg = batch * p->nsky;
-  const int hp = p->geo.ny + 2;
+  const int hp = p->geo.ny + 4;  // ny + 1 bins, pitch a multiple of 4 (32-byte group stores)
   const size_t hsize = (size_t)nimg * p->geo.nx * hp;  // H, then HT ([nimg][ny+1][nx])
   FR_TRY(ws_reserve_h(w, hsize + (size_t)nimg * (p->geo.ny + 1) * p->geo.nx));
   PsfArgs a;
@@ -1089,7 +1089,7 @@ int fr_fast_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, i
   const size_t n = (size_t)nimg * g.nx * g.ny;
   FR_TRY(ws_reserve_imgs(w, n));
   // spectra scratch for both the PSF passes and the noise passes (the PSF's is the larger)
-  FR_TRY(ws_reserve_h(w, (size_t)nimg * g.nx * (2 * (size_t)g.ny + 3)));
+  FR_TRY(ws_reserve_h(w, (size_t)nimg * g.nx * (2 * (size_t)g.ny + 5)));
   FR_TRY(ws_reserve_red(w, (size_t)std::max(batch, 4)));
   // t = PSF * sky - dirty = -r (Sec. 3.3.2 response)
   FR_TRY(psf_common(p, sky, batch, w->img_a, dirty, nullptr, s));

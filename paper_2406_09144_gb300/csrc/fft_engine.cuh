@@ -95,7 +95,7 @@ struct SeqView {
 
 // Transposed stores write each output index o as a run of consecutive sequences. With few
 // sequences per CTA that run is short (8 bytes at B = 1), so ops that support it (Op::GROUP)
-// gather the run of a thread-block cluster instead: CL = 4 / B CTAs (B < 4) hold 4 consecutive
+// gather the run of a thread-block cluster instead: at B = 1, CL = 4 CTAs hold 4 consecutive
 // sequences, and after a cluster barrier each CTA writes 1/CL of the outputs as 32-byte groups,
 // reading the other CTAs' sequences through distributed shared memory (8 sequences in 64-byte
 // groups measured slower). Such ops add
@@ -105,7 +105,8 @@ constexpr int GROUP_SEQ = 4;  // consecutive sequences per output run (32 bytes)
 
 template <int B, class Op>
 constexpr int cluster_size() {
-  if constexpr (Op::TRANSPOSED && Op::GROUP) return B >= GROUP_SEQ ? 1 : GROUP_SEQ / B;
+  // one sequence per CTA (8192 and 16384 points); at B = 2 the 16-byte runs measured as fast
+  if constexpr (Op::TRANSPOSED && Op::GROUP && B == 1) return GROUP_SEQ;
   return 1;
 }
 

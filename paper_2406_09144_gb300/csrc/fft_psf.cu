@@ -75,6 +75,11 @@ struct P2Op : OpBase {
     h[((size_t)blockIdx.y * nx + o) * hp + q] = s[o];
     return 0.0;
   }
+  static constexpr bool GROUP = true;
+  __device__ float2 pick(int, int o, SeqView s) const { return s[o]; }
+  __device__ void store_group(int q0, int o, const float2* v, int n) const {
+    store_run(h + ((size_t)blockIdx.y * nx + o) * hp + q0, v, n);
+  }
 };
 
 struct P3Op : OpBase {
