@@ -24,7 +24,7 @@ struct FftCfg {
   static constexpr size_t SMEM = size_t(B) * LP * sizeof(float2);
   // CTAs per SM the register budget is sized for: four at L = 2048 (64 registers, no spills)
   static constexpr int MINB = NT >= 1024 ? 1 : (NT >= 512 || LOG2L < 11 ? 2 : 4);
-  static constexpr int MINB_SUM = NT >= 512 ? 1 : 2;  // summing and multi-output passes
+  static constexpr int MINB_SUM = NT >= 512 ? 1 : 2;  // multi-output passes
   static constexpr int MINB_TWO = NT >= 1024 ? 1 : 2;  // two-transform passes
 };
 
@@ -241,82 +241,6 @@ int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
   } else {
     kern<<<dim3(nblk, nimg), C::NT, C::SMEM, s>>>(op, tw);
   }
-  FR_LAUNCHED();
-  return FR_OK;
-}
-
-// Summing pass: for each of op.nterms() inputs per sequence (blockIdx.x selects B sequences),
-// load, transform and add op.value(t, seq, o, view) into per-thread accumulators kept in shared
-// memory after the transform buffer; one op.store(seq, o, sum) per output at the end. The next
-// input's loads are issued before the current one is transformed. Row-major outputs (o fastest),
-// nout <= L.
-//   float2 load(int t, int seq, int i); float value(int t, int seq, int o, SeqView v);
-//   void store(int seq, int o, float sum)
-template <int LOG2L, int DIR, class Op>
-__global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB_SUM)
-    fft_pass_sum_kernel(Op op, const float2* __restrict__ tw) {
-  using C = FftCfg<LOG2L>;
-  constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
-  constexpr int PER = B * L / NT;
-  extern __shared__ float2 smem[];
-  float* accs = reinterpret_cast<float*>(smem + B * LP);  // [B * nout], one entry per output
-  const int nseq = op.nseq(), nout = op.nout(), nterm = op.nterms();
-  const int seq0 = blockIdx.x * B;
-#pragma unroll
-  for (int k = 0; k < PER; ++k) accs[threadIdx.x + k * NT] = 0.f;  // B * nout <= B * L
-  float2 r[PER];
-  auto fetch = [&](int t) {
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int idx = threadIdx.x + k * NT;
-      const int b = idx / L, i = idx % L;
-      r[k] = (seq0 + b < nseq) ? op.load(t, seq0 + b, i) : make_float2(0.f, 0.f);
-    }
-  };
-  if (nterm > 0) fetch(0);
-  for (int t = 0; t < nterm; ++t) {
-    if (t > 0) __syncthreads();  // the previous term's outputs have been read
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int idx = threadIdx.x + k * NT;
-      smem[(idx / L) * LP + spad(idx % L)] = r[k];
-    }
-    __syncthreads();
-    if (t + 1 < nterm) fetch(t + 1);
-    fft_stages<LOG2L, 0, DIR>(smem, tw);
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int idx = threadIdx.x + k * NT;
-      if (idx < B * nout) {
-        const int b = idx / nout, o = idx % nout;
-        if (seq0 + b < nseq) accs[idx] += op.value(t, seq0 + b, o, SeqView{smem + b * LP});
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = threadIdx.x + k * NT;
-    if (idx < B * nout) {
-      const int b = idx / nout, o = idx % nout;
-      if (seq0 + b < nseq) op.store(seq0 + b, o, accs[idx]);
-    }
-  }
-}
-
-template <int LOG2L, int DIR, class Op>
-int launch_pass_sum(const Op& op, const float2* tw, cudaStream_t s) {
-  using C = FftCfg<LOG2L>;
-  const int nblk = (op.nseq() + C::B - 1) / C::B;
-  if (nblk == 0) return FR_OK;
-  auto kern = fft_pass_sum_kernel<LOG2L, DIR, Op>;
-  constexpr size_t smem = C::SMEM + size_t(C::B) * C::L * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    attr = true;
-  }
-  kern<<<nblk, C::NT, smem, s>>>(op, tw);
   FR_LAUNCHED();
   return FR_OK;
 }
