@@ -9,6 +9,9 @@ With it:
   * PsfLikelihood / ExactLikelihood  L_b = 1/2 s_b.(A s_b) - s_b.d_b with A = PSF * (Sec. 3.3.2)
     or R^dagger N^-1 R: grad_s = (A s - d) * grad_L (A is self-adjoint), grad_d = -s * grad_L.
     The forward kernel already produces A s - d, so backward costs no extra launch.
+  * FastLikelihood  H_b = 1/2 r_b.(N'^-1 r_b), r = d - PSF * s (Eq. ham_new, Sec. 3.3.3, after
+    Plan.noise_fit): grad_s = -PSF * (N'^-1 r) * grad_H (from the forward kernel), and
+    grad_d = N'^-1 r * grad_H (N'^-1 symmetric; computed only when asked for).
 All arithmetic runs in the library's CUDA kernels through binding.Plan.
 """
 from __future__ import annotations
@@ -77,6 +80,30 @@ class PsfLikelihood(torch.autograd.Function):
         return gs, gd, None, None
 
 
+class FastLikelihood(torch.autograd.Function):
+    """H_b of Eq. ham_new for sky, dirty [batch, nsky, nx, ny] (or [nsky, nx, ny]); returns [batch]."""
+
+    @staticmethod
+    def forward(ctx, sky, dirty, plan):
+        value, grad = plan.fast_likelihood_grad(sky.contiguous(), dirty.contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(sky, dirty, grad)
+        return torch.as_tensor(value, dtype=torch.float64, device=sky.device)
+
+    @staticmethod
+    def backward(ctx, grad_value):
+        sky, dirty, grad = ctx.saved_tensors
+        gv = grad_value.to(torch.float32).view(-1, *([1] * (sky.dim() - 1)))
+        if sky.dim() == 3:
+            gv = gv.view(*([1] * sky.dim()))
+        gs = grad * gv if ctx.needs_input_grad[0] else None
+        gd = None
+        if ctx.needs_input_grad[1]:
+            r = dirty.contiguous() - ctx.plan.psf_apply(sky.contiguous())
+            gd = ctx.plan.noise_apply_inverse(r) * gv
+        return gs, gd, None
+
+
 def degrid(sky, plan):
     return Degrid.apply(sky, plan)
 
@@ -91,3 +118,7 @@ def psf_likelihood(sky, dirty, plan):
 
 def exact_likelihood(sky, dirty, plan):
     return PsfLikelihood.apply(sky, dirty, plan, True)
+
+
+def fast_likelihood(sky, dirty, plan):
+    return FastLikelihood.apply(sky, dirty, plan)

@@ -122,6 +122,31 @@ def test_noise_model_errors():
         p16.noise_fit(1.0)  # periodic 16-point transforms are below the FFT engine's range
 
 
+def test_fast_likelihood_autograd():
+    """torch.autograd through FastLikelihood: d/dsky is the kernel's gradient, d/ddirty is
+    N'^-1 r (checked against the oracle's N'^-1 with the GPU kernel)."""
+    from paper_2406_09144_gb300.autograd import fast_likelihood
+    obs, plan = make(nx=32, ny=32, wc=0.5, seed=63)
+    plan.noise_fit(3.0)
+    K = plan.noise_kernel().cpu().numpy().astype(np.float64)
+    _, psf, _ = plan.dirty_psf(want_dirty=False)
+    psf = psf.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(5)
+    sky = dev(rng.standard_normal((2, 1, 32, 32))).requires_grad_(True)
+    dirty = dev(rng.standard_normal((2, 1, 32, 32)) * 20.0).requires_grad_(True)
+    loss = (fast_likelihood(sky, dirty, plan) * torch.tensor([1.0, 2.0], dtype=torch.float64,
+                                                              device="cuda")).sum()
+    loss.backward()
+    _, g = plan.fast_likelihood_grad(sky.detach(), dirty.detach())
+    assert rel(sky.grad[0].cpu().numpy(), g[0].cpu().numpy()) <= 1e-6
+    assert rel(sky.grad[1].cpu().numpy(), 2 * g[1].cpu().numpy()) <= 1e-6
+    s64 = sky.detach().cpu().numpy().astype(np.float64)
+    d64 = dirty.detach().cpu().numpy().astype(np.float64)
+    for b, wgt in ((0, 1.0), (1, 2.0)):
+        r = d64[b] - oracle.psf_apply(psf, s64[b])
+        assert rel(dirty.grad[b].cpu().numpy(), wgt * noise.noise_inverse(r, K)) <= 1e-5
+
+
 @pytest.mark.slow
 def test_vla_full_size_noise_model():
     """VLA-like workload at full size: the fitted kernel is real, bounded below by eps and even
