@@ -15,7 +15,8 @@ Sections and equations cited:
   Eq. (rime), Sec. 2       - measurement equation R
   Eq. (ham), Sec. 3.1.2    - likelihood Hamiltonian, N^-1 = visibility weights
   Eq. (clean), Sec. 3.2    - R^dagger N^-1 R I = R^dagger N^-1 V, dirty image, PSF
-  Sec. 3.3.2               - PSF convolution on a 2x padded grid
+  Sec. 3.3.2               - PSF convolution on a 2x padded grid, and with reduced padding
+                             (the PSF truncated to the window the padded grid holds)
   Algorithm 1              - major-cycle residual d = I^D - R^dagger N^-1 R I
   Eq. (ham_new), Sec. 3.3.1, Sec. 3.3.3 (oracle.noise) - noise kernel K = exp(xi) + eps,
                              its fit, N'^-1 and the fast-resolve Hamiltonian
@@ -35,6 +36,9 @@ from .measurement import (  # noqa: F401
     grid,
     psf,
     psf_apply,
+    psf_window,
+    truncate_psf,
+    psf_apply_truncated,
     likelihood,
     likelihood_exact,
     residual_dirty,

@@ -179,6 +179,39 @@ def psf_apply(psf_img, sky):
     return out
 
 
+def psf_window(nx, ny, lx, ly):
+    """Half-widths (hx, hy) of the PSF window a zero-padded lx x ly grid holds without
+    wrap-around (reduced padding, Sec. 3.3.2): hx = min(lx - nx, nx - 1), hy likewise.
+    lx = 2nx, ly = 2ny give (nx - 1, ny - 1): every offset of the cropped product."""
+    return min(lx - nx, nx - 1), min(ly - ny, ny - 1)
+
+
+def truncate_psf(psf_img, hx, hy):
+    """The PSF image with the sidelobes at offsets |a| > hx or |b| > hy set to zero (the
+    reduced padding of Sec. 3.3.2 neglects them). psf_img [npsf, 2nx, 2ny] (offset (a, b) at
+    index (a + nx, b + ny)) -> same shape, float64."""
+    P = np.array(psf_img, dtype=np.float64)
+    if P.ndim == 2:
+        P = P[None]
+    _, nx2, ny2 = P.shape
+    a = np.arange(nx2) - nx2 // 2
+    b = np.arange(ny2) - ny2 // 2
+    keep = (np.abs(a)[:, None] <= hx) & (np.abs(b)[None, :] <= hy)
+    return P * keep[None]
+
+
+def psf_apply_truncated(psf_img, sky, lx, ly):
+    """PSF convolution with reduced padding (Sec. 3.3.2) on an lx x ly padded grid: the linear
+    convolution of psf_apply with the PSF truncated to the window psf_window(nx, ny, lx, ly).
+
+        out_b(p) = sum_{q in sky} PSF_t(p - q) s_b(q)
+    """
+    sky = np.asarray(sky, dtype=np.float64)
+    nx, ny = sky.shape[-2:]
+    hx, hy = psf_window(nx, ny, lx, ly)
+    return psf_apply(truncate_psf(psf_img, hx, hy), sky)
+
+
 def likelihood(psf_img, sky, dirty):
     """Likelihood in image space with the PSF approximation R^dagger N^-1 R ~ PSF * (Sec. 3.3.2):
     Eq. (ham) expanded with Eq. (clean) and constants dropped,

@@ -180,6 +180,84 @@ def test_psf_apply_equals_scipy_linear_convolution():
     assert _rel(oracle.psf_apply(P[None], s[None])[0], ref) < 1e-12
 
 
+# ---------------------------------------------------- reduced padding (truncated PSF, Sec. 3.3.2)
+
+def test_truncated_psf_with_full_padding_is_the_exact_convolution():
+    """lx = 2nx, ly = 2ny keep every offset the cropped product reaches: no truncation."""
+    rng = np.random.default_rng(30)
+    nx, ny = 10, 12
+    P = rng.standard_normal((2, 2 * nx, 2 * ny))
+    s = rng.standard_normal((2, nx, ny))
+    assert oracle.psf_window(nx, ny, 2 * nx, 2 * ny) == (nx - 1, ny - 1)
+    assert _rel(oracle.psf_apply_truncated(P, s, 2 * nx, 2 * ny), oracle.psf_apply(P, s)) < 1e-14
+
+
+def test_truncated_psf_delta_response_closed_form():
+    """A unit sky pixel at q returns PSF(p - q) inside the window |p - q| <= (hx, hy) (edges
+    included) and exactly zero outside it."""
+    rng = np.random.default_rng(31)
+    nx, ny, lx, ly = 12, 16, 15, 22
+    hx, hy = oracle.psf_window(nx, ny, lx, ly)
+    assert (hx, hy) == (3, 6)
+    P = rng.uniform(1.0, 2.0, (1, 2 * nx, 2 * ny))  # no zero inside: every kept offset shows
+    for q in [(0, 0), (nx - 1, ny - 1), (5, 7)]:
+        s = np.zeros((1, nx, ny))
+        s[0][q] = 1.0
+        out = oracle.psf_apply_truncated(P, s, lx, ly)[0]
+        for px in range(nx):
+            for py in range(ny):
+                a, b = px - q[0], py - q[1]
+                want = P[0, nx + a, ny + b] if abs(a) <= hx and abs(b) <= hy else 0.0
+                assert out[px, py] == want, (q, px, py)
+
+
+def _periodic_kernel(P, nx, ny, lx, ly, hx, hy):
+    K = np.zeros((lx, ly))
+    for a in range(-hx, hx + 1):
+        for b in range(-hy, hy + 1):
+            K[a % lx, b % ly] += P[nx + a, ny + b]
+    return K
+
+
+@pytest.mark.parametrize("lx,ly", [(15, 22), (20, 24), (13, 17), (16, 30)])
+def test_truncated_psf_equals_padded_fft_convolution(lx, ly):
+    """The padded FFT convolution of Sec. 3.3.2, P^dag FFT^-1[FFT[K] . FFT[P s]] on an lx x ly
+    grid with the periodic kernel K of the window, equals the truncated linear convolution
+    (numpy.fft); one offset more than the window and the period wraps it onto the crop."""
+    rng = np.random.default_rng(32)
+    nx, ny = 12, 16
+    P = rng.standard_normal((2 * nx, 2 * ny))
+    s = rng.standard_normal((nx, ny))
+    hx, hy = oracle.psf_window(nx, ny, lx, ly)
+    pad = np.zeros((lx, ly))
+    pad[:nx, :ny] = s
+
+    def fftconv(hx_, hy_):
+        K = _periodic_kernel(P, nx, ny, lx, ly, hx_, hy_)
+        return np.real(np.fft.ifft2(np.fft.fft2(K) * np.fft.fft2(pad)))[:nx, :ny]
+
+    ref = oracle.psf_apply_truncated(P[None], s[None], lx, ly)[0]
+    assert _rel(fftconv(hx, hy), ref) < 1e-12
+    if hx + 1 <= nx - 1:  # a wider window aliases: the window rule is the largest exact one
+        wide = oracle.psf_apply(oracle.truncate_psf(P[None], hx + 1, hy), s[None])[0]
+        assert _rel(fftconv(hx + 1, hy), wide) > 1e-3
+
+
+def test_truncation_error_bounded_by_dropped_sidelobes():
+    """|PSF_t * s - PSF * s| <= (sum of |PSF| outside the window) max|s| at every pixel (Young)."""
+    obs = _tiny_w0_obs(nchan=1, seed=33)
+    nx, ny, dl = obs.nx, obs.ny, obs.pixsize
+    P = oracle.psf(obs.uvw, obs.freqs, dl, dl, nx, ny, obs.weights)
+    s = np.random.default_rng(34).uniform(0, 1, (1, nx, ny))
+    full = oracle.psf_apply(P, s)
+    for lx, ly in [(nx + 2, ny + 3), (nx + nx // 2, 2 * ny), (2 * nx, ny + 4)]:
+        hx, hy = oracle.psf_window(nx, ny, lx, ly)
+        dropped = np.abs(P - oracle.truncate_psf(P, hx, hy)).sum()
+        err = np.abs(oracle.psf_apply_truncated(P, s, lx, ly) - full).max()
+        assert err <= dropped * s.max() * (1 + 1e-12)
+        assert err > 0
+
+
 def test_psf_per_channel_sums_to_mfs_psf():
     obs = _tiny_w0_obs(nchan=3, seed=12)
     a = oracle.psf(obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, obs.nx, obs.ny, obs.weights, nsky=3)
