@@ -375,6 +375,59 @@ def main():
                    "major_cycle_ms": t_major / args.steps,
                    "eps_noise": eps_noise}
 
+    # reduced padding (Sec. 3.3.2): the PSF likelihood on lx x ly padded grids, the PSF
+    # truncated to the window they hold, against the full 2nx x 2ny padding; a batch of skies
+    # larger than L2, rate and bytes of the PSF passes, and the truncation error
+    reduced = None
+    if rank == 0:
+        nb = max(1, 32 // obs.nsky)
+        skies = torch.from_numpy(np.stack([synth.sky_image(obs.nx, obs.ny, seed=100 + i)
+                                           for i in range(nb)]).astype(np.float32)[:, None]
+                                 .repeat(obs.nsky, axis=1)).to(dev)
+        dirt = skies.flip(-1).contiguous()
+        gb = torch.empty_like(skies)
+        rows = []
+        ref_out = None
+        lengths = [(L, L2) for L, L2 in zip(B.padded_lengths(obs.nx), B.padded_lengths(obs.ny))]
+        for lx, ly in reversed(lengths):  # full padding first: the reference output
+            plan.set_psf_padding(lx, ly)
+            out = plan.psf_apply(skies)
+            for _ in range(3):
+                plan.likelihood_grad(skies, dirt, grad=gb, want_value=False)
+            torch.cuda.synchronize()
+            B.profile_enable(True)
+            t = 0.0
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                plan.likelihood_grad(skies, dirt, grad=gb, want_value=False)
+                b.record(stream)
+                b.synchronize()
+                t += a.elapsed_time(b)
+            pc = B.profile_read()
+            B.profile_enable(False)
+            pms = sum(pc[k][0] for k in ("psf_rows", "psf_cols") if k in pc)
+            pby = sum(pc[k][1] for k in ("psf_rows", "psf_cols") if k in pc)
+            if ref_out is None:
+                ref_out = out.clone()
+            err = float(torch.linalg.vector_norm((out - ref_out).double()) /
+                        torch.linalg.vector_norm(ref_out.double()))
+            ms = t / args.steps
+            rows.append({"lx": lx, "ly": ly,
+                         "window": [min(lx - obs.nx, obs.nx - 1), min(ly - obs.ny, obs.ny - 1)],
+                         "likelihood_ms": ms,
+                         "mpix_s": nb * obs.nsky * obs.nx * obs.ny / (ms * 1e-3) / 1e6,
+                         "psf_passes_GBps": pby / (pms * 1e-3) / 1e9 if pms else None,
+                         "psf_passes_frac_of_measured_hbm": (pby / (pms * 1e-3) / 1e9 / peak)
+                         if pms else None,
+                         "rel_err_vs_full_padding": err})
+        plan.set_psf_padding(2 * obs.nx, 2 * obs.ny)
+        reduced = {"batch": nb, "sky": "point+blob skies, one per batch element",
+                   "rows": rows}
+        del skies, dirt, gb, out, ref_out
+        torch.cuda.synchronize()
+
     # end to end through the C ABI with host buffers: H2D sky + vis, R and R^dag, D2H results
     e2e = None
     if True:
@@ -450,7 +503,7 @@ def main():
             "psf_likelihood_ms": t_psf / args.steps,
             "plan_s": plan_s,
             "plan": {k: info[k] for k in ("support", "wplanes_total", "work_items", "grid_nu")},
-            "minor_major": minor_major, "roofline_alu": alu,
+            "minor_major": minor_major, "psf_reduced_padding": reduced, "roofline_alu": alu,
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
         }

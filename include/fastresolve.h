@@ -100,10 +100,29 @@ int fr_dirty_psf(fr_plan_t plan, const fr_cf32 *vis, float *dirty, float *psf, d
                  void *stream);
 
 /* PSF convolution (Sec. 3.3.2): out = P^dag FFT^-1[FFT[PSF] . FFT[P sky]], i.e. the linear
- * convolution out(p) = sum_q PSF(p - q) sky(q) cropped to the image.
+ * convolution out(p) = sum_q PSF_t(p - q) sky(q) cropped to the image, on the lx x ly padded
+ * grid set by fr_psf_set_padding (default 2nx x 2ny: PSF_t = PSF, the exact convolution).
  *   sky, out  device [batch][nsky][nx][ny]; image b*nsky + s uses the PSF of image s.
  *   batch     >= 1 */
 int fr_psf_apply(fr_plan_t plan, const float *sky, int32_t batch, float *out, void *stream);
+
+/* Reduced padding (Sec. 3.3.2): the PSF convolution of fr_psf_apply, fr_likelihood_grad
+ * (exact == 0), fr_fast_likelihood_grad and the serving path runs on an lx x ly zero-padded
+ * grid with the PSF truncated to offsets |a| <= hx = min(lx - nx, nx - 1), |b| <= hy =
+ * min(ly - ny, ny - 1) (sidelobes beyond them neglected):
+ *   out(p) = sum_q PSF_t(p - q) sky(q),  PSF_t(a, b) = PSF(a, b) inside the window, else 0,
+ * which the lx-periodic transforms compute exactly. Smaller lx, ly move fewer bytes and lose
+ * the truncated sidelobes; lx = 2nx, ly = 2ny restore the whole PSF.
+ *   lx, ly  even, nx < lx <= 2nx, ny < ly <= 2ny, each 2^k (32..16384), 3 2^k (48..6144) or
+ *           5 2^k (80..5120)
+ * Rebuilds the plan's transfer function in place on `stream` and synchronises it: no PSF call
+ * on this plan may be in flight on any stream, and CUDA graphs captured before keep the old
+ * lengths (capture again). Errors: FR_EINVAL (range, parity, FR_NO_PSF plan), FR_EUNSUPPORTED
+ * (a length of another form), FR_ENOMEM, FR_ECUDA; on error the previous padding stays. */
+int fr_psf_set_padding(fr_plan_t plan, int32_t lx, int32_t ly, void *stream);
+
+/* The current padded lengths (host outputs). FR_EINVAL for a FR_NO_PSF plan. */
+int fr_psf_padding(fr_plan_t plan, int32_t *lx, int32_t *ly);
 
 /* Likelihood value and gradient (Eq. ham with Eq. clean, constants dropped):
  *   L_b = 1/2 s_b^T (A s_b) - s_b^T d_b,  grad_b = A s_b - d_b
@@ -223,10 +242,11 @@ int fr_profile_read(double *ms, double *bytes, uint64_t *launches, int32_t ncat)
 const char *fr_profile_category(int32_t cat);
 
 /* Host-only check of the FFT passes' Stockham index and butterfly arithmetic: transforms
- * `batch` sequences of 2^log2l complex values in place (interleaved float32 re, im) on the CPU
- * with the same stage code the kernels use. dir = -1 forward, +1 inverse (unnormalised).
- * Returns FR_EINVAL for log2l outside [1, 14]. Test support; needs no GPU. */
-int fr_selftest_fft_host(float *data, int32_t log2l, int32_t batch, int32_t dir);
+ * `batch` sequences of n complex values in place (interleaved float32 re, im) on the CPU
+ * with the same stage code and radix schedule the kernels use. dir = -1 forward, +1 inverse
+ * (unnormalised). Returns FR_EINVAL unless 2 <= n <= 16384 with n = 2^k 3^a 5^b. Test
+ * support; needs no GPU. */
+int fr_selftest_fft_host(float *data, int32_t n, int32_t batch, int32_t dir);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,8 @@ EXPORTS = ["fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_app
            "fr_likelihood_grad", "fr_major_cycle", "fr_plan_get_info", "fr_plan_footprint",
            "fr_plan_check", "fr_plan_destroy", "fr_strerror", "fr_last_error", "fr_launch_count",
            "fr_selftest_fft_host", "fr_psf_convolve_noalloc", "fr_noise_fit", "fr_noise_kernel",
-           "fr_noise_apply_inverse", "fr_fast_likelihood_grad"]
+           "fr_noise_apply_inverse", "fr_fast_likelihood_grad", "fr_psf_set_padding",
+           "fr_psf_padding"]
 
 
 class FastResolveError(RuntimeError):
@@ -67,6 +68,8 @@ def load(path: str = LIB_PATH):
     lib.fr_noise_kernel.argtypes = [P, P, P]
     lib.fr_noise_apply_inverse.argtypes = [P, P, I32, P, P]
     lib.fr_fast_likelihood_grad.argtypes = [P, P, P, I32, P, P, P]
+    lib.fr_psf_set_padding.argtypes = [P, I32, I32, P]
+    lib.fr_psf_padding.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
     lib.fr_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
     lib.fr_plan_footprint.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
     lib.fr_plan_check.argtypes = [P, P]
@@ -90,7 +93,7 @@ def load(path: str = LIB_PATH):
     lib.fr_psf_convolve_noalloc.restype = ctypes.c_int
     for name in ("fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
                  "fr_likelihood_grad", "fr_major_cycle", "fr_plan_get_info", "fr_plan_footprint",
-                 "fr_plan_check", "fr_selftest_fft_host"):
+                 "fr_plan_check", "fr_selftest_fft_host", "fr_psf_set_padding", "fr_psf_padding"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -125,12 +128,25 @@ def profile_read() -> dict:
 
 
 def selftest_fft_host(x: np.ndarray, direction: int) -> np.ndarray:
-    """Run the FFT passes' stage arithmetic on the CPU (no GPU): x complex [batch, 2^k]."""
+    """Run the FFT passes' stage arithmetic on the CPU (no GPU): x complex [batch, n],
+    n = 2^k 3^a 5^b."""
     a = np.ascontiguousarray(x, dtype=np.complex64).copy()
     batch, n = a.shape
-    lg = int(n).bit_length() - 1
-    check(load().fr_selftest_fft_host(a.ctypes.data, lg, batch, direction))
+    check(load().fr_selftest_fft_host(a.ctypes.data, n, batch, direction))
     return a
+
+
+def padded_lengths(n: int):
+    """The padded PSF transform lengths fr_psf_set_padding takes for an image side n: even
+    L in (n, 2n] of the form 2^k (32..16384), 3 2^k (48..6144) or 5 2^k (80..5120)."""
+    out = []
+    for c, lo, hi in ((1, 32, 16384), (3, 48, 6144), (5, 80, 5120)):
+        L = c * 16
+        while L <= min(2 * n, hi):
+            if L > n and L >= lo:
+                out.append(L)
+            L *= 2
+    return sorted(out)
 
 
 # ------------------------------------------------------------------------------- torch side
@@ -271,6 +287,18 @@ class Plan:
         check(load().fr_psf_apply(self._h, _dev(sky, torch.float32, shape, "sky"), batch,
                                   _dev(out, torch.float32, shape, "out"), _stream_ptr(stream)))
         return out
+
+    def set_psf_padding(self, lx, ly, stream=None):
+        """Reduced padding (Sec. 3.3.2): run the PSF convolutions on an lx x ly grid with the
+        PSF truncated to |a| <= min(lx - nx, nx - 1), |b| <= min(ly - ny, ny - 1);
+        lx = 2 nx, ly = 2 ny is the exact default. See padded_lengths()."""
+        check(load().fr_psf_set_padding(self._h, int(lx), int(ly), _stream_ptr(stream)))
+
+    @property
+    def psf_padding(self):
+        lx, ly = ctypes.c_int32(), ctypes.c_int32()
+        check(load().fr_psf_padding(self._h, ctypes.byref(lx), ctypes.byref(ly)))
+        return lx.value, ly.value
 
     def likelihood_grad(self, sky, dirty, exact=False, grad=None, want_value=True, stream=None):
         """L = 1/2 s.(A s) - s.d and grad = A s - d with A = PSF * or R^dagger N^-1 R."""

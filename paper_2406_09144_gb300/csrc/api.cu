@@ -196,8 +196,7 @@ int zero_psf_edges(float* psf, int nsky, int nx2, int ny2, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------ twiddles
-static int make_twiddles(float2** out, int log2l, cudaStream_t s) {
-  const int L = 1 << log2l;
+static int make_twiddles(float2** out, int L, cudaStream_t s) {
   std::vector<float2> h(L);
   for (int m = 0; m < L; ++m) {
     const double a = -2.0 * M_PI * (double)m / (double)L;
@@ -215,10 +214,34 @@ int ensure_twiddles(fr_plan* p, int log2l, cudaStream_t s) {
     return FR_EUNSUPPORTED;
   }
   if (!p->tw[log2l]) {
-    FR_TRY(make_twiddles(&p->tw[log2l], log2l, s));
+    FR_TRY(make_twiddles(&p->tw[log2l], 1 << log2l, s));
     p->resident += ((size_t)1 << log2l) * sizeof(float2);
   }
   return FR_OK;
+}
+
+// twiddle table of any length the PSF passes take (power of two or 3 2^k, 5 2^k)
+static int ensure_twiddles_len(fr_plan* p, int L, cudaStream_t s) {
+  if (!fft_len_supported(L)) {
+    set_error("FFT length %d unsupported", L);
+    return FR_EUNSUPPORTED;
+  }
+  if ((L & (L - 1)) == 0) return ensure_twiddles(p, ilog2(L), s);
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (!p->tw_mixed.count(L)) {
+    float2* t = nullptr;
+    FR_TRY(make_twiddles(&t, L, s));
+    p->tw_mixed[L] = t;
+    p->resident += (size_t)L * sizeof(float2);
+  }
+  return FR_OK;
+}
+
+static const float2* twiddles_of(fr_plan* p, int L) {
+  if ((L & (L - 1)) == 0) return p->tw[ilog2(L)];
+  std::lock_guard<std::mutex> lk(p->mu);
+  auto it = p->tw_mixed.find(L);
+  return it == p->tw_mixed.end() ? nullptr : it->second;
 }
 
 // ------------------------------------------------------------------------ workspaces
@@ -544,8 +567,10 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
   }
   if (r == FR_OK) r = zero_psf_edges(p->psf_img, p->nsky, pg.nx, pg.ny, s);
   if (r == FR_OK)
-    r = build_transfer(p->geo.nx, p->geo.ny, p->nsky, p->psf_img, h, p->transfer,
+    r = build_transfer(p->geo.nx, p->geo.ny, p->nsky, p->psf_img, pg.nx, pg.ny, h, p->transfer,
                        p->tw[ilog2(pg.ny)], p->tw[ilog2(pg.nx)], s);
+  p->psf_lx = pg.nx;
+  p->psf_ly = pg.ny;
   // psf_norm = sum of the kept weights per image (FP64)
   double* d_norm = nullptr;
   if (r == FR_OK) {
@@ -737,6 +762,7 @@ static void plan_free(fr_plan* p) {
   cudaFree(p->noise_kinv);
   cudaFree(p->status);
   for (float2*& t : p->tw) cudaFree(t);
+  for (auto& kv : p->tw_mixed) cudaFree(kv.second);
   delete p;
 }
 
@@ -747,16 +773,17 @@ static void host_stage(const float2* in, float2* out, const float2* tw, int L, i
 }
 
 template <int DIR>
-static void host_fft(float2* buf, float2* tmp, const float2* tw, int log2l) {
-  const int L = 1 << log2l;
+static void host_fft(float2* buf, float2* tmp, const float2* tw, int L) {
   int Ns = 1;
   float2* a = buf;
   float2* b = tmp;
-  for (int st = 0; st < num_stages(log2l); ++st) {
-    const int R = 1 << stage_bits(log2l, st);
+  for (int st = 0; st < fft_num_stages(L); ++st) {
+    const int R = fft_radix(L, st);
     switch (R) {
       case 2: host_stage<2, DIR>(a, b, tw, L, Ns); break;
+      case 3: host_stage<3, DIR>(a, b, tw, L, Ns); break;
       case 4: host_stage<4, DIR>(a, b, tw, L, Ns); break;
+      case 5: host_stage<5, DIR>(a, b, tw, L, Ns); break;
       case 8: host_stage<8, DIR>(a, b, tw, L, Ns); break;
       default: host_stage<16, DIR>(a, b, tw, L, Ns); break;
     }
@@ -898,12 +925,15 @@ static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, 
   Workspace* w;
   FR_TRY(get_ws(p, s, &w));
   const int nimg = batch * p->nsky;
-  const int hp = p->geo.ny + 4;  // ny + 1 bins, pitch a multiple of 4 (32-byte group stores)
-  const size_t hsize = (size_t)nimg * p->geo.nx * hp;  // H, then HT ([nimg][ny+1][nx])
-  FR_TRY(ws_reserve_h(w, hsize + (size_t)nimg * (p->geo.ny + 1) * p->geo.nx));
+  const int lx = p->psf_lx, ly = p->psf_ly, nq = ly / 2 + 1;
+  const int hp = (nq + 3) & ~3;  // ly/2 + 1 bins, pitch a multiple of 4 (32-byte group stores)
+  const size_t hsize = (size_t)nimg * p->geo.nx * hp;  // H, then HT ([nimg][ly/2+1][nx])
+  FR_TRY(ws_reserve_h(w, hsize + (size_t)nimg * nq * p->geo.nx));
   PsfArgs a;
   a.nx = p->geo.nx;
   a.ny = p->geo.ny;
+  a.lx = lx;
+  a.ly = ly;
   a.nimg = nimg;
   a.nsky = p->nsky;
   a.hp = hp;
@@ -917,8 +947,7 @@ static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, 
     FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, batch * sizeof(double), s));
     a.value = w->red;
   }
-  FR_TRY(psf_apply_passes(a, w->h, w->h + hsize, p->tw[ilog2(2 * a.ny)], p->tw[ilog2(2 * a.nx)],
-                          s));
+  FR_TRY(psf_apply_passes(a, w->h, w->h + hsize, twiddles_of(p, ly), twiddles_of(p, lx), s));
   if (dirty && value) {
     FR_CUDA_TRY(cudaMemcpyAsync(value, w->red, batch * sizeof(double), cudaMemcpyDeviceToHost, s));
     FR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -932,6 +961,55 @@ int fr_psf_apply(fr_plan_t p, const float* sky, int32_t batch, float* out, void*
     return FR_EINVAL;
   }
   return psf_common(p, sky, batch, out, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int fr_psf_set_padding(fr_plan_t p, int32_t lx, int32_t ly, void* stream) {
+  if (!p) {
+    set_error("plan must be non-null");
+    return FR_EINVAL;
+  }
+  if (!p->has_psf) {
+    set_error("plan was created with FR_NO_PSF");
+    return FR_EINVAL;
+  }
+  const int nx = p->geo.nx, ny = p->geo.ny;
+  if (lx <= nx || lx > 2 * nx || ly <= ny || ly > 2 * ny || (lx & 1) || (ly & 1)) {
+    set_error("padded PSF lengths %d x %d: need even nx < lx <= 2nx, ny < ly <= 2ny (%d x %d image)",
+              lx, ly, nx, ny);
+    return FR_EINVAL;
+  }
+  if (!psf_padding_ok(nx, ny, lx, ly)) {
+    set_error("padded PSF lengths %d x %d: each must be 2^k (32..16384), 3 2^k (48..6144) or "
+              "5 2^k (80..5120)", lx, ly);
+    return FR_EUNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  FR_TRY(ensure_twiddles_len(p, lx, s));
+  FR_TRY(ensure_twiddles_len(p, ly, s));
+  float2* ht = nullptr;
+  FR_CUDA_TRY(cudaMallocAsync(&ht, (size_t)p->nsky * (ly / 2 + 1) * lx * sizeof(float2), s));
+  const int r = build_transfer(nx, ny, p->nsky, p->psf_img, lx, ly, ht, p->transfer,
+                               twiddles_of(p, ly), twiddles_of(p, lx), s);
+  cudaFreeAsync(ht, s);
+  if (r != FR_OK) return r;
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  p->psf_lx = lx;
+  p->psf_ly = ly;
+  return FR_OK;
+}
+
+int fr_psf_padding(fr_plan_t p, int32_t* lx, int32_t* ly) {
+  if (!p || !lx || !ly) {
+    set_error("plan, lx, ly must be non-null");
+    return FR_EINVAL;
+  }
+  if (!p->has_psf) {
+    set_error("plan was created with FR_NO_PSF");
+    return FR_EINVAL;
+  }
+  *lx = p->psf_lx;
+  *ly = p->psf_ly;
+  return FR_OK;
 }
 
 int fr_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, int32_t batch,
@@ -1224,12 +1302,13 @@ int fr_plan_check(fr_plan_t p, void* stream) {
   return FR_OK;
 }
 
-int fr_selftest_fft_host(float* data, int32_t log2l, int32_t batch, int32_t dir) {
-  if (!data || log2l < 1 || log2l > 14 || batch < 1 || (dir != 1 && dir != -1)) {
+int fr_selftest_fft_host(float* data, int32_t n, int32_t batch, int32_t dir) {
+  if (!data || n < 2 || n > 16384 || batch < 1 || (dir != 1 && dir != -1) ||
+      strip_factor(strip_factor(odd_part(n), 5), 3) != 1) {
     set_error("bad arguments to fr_selftest_fft_host");
     return FR_EINVAL;
   }
-  const int L = 1 << log2l;
+  const int L = n;
   std::vector<float2> tw(L), a(spad_len(L)), b(spad_len(L));
   for (int m = 0; m < L; ++m) {
     const double ang = -2.0 * M_PI * (double)m / (double)L;
@@ -1239,9 +1318,9 @@ int fr_selftest_fft_host(float* data, int32_t log2l, int32_t batch, int32_t dir)
     float2* x = reinterpret_cast<float2*>(data) + (size_t)q * L;
     for (int i = 0; i < L; ++i) a[spad(i)] = x[i];
     if (dir < 0)
-      host_fft<-1>(a.data(), b.data(), tw.data(), log2l);
+      host_fft<-1>(a.data(), b.data(), tw.data(), L);
     else
-      host_fft<1>(a.data(), b.data(), tw.data(), log2l);
+      host_fft<1>(a.data(), b.data(), tw.data(), L);
     for (int i = 0; i < L; ++i) x[i] = a[spad(i)];
   }
   return FR_OK;

@@ -1,8 +1,10 @@
-// Radix-2/4/8/16 Stockham FFT building blocks shared by every FFT pass kernel.
+// Radix-2/3/4/5/8/16 Stockham FFT building blocks shared by every FFT pass kernel.
 //
 // The FFT passes implement the FFT[...] / FFT^-1[...] of the padded PSF convolution
 // (Sec. 3.3.2) and the oversampled-grid transforms of the measurement operator R (Eq. rime)
-// and its adjoint. Only power-of-two lengths are supported.
+// and its adjoint. Lengths are L = c 2^k with an odd part c made of factors 3 and 5 (the
+// reduced-padding PSF transforms use 3 2^k and 5 2^k; everything else is a power of two): one
+// radix-3 or radix-5 stage per odd factor runs first, then the power-of-two stages.
 //
 // A Stockham stage with radix R and current sub-transform size Ns maps, for each butterfly
 // task j in [0, L/R):
@@ -39,7 +41,7 @@ FR_HD float2 mul_i(float2 a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// In-register DFTs of size 2, 4, 8, 16 with exponent sign DIR (-1 forward, +1 inverse).
+// In-register DFTs of size 2, 3, 4, 5, 8, 16 with exponent sign DIR (-1 forward, +1 inverse).
 // Input and output in natural order.
 // ---------------------------------------------------------------------------------------
 template <int DIR>
@@ -132,16 +134,54 @@ FR_HD void dft16(float2* v) {
   }
 }
 
+// DFT_3: X_k = sum_n x_n w^(nk), w = exp(DIR 2 pi i / 3) = -1/2 + DIR i sqrt(3)/2
+template <int DIR>
+FR_HD void dft3(float2* v) {
+  const float s3 = 0.86602540378443864676f;  // sin(2 pi / 3)
+  const float2 a = v[0], sum = cadd(v[1], v[2]);
+  const float2 m = make_float2(a.x - 0.5f * sum.x, a.y - 0.5f * sum.y);
+  const float2 d = cscale(mul_i<DIR>(csub(v[1], v[2])), s3);
+  v[0] = cadd(a, sum);
+  v[1] = cadd(m, d);
+  v[2] = csub(m, d);
+}
+
+// DFT_5 from the symmetric pairs (x1 + x4, x2 + x3) and antisymmetric pairs (x1 - x4, x2 - x3):
+//   X_1,4 = x0 + c1 p1 + c2 p2 +- DIR i (s1 q1 + s2 q2)
+//   X_2,3 = x0 + c2 p1 + c1 p2 +- DIR i (s2 q1 - s1 q2)
+// with c_j = cos(2 pi j / 5), s_j = sin(2 pi j / 5)
+template <int DIR>
+FR_HD void dft5(float2* v) {
+  const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+  const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+  const float2 x0 = v[0];
+  const float2 p1 = cadd(v[1], v[4]), p2 = cadd(v[2], v[3]);
+  const float2 q1 = csub(v[1], v[4]), q2 = csub(v[2], v[3]);
+  const float2 a1 = make_float2(x0.x + c1 * p1.x + c2 * p2.x, x0.y + c1 * p1.y + c2 * p2.y);
+  const float2 a2 = make_float2(x0.x + c2 * p1.x + c1 * p2.x, x0.y + c2 * p1.y + c1 * p2.y);
+  const float2 b1 = mul_i<DIR>(make_float2(s1 * q1.x + s2 * q2.x, s1 * q1.y + s2 * q2.y));
+  const float2 b2 = mul_i<DIR>(make_float2(s2 * q1.x - s1 * q2.x, s2 * q1.y - s1 * q2.y));
+  v[0] = cadd(x0, cadd(p1, p2));
+  v[1] = cadd(a1, b1);
+  v[4] = csub(a1, b1);
+  v[2] = cadd(a2, b2);
+  v[3] = csub(a2, b2);
+}
+
 template <int R, int DIR>
 FR_HD void dft_r(float2* v) {
-  if constexpr (R == 2) {
+  if constexpr (R == 3) {
+    dft3<DIR>(v);
+  } else if constexpr (R == 5) {
+    dft5<DIR>(v);
+  } else if constexpr (R == 2) {
     dft2<DIR>(v[0], v[1]);
   } else if constexpr (R == 4) {
     dft4<DIR>(v[0], v[1], v[2], v[3]);
   } else if constexpr (R == 8) {
     dft8<DIR>(v);
   } else {
-    static_assert(R == 16, "radix must be 2, 4, 8 or 16");
+    static_assert(R == 16, "radix must be 2, 3, 4, 5, 8 or 16");
     dft16<DIR>(v);
   }
 }
@@ -154,6 +194,25 @@ constexpr int stage_bits(int log2l, int s) {
   return log2l / num_stages(log2l) + (s < (log2l % num_stages(log2l)) ? 1 : 0);
 }
 constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+// Mixed lengths L = c 2^k: the exponent k, the odd part c, its factors (5s first, then 3s) and
+// the full stage schedule (odd stages, then the power-of-two schedule of 2^k).
+constexpr int pow2_exp(int L) { return (L > 1 && (L & 1) == 0) ? 1 + pow2_exp(L >> 1) : 0; }
+constexpr int odd_part(int L) { return L >> pow2_exp(L); }
+constexpr int count_factor(int c, int f) { return (c > 1 && c % f == 0) ? 1 + count_factor(c / f, f) : 0; }
+constexpr int strip_factor(int c, int f) { return (c > 1 && c % f == 0) ? strip_factor(c / f, f) : c; }
+// lengths the pass kernels take: 16 | L (16 points per thread) and c a product of 3s and 5s
+constexpr bool fft_length_ok(int L) {
+  return L >= 16 && L % 16 == 0 && strip_factor(strip_factor(odd_part(L), 5), 3) == 1;
+}
+constexpr int odd_stages(int L) { return count_factor(odd_part(L), 5) + count_factor(odd_part(L), 3); }
+constexpr int fft_num_stages(int L) { return odd_stages(L) + num_stages(pow2_exp(L)); }
+constexpr int fft_radix(int L, int s) {
+  return s < count_factor(odd_part(L), 5) ? 5
+         : s < odd_stages(L)              ? 3
+                                          : 1 << stage_bits(pow2_exp(L), s - odd_stages(L));
+}
+constexpr int fft_ns_before(int L, int st) { return st == 0 ? 1 : fft_radix(L, st - 1) * fft_ns_before(L, st - 1); }
 
 // Shared-memory padding: one float2 of padding after every 16 elements breaks the
 // power-of-two strides of the Stockham scatter.
@@ -175,6 +234,40 @@ FR_HD void twiddle_rec(float2* v, const float2* pw, float2* wr) {
   }
 }
 
+FR_HD float2 ld_tw(const float2* p) {
+#ifdef __CUDA_ARCH__
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
+
+// v[r] *= w^(r k), w = exp(DIR 2 pi i / (Ns R)) = tw[tstep] (conjugated for DIR = +1), tstep =
+// L / (Ns R). Power-of-two radices build w^(r k) from the log2(R) entries w^(k 2^e) (a few
+// ulp, log2(R) loads); radix 3 and 5 load their R - 1 entries tw[r k tstep] (r k tstep < L).
+template <int R, int DIR>
+FR_HD void apply_twiddles(float2* v, const float2* tw, int k, int tstep) {
+  if constexpr ((R & (R - 1)) == 0) {
+    constexpr int LB = ilog2(R);
+    float2 pw[LB];
+#pragma unroll
+    for (int e = 0; e < LB; ++e) {
+      float2 w = ld_tw(&tw[(k * tstep) << e]);
+      if (DIR > 0) w.y = -w.y;
+      pw[e] = w;
+    }
+    float2 wr[R];
+    twiddle_rec<R, 1>(v, pw, wr);
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = ld_tw(&tw[r * k * tstep]);
+      if (DIR > 0) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+  }
+}
+
 // One Stockham stage on a single task j, reading from `in` and writing to `out`
 // (both indexed through spad), with the same twiddle construction as the kernels; used by the
 // host emulation tests.
@@ -186,17 +279,7 @@ FR_HD void stockham_task(const float2* in, float2* out, const float2* tw, int L,
   const int tstep = L / (Ns * R);
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = in[spad(j + r * stride)];
-  if (Ns > 1) {
-    constexpr int LB = ilog2(R);
-    float2 pw[LB];
-    for (int e = 0; e < LB; ++e) {
-      float2 w = tw[(k * tstep) << e];
-      if (DIR > 0) w.y = -w.y;
-      pw[e] = w;
-    }
-    float2 wr[R];
-    twiddle_rec<R, 1>(v, pw, wr);
-  }
+  if (Ns > 1) apply_twiddles<R, DIR>(v, tw, k, tstep);
   dft_r<R, DIR>(v);
   const int base = (j / Ns) * Ns * R + k;
 #pragma unroll

@@ -1,7 +1,7 @@
 // Shared-memory FFT engine and the generic FFT pass kernel.
 //
 // Every pass reads the sequences it transforms from contiguous memory: a CTA loads B
-// sequences of length L = 2^LOG2L (register-staged, 16 complex values per thread, all loads in
+// sequences of length L (a supported length of fft_core.cuh; register-staged, 16 complex values per thread, all loads in
 // flight before the first shared-memory store), runs the Stockham stages of fft_core.cuh
 // on them in shared memory (sequence b at b * LP, element i at spad(i)), and hands them to the
 // pass's store, which writes either along the sequence (row-major) or across the B sequences
@@ -13,77 +13,76 @@
 
 namespace fr {
 
-template <int LOG2L>
+constexpr int pow2_floor(int x) { return x < 2 ? 1 : 2 * pow2_floor(x / 2); }
+
+template <int LEN>
 struct FftCfg {
-  static constexpr int L = 1 << LOG2L;
-  // L = 8192 and 16384 run one sequence per CTA so that two CTAs share an SM and overlap
-  // their load, transform and store phases; L = 4096 keeps two (16-byte transposed stores)
-  static constexpr int B = (L >= 8192) ? 1 : (L >= 4096 ? 2 : 4096 / L);
+  static_assert(fft_length_ok(LEN), "unsupported FFT length");
+  static constexpr int L = LEN;
+  // L >= 8192 runs one sequence per CTA so that two CTAs share an SM and overlap their load,
+  // transform and store phases; 4096 <= L < 8192 keeps two (16-byte transposed stores)
+  static constexpr int B = (L >= 8192) ? 1 : (L >= 4096 ? 2 : pow2_floor(4096 / L));
   static constexpr int NT = (B * L) / 16;     // threads: 16 points each
   static constexpr int LP = spad_len(L) + 1;  // odd stride between sequences
   static constexpr size_t SMEM = size_t(B) * LP * sizeof(float2);
-  // CTAs per SM the register budget is sized for: four at L = 2048 (64 registers, no spills)
-  static constexpr int MINB = NT >= 1024 ? 1 : (NT >= 512 || LOG2L < 11 ? 2 : 4);
-  static constexpr int MINB_SUM = NT >= 512 ? 1 : 2;  // multi-output passes
-  static constexpr int MINB_TWO = NT >= 1024 ? 1 : 2;  // two-transform passes
+  // CTAs per SM the register budget is sized for: four at L = 2048 (64 registers, no spills);
+  // never fewer than 64 registers a thread (the 640- and 768-thread CTAs of 5 2^k and 3 2^k)
+  static constexpr int FIT64 = 65536 / (NT * 64) > 1 ? 65536 / (NT * 64) : 1;
+  static constexpr int cap(int m) { return m < FIT64 ? m : FIT64; }
+  // the 3 2^k and 5 2^k lengths (160- to 768-thread CTAs) target 64 registers outright
+  // (measured 18 % faster at 1536 than the power-of-two rule, which let 110 registers through)
+  static constexpr bool POW2 = (L & (L - 1)) == 0;
+  static constexpr int MINB =
+      POW2 ? cap(NT >= 1024 ? 1 : (NT >= 512 || L < 2048 ? 2 : 4)) : FIT64;
+  static constexpr int MINB_SUM = cap(NT >= 512 ? 1 : 2);  // multi-output passes
+  // two-transform passes; the mixed lengths one CTA below the 64-register count (measured
+  // fastest at 1280 and 1536: 72 and 80 registers, small spills)
+  static constexpr int MINB_TWO = POW2 ? cap(NT >= 1024 ? 1 : 2) : (FIT64 > 1 ? FIT64 - 1 : 1);
 };
 
-constexpr int ns_before(int log2l, int st) {
-  int b = 0;
-  for (int s = 0; s < st; ++s) b += stage_bits(log2l, s);
-  return 1 << b;
-}
-
-template <int LOG2L, int ST, int DIR>
+template <int L, int ST, int DIR>
 __device__ __forceinline__ void fft_stages(float2* s, const float2* __restrict__ tw) {
-  if constexpr (ST < num_stages(LOG2L)) {
-    using C = FftCfg<LOG2L>;
-    constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
-    constexpr int R = 1 << stage_bits(LOG2L, ST);
-    constexpr int NS = ns_before(LOG2L, ST);
+  if constexpr (ST < fft_num_stages(L)) {
+    using C = FftCfg<L>;
+    constexpr int B = C::B, NT = C::NT, LP = C::LP;
+    constexpr int R = fft_radix(L, ST);
+    constexpr int NS = fft_ns_before(L, ST);
     constexpr int LR = L / R;
     constexpr int NTASK = B * LR;
-    static_assert(NTASK % NT == 0, "tasks must divide evenly among threads");
-    constexpr int TPT = NTASK / NT;
+    // power-of-two radices split evenly (16 / R tasks per thread); radix 3 and 5 take
+    // ceil(16 / R) with the last round partly idle
+    constexpr bool EVEN = NTASK % NT == 0;
+    constexpr int TPT = (NTASK + NT - 1) / NT;
     constexpr int TSTEP = L / (NS * R);
     float2 v[TPT][R];
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       const int t = threadIdx.x + q * NT;
-      const int b = t / LR, j = t % LR;
-      const int k = j & (NS - 1);
-      const float2* src = s + b * LP;
+      if (EVEN || t < NTASK) {
+        const int b = t / LR, j = t % LR;
+        const int k = (NS & (NS - 1)) == 0 ? (j & (NS - 1)) : j % NS;
+        const float2* src = s + b * LP;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = src[spad(j + r * LR)];
-      if constexpr (ST > 0) {
-        // w^r for r < R from the table entries w^1, w^2, w^4, w^8 (w = exp(dir 2 pi i k / (NS R)))
-        // and at most two further products per factor: a few ulp, log2(R) loads per butterfly
-        constexpr int LB = stage_bits(LOG2L, ST);
-        float2 pw[LB];
-#pragma unroll
-        for (int e = 0; e < LB; ++e) {
-          float2 w = __ldg(&tw[(k * TSTEP) << e]);
-          if (DIR > 0) w.y = -w.y;
-          pw[e] = w;
-        }
-        float2 wr[R];
-        twiddle_rec<R, 1>(v[q], pw, wr);
+        for (int r = 0; r < R; ++r) v[q][r] = src[spad(j + r * LR)];
+        if constexpr (ST > 0) apply_twiddles<R, DIR>(v[q], tw, k, TSTEP);
+        dft_r<R, DIR>(v[q]);
       }
-      dft_r<R, DIR>(v[q]);
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       const int t = threadIdx.x + q * NT;
-      const int b = t / LR, j = t % LR;
-      const int k = j & (NS - 1);
-      float2* dst = s + b * LP;
-      const int base = (j / NS) * NS * R + k;
+      if (EVEN || t < NTASK) {
+        const int b = t / LR, j = t % LR;
+        const int k = (NS & (NS - 1)) == 0 ? (j & (NS - 1)) : j % NS;
+        float2* dst = s + b * LP;
+        const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[spad(base + r * NS)] = v[q][r];
+        for (int r = 0; r < R; ++r) dst[spad(base + r * NS)] = v[q][r];
+      }
     }
     __syncthreads();
-    fft_stages<LOG2L, ST + 1, DIR>(s, tw);
+    fft_stages<L, ST + 1, DIR>(s, tw);
   }
 }
 
@@ -138,11 +137,11 @@ __device__ __forceinline__ const float2* cluster_map(const float2* p, uint32_t r
 //   void mid(float2* s, int seq0)      between the transforms (TWO)
 //   double store(int seq, int o, SeqView v)   o < nout(); per-thread results are summed
 //   void finish(int seq0, double acc)
-template <int LOG2L, int DIR, int DIR2, class Op>
-__global__ void __launch_bounds__(FftCfg<LOG2L>::NT,
-                                  Op::TWO ? FftCfg<LOG2L>::MINB_TWO : FftCfg<LOG2L>::MINB)
+template <int LEN, int DIR, int DIR2, class Op>
+__global__ void __launch_bounds__(FftCfg<LEN>::NT,
+                                  Op::TWO ? FftCfg<LEN>::MINB_TWO : FftCfg<LEN>::MINB)
     fft_pass_kernel(Op op, const float2* __restrict__ tw) {
-  using C = FftCfg<LOG2L>;
+  using C = FftCfg<LEN>;
   constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
   constexpr int PER = B * L / NT;
   extern __shared__ float2 smem[];
@@ -162,11 +161,11 @@ __global__ void __launch_bounds__(FftCfg<LOG2L>::NT,
   }
   __syncthreads();
   op.after_load(seq0, min(B, nseq - seq0));
-  fft_stages<LOG2L, 0, DIR>(smem, tw);
+  fft_stages<L, 0, DIR>(smem, tw);
   if constexpr (Op::TWO) {
     op.template mid<B, NT, L, LP>(smem, seq0);
     __syncthreads();
-    fft_stages<LOG2L, 0, DIR2>(smem, tw);
+    fft_stages<L, 0, DIR2>(smem, tw);
   }
   const int nout = op.nout();
   double acc = 0.0;
@@ -210,12 +209,12 @@ __global__ void __launch_bounds__(FftCfg<LOG2L>::NT,
   op.finish(seq0, acc);
 }
 
-template <int LOG2L, int DIR, int DIR2, class Op>
+template <int LEN, int DIR, int DIR2, class Op>
 int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
-  using C = FftCfg<LOG2L>;
+  using C = FftCfg<LEN>;
   const int nblk = (op.nseq() + C::B - 1) / C::B;
   if (nblk == 0 || nimg == 0) return FR_OK;
-  auto kern = fft_pass_kernel<LOG2L, DIR, DIR2, Op>;
+  auto kern = fft_pass_kernel<LEN, DIR, DIR2, Op>;
   static bool attr = false;
   if (!attr) {
     FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -250,10 +249,10 @@ int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
 //   float2 load(int seq, int i)        raw element (zero padding costs no load)
 //   float2 prep(int t, float2& raw)    input of transform t; may update raw for transform t + 1
 //   double store(int t, int seq, int o, SeqView v)   mapping per Op::TRANSPOSED
-template <int LOG2L, int DIR, class Op>
-__global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB_SUM)
+template <int LEN, int DIR, class Op>
+__global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB_SUM)
     fft_pass_multi_kernel(Op op, const float2* __restrict__ tw) {
-  using C = FftCfg<LOG2L>;
+  using C = FftCfg<LEN>;
   constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
   constexpr int PER = B * L / NT;
   extern __shared__ float2 smem[];
@@ -274,7 +273,7 @@ __global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB_SUM)
       smem[(idx / L) * LP + spad(idx % L)] = op.prep(t, r[k]);
     }
     __syncthreads();
-    fft_stages<LOG2L, 0, DIR>(smem, tw);
+    fft_stages<L, 0, DIR>(smem, tw);
     if constexpr (Op::TRANSPOSED) {
       for (int idx = threadIdx.x; idx < B * nout; idx += NT) {
         const int o = idx / B, b = idx % B;
@@ -289,12 +288,12 @@ __global__ void __launch_bounds__(FftCfg<LOG2L>::NT, FftCfg<LOG2L>::MINB_SUM)
   }
 }
 
-template <int LOG2L, int DIR, class Op>
+template <int LEN, int DIR, class Op>
 int launch_pass_multi(const Op& op, const float2* tw, cudaStream_t s) {
-  using C = FftCfg<LOG2L>;
+  using C = FftCfg<LEN>;
   const int nblk = (op.nseq() + C::B - 1) / C::B;
   if (nblk == 0) return FR_OK;
-  auto kern = fft_pass_multi_kernel<LOG2L, DIR, Op>;
+  auto kern = fft_pass_multi_kernel<LEN, DIR, Op>;
   static bool attr = false;
   if (!attr) {
     FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -329,22 +328,57 @@ struct OpBase {
   __device__ void finish(int, double) const {}
 };
 
-// Dispatch a templated functor on a runtime log2 length in [5, 14].
+// Dispatch a templated functor (templated on the length) on a runtime log2 length in [5, 14].
 #define FR_LOG2_DISPATCH(log2l, F, ...)                      \
   switch (log2l) {                                           \
-    case 5: return F<5>(__VA_ARGS__);                        \
-    case 6: return F<6>(__VA_ARGS__);                        \
-    case 7: return F<7>(__VA_ARGS__);                        \
-    case 8: return F<8>(__VA_ARGS__);                        \
-    case 9: return F<9>(__VA_ARGS__);                        \
-    case 10: return F<10>(__VA_ARGS__);                      \
-    case 11: return F<11>(__VA_ARGS__);                      \
-    case 12: return F<12>(__VA_ARGS__);                      \
-    case 13: return F<13>(__VA_ARGS__);                      \
-    case 14: return F<14>(__VA_ARGS__);                      \
+    case 5: return F<32>(__VA_ARGS__);                       \
+    case 6: return F<64>(__VA_ARGS__);                       \
+    case 7: return F<128>(__VA_ARGS__);                      \
+    case 8: return F<256>(__VA_ARGS__);                      \
+    case 9: return F<512>(__VA_ARGS__);                      \
+    case 10: return F<1024>(__VA_ARGS__);                    \
+    case 11: return F<2048>(__VA_ARGS__);                    \
+    case 12: return F<4096>(__VA_ARGS__);                    \
+    case 13: return F<8192>(__VA_ARGS__);                    \
+    case 14: return F<16384>(__VA_ARGS__);                   \
     default:                                                 \
       ::fr::set_error("FFT length 2^%d unsupported", log2l); \
       return FR_EUNSUPPORTED;                                \
+  }
+
+// Dispatch on a runtime length: the powers of two 32 .. 16384, 3 2^k for 48 .. 6144 and
+// 5 2^k for 80 .. 5120 (the reduced-padding PSF transforms of images up to 4096 a side);
+// fft_len_supported() agrees.
+#define FR_LEN_DISPATCH(len, F, ...)                                   \
+  switch (len) {                                                       \
+    case 32: return F<32>(__VA_ARGS__);                                \
+    case 64: return F<64>(__VA_ARGS__);                                \
+    case 128: return F<128>(__VA_ARGS__);                              \
+    case 256: return F<256>(__VA_ARGS__);                              \
+    case 512: return F<512>(__VA_ARGS__);                              \
+    case 1024: return F<1024>(__VA_ARGS__);                            \
+    case 2048: return F<2048>(__VA_ARGS__);                            \
+    case 4096: return F<4096>(__VA_ARGS__);                            \
+    case 8192: return F<8192>(__VA_ARGS__);                            \
+    case 16384: return F<16384>(__VA_ARGS__);                          \
+    case 48: return F<48>(__VA_ARGS__);                                \
+    case 96: return F<96>(__VA_ARGS__);                                \
+    case 192: return F<192>(__VA_ARGS__);                              \
+    case 384: return F<384>(__VA_ARGS__);                              \
+    case 768: return F<768>(__VA_ARGS__);                              \
+    case 1536: return F<1536>(__VA_ARGS__);                            \
+    case 3072: return F<3072>(__VA_ARGS__);                            \
+    case 6144: return F<6144>(__VA_ARGS__);                            \
+    case 80: return F<80>(__VA_ARGS__);                                \
+    case 160: return F<160>(__VA_ARGS__);                              \
+    case 320: return F<320>(__VA_ARGS__);                              \
+    case 640: return F<640>(__VA_ARGS__);                              \
+    case 1280: return F<1280>(__VA_ARGS__);                            \
+    case 2560: return F<2560>(__VA_ARGS__);                            \
+    case 5120: return F<5120>(__VA_ARGS__);                            \
+    default:                                                           \
+      ::fr::set_error("FFT length %d unsupported", (int)(len));        \
+      return FR_EUNSUPPORTED;                                          \
   }
 
 }  // namespace fr

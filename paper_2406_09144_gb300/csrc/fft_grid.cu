@@ -297,29 +297,29 @@ struct G2TermsAddOp : OpBase {
   }
 };
 
-template <int LG>
-static int run_d1(const D1Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, 1, tw, s); }
-template <int LG>
-static int run_d2(const D2Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, 1, tw, s); }
-template <int LG>
-static int run_g1(const G1Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, 1, tw, s); }
-template <int LG>
-static int run_g2(const G2Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, 1, tw, s); }
+template <int LEN>
+static int run_d1(const D1Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LEN, -1, -1>(op, 1, tw, s); }
+template <int LEN>
+static int run_d2(const D2Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LEN, -1, -1>(op, 1, tw, s); }
+template <int LEN>
+static int run_g1(const G1Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, 1, tw, s); }
+template <int LEN>
+static int run_g2(const G2Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, 1, tw, s); }
 
 static int d1(int lg, const D1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1, op, tw, s); }
 static int d2(int lg, const D2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2, op, tw, s); }
 static int g1(int lg, const G1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1, op, tw, s); }
 static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2, op, tw, s); }
-template <int LG>
-static int run_d1m(const D1TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass_multi<LG, -1>(op, tw, s); }
+template <int LEN>
+static int run_d1m(const D1TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass_multi<LEN, -1>(op, tw, s); }
 static int d1m(int lg, const D1TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1m, op, tw, s); }
-template <int LG>
-static int run_d2i(const D2TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, 1, tw, s); }
+template <int LEN>
+static int run_d2i(const D2TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass<LEN, -1, -1>(op, 1, tw, s); }
 static int d2i(int lg, const D2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2i, op, tw, s); }
-template <int LG>
-static int run_g1t(const G1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, nt, tw, s); }
-template <int LG>
-static int run_g2a(const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, nt, tw, s); }
+template <int LEN>
+static int run_g1t(const G1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nt, tw, s); }
+template <int LEN>
+static int run_g2a(const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nt, tw, s); }
 static int g2a(int lg, const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2a, op, nt, tw, s); }
 static int g1t(int lg, const G1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1t, op, nt, tw, s); }
 

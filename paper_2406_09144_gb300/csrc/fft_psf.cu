@@ -1,18 +1,26 @@
-// PSF convolution on the 2x padded grid (Sec. 3.3.2):
-//   out = P^dag FFT^-1[ T . FFT[P s] ],  T = FFT[ifftshift(PSF)] / (4 nx ny)  (real: PSF even)
-// in three passes over half spectra (the sky and the PSF are real), each reading contiguous
-// sequences:
-//   P1 (sky rows, length 2ny): two real rows per complex transform, zero padded from ny to 2ny;
-//      both rows' half spectra (ny + 1 bins) are separated by Hermitian symmetry and stored
-//      transposed, HT[img][q][jx];
-//   P2 (HT rows, length 2nx): rows >= nx are zero padding; forward FFT, multiply by T (stored
+// PSF convolution on a zero-padded periodic grid of lx x ly (Sec. 3.3.2):
+//   out = P^dag FFT^-1[ T . FFT[P s] ],  T = FFT[K] / (lx ly)  (real: K even)
+// K is the periodic kernel image: PSF(a, b) at (a mod lx, b mod ly) for |a| <= hx, |b| <= hy,
+// zero elsewhere, hx = min(lx - nx, nx - 1) (same for y). With nx < lx <= 2nx the circular
+// convolution of size lx reproduces the linear convolution with that kernel on the nx outputs
+// exactly (an offset d of the cropped product has |d| <= nx - 1, and d and d - lx are never both
+// inside [-hx, hx] when lx >= nx + hx). lx = 2nx, ly = 2ny keep the whole PSF (exact R' ~
+// PSF *); shorter lengths truncate the PSF sidelobes beyond hx, hy and cut the transform sizes
+// (the reduced padding of Sec. 3.3.2). Three passes over half spectra (the sky and the PSF are
+// real), each reading contiguous sequences:
+//   P1 (sky rows, length ly): two real rows per complex transform, zero padded from ny to ly;
+//      both rows' half spectra (nh + 1 bins, nh = ly / 2) are separated by Hermitian symmetry
+//      and stored transposed, HT[img][q][jx];
+//   P2 (HT rows, length lx): rows >= nx are zero padding; forward FFT, multiply by T (stored
 //      transposed as TT[q][p]), inverse FFT, keep [0, nx) (the crop P^dag along x), stored
 //      transposed back to H[img][jx][q];
-//   P3 (H row pairs, length 2ny): Hermitian extension of two half spectra into one complex
+//   P3 (H row pairs, length ly): Hermitian extension of two half spectra into one complex
 //      inverse FFT, keep [0, ny) (the crop along y). In likelihood mode the epilogue forms
 //      grad = conv - d and accumulates L = 1/2 s.conv - s.d in FP64 (Eq. ham with Eq. clean).
-// The transfer function is built once per plan from the PSF image: P1 on the PSF rows, then a
-// forward transform of the HT rows.
+// The transfer function is built from the PSF image: P1 on the rows of K (gathered from the
+// PSF image on the fly), then a forward transform of the HT rows.
+#include <algorithm>
+
 #include "fft_engine.cuh"
 
 namespace fr {
@@ -21,45 +29,58 @@ struct P1Op : OpBase {
   static constexpr bool TRANSPOSED = true;
   const float* src;  // real rows, row rho at src + rho * in_pitch
   int in_len, in_pitch;
-  float2* ht;        // [img][nyh + 1][rows_img]
-  int rows_img, nrows, nyh;
+  float2* ht;        // [img][nh + 1][rows_img]
+  int rows_img, nrows, nh;
   __host__ __device__ int nseq() const { return nrows >> 1; }
-  __host__ __device__ int nout() const { return nyh + 1; }
+  __host__ __device__ int nout() const { return nh + 1; }
   __device__ float2 load(int r, int i) const {
     if (i >= in_len) return make_float2(0.f, 0.f);
     const size_t a = (size_t)(2 * r) * in_pitch + i;
     return make_float2(__ldg(&src[a]), __ldg(&src[a + in_pitch]));
   }
   __device__ double store(int r, int k, SeqView v) const {
-    const int L = 2 * nyh;
-    const float2 z = v[k], zm = v[(L - k) & (L - 1)];
+    const float2 z = v[k], zm = v[k == 0 ? 0 : 2 * nh - k];
     const float2 x1 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
     const float2 x2 = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
     const int rho = 2 * r;
     const int img = rho / rows_img, jx = rho - img * rows_img;
-    float2* dst = ht + ((size_t)img * (nyh + 1) + k) * rows_img + jx;
+    float2* dst = ht + ((size_t)img * (nh + 1) + k) * rows_img + jx;
     dst[0] = x1;
     dst[1] = x2;
     return 0.0;
   }
 };
 
+// P1 on the rows of the periodic kernel image K (rows_img = lx, rows of length ly), read from
+// the PSF image [grp][2nx][2ny] (origin at (nx, ny)) without materialising K
+struct PK1Op : P1Op {
+  int nx, ny, lx, ly, hx, hy;
+  __device__ float at(int rho, int iy) const {
+    const int g = rho / lx, ix = rho - g * lx;
+    const int a = ix <= hx ? ix : ix - lx;
+    const int b = iy <= hy ? iy : iy - ly;
+    if (a < -hx || b < -hy) return 0.f;
+    return __ldg(&src[((size_t)g * 2 * nx + nx + a) * (2 * ny) + ny + b]);
+  }
+  __device__ float2 load(int r, int i) const { return make_float2(at(2 * r, i), at(2 * r + 1, i)); }
+};
+
 struct P2Op : OpBase {
   static constexpr bool TRANSPOSED = true;
   static constexpr bool TWO = true;
-  const float2* ht;       // [img][nyh + 1][nx]
+  const float2* ht;       // [img][nh + 1][nx]
   float2* h;              // [img][nx][hp]
-  int hp, nx, nyh, nsky;
-  const float* transfer;  // [nsky][nyh + 1][2nx]
-  __host__ __device__ int nseq() const { return nyh + 1; }
+  int hp, nx, nh, nsky;
+  const float* transfer;  // [nsky][nh + 1][lx]
+  __host__ __device__ int nseq() const { return nh + 1; }
   __host__ __device__ int nout() const { return nx; }
   __device__ float2 load(int q, int i) const {
     if (i >= nx) return make_float2(0.f, 0.f);
-    return ht[((size_t)blockIdx.y * (nyh + 1) + q) * nx + i];
+    return ht[((size_t)blockIdx.y * (nh + 1) + q) * nx + i];
   }
   template <int B, int NT, int L, int LP>
   __device__ void mid(float2* s, int q0) const {
-    const int nq = nyh + 1;
+    const int nq = nh + 1;
     const float* T = transfer + (size_t)(blockIdx.y % nsky) * nq * L;
     for (int idx = threadIdx.x; idx < B * L; idx += NT) {
       const int c = idx / L, p = idx % L;
@@ -84,28 +105,27 @@ struct P2Op : OpBase {
 
 struct P3Op : OpBase {
   const float2* h;
-  int hp, nyh, nrows;
-  float* out;          // [nrows][nyh]: the convolution, or grad in likelihood mode
+  int hp, nh, ny, nrows;
+  float* out;          // [nrows][ny]: the convolution, or grad in likelihood mode
   const float* sky;    // likelihood mode only
   const float* dirty;  // likelihood mode only (null: plain convolution)
   double* value;       // [nrows / (nx * nsky)]
   int nx, nsky, B;     // B: row pairs per CTA of this instantiation
   __host__ __device__ int nseq() const { return nrows >> 1; }
-  __host__ __device__ int nout() const { return nyh; }
+  __host__ __device__ int nout() const { return ny; }
   __device__ float2 load(int r, int k) const {
-    const int L = 2 * nyh;
     float2 x1, x2;
     const float2* h0 = h + (size_t)(2 * r) * hp;
     const float2* h1 = h0 + hp;
-    if (k <= nyh) {
+    if (k <= nh) {
       x1 = h0[k];
       x2 = h1[k];
-      if (k == 0 || k == nyh) {
+      if (k == 0 || k == nh) {
         x1.y = 0.f;
         x2.y = 0.f;
       }
     } else {
-      const int km = L - k;
+      const int km = 2 * nh - k;
       x1 = cconj(h0[km]);
       x2 = cconj(h1[km]);
     }
@@ -119,7 +139,7 @@ struct P3Op : OpBase {
   }
   __device__ double store(int r, int n, SeqView v) const {
     const float2 z = v[n];
-    const size_t a0 = (size_t)(2 * r) * nyh + n, a1 = a0 + nyh;
+    const size_t a0 = (size_t)(2 * r) * ny + n, a1 = a0 + ny;
     if (!dirty) {
       out[a0] = z.x;
       out[a1] = z.y;
@@ -151,52 +171,70 @@ struct P3Op : OpBase {
   }
 };
 
-// forward transform of the PSF half spectra along x -> real transfer function TT[q][p]
+// forward transform of the kernel half spectra along x -> real transfer function TT[q][p]
 struct TOp : OpBase {
-  const float2* ht;  // [grp][nyh + 1][nx2]
-  int nx2, nyh;
-  float* transfer;   // [grp][nyh + 1][nx2]
+  const float2* ht;  // [grp][nh + 1][lx]
+  int lx, nh;
+  float* transfer;   // [grp][nh + 1][lx]
   float scale;
-  __host__ __device__ int nseq() const { return nyh + 1; }
-  __host__ __device__ int nout() const { return nx2; }
+  __host__ __device__ int nseq() const { return nh + 1; }
+  __host__ __device__ int nout() const { return lx; }
   __device__ float2 load(int q, int i) const {
-    return ht[((size_t)blockIdx.y * (nyh + 1) + q) * nx2 + i];
+    return ht[((size_t)blockIdx.y * (nh + 1) + q) * lx + i];
   }
   __device__ double store(int q, int p, SeqView s) const {
-    // ifftshift by (nx2/2, nyh): multiply by (-1)^(p + q); the result is real (PSF even)
-    const float sg = ((p + q) & 1) ? -scale : scale;
-    transfer[((size_t)blockIdx.y * (nyh + 1) + q) * nx2 + p] = sg * s[p].x;
+    // K is even, so its transform is real: keep the real part
+    transfer[((size_t)blockIdx.y * (nh + 1) + q) * lx + p] = scale * s[p].x;
     return 0.0;
   }
 };
 
-template <int LG>
+template <int LEN>
 static int run_p1(const P1Op& op, const float2* tw, cudaStream_t s) {
-  return launch_pass<LG, -1, -1>(op, 1, tw, s);
+  return launch_pass<LEN, -1, -1>(op, 1, tw, s);
 }
-template <int LG>
+template <int LEN>
+static int run_pk1(const PK1Op& op, const float2* tw, cudaStream_t s) {
+  return launch_pass<LEN, -1, -1>(op, 1, tw, s);
+}
+template <int LEN>
 static int run_p2(const P2Op& op, int nimg, const float2* tw, cudaStream_t s) {
-  return launch_pass<LG, -1, 1>(op, nimg, tw, s);
+  return launch_pass<LEN, -1, 1>(op, nimg, tw, s);
 }
-template <int LG>
+template <int LEN>
 static int run_p3(const P3Op& op, const float2* tw, cudaStream_t s) {
   P3Op o = op;
-  o.B = FftCfg<LG>::B;
-  return launch_pass<LG, 1, 1>(o, 1, tw, s);
+  o.B = FftCfg<LEN>::B;
+  return launch_pass<LEN, 1, 1>(o, 1, tw, s);
 }
-template <int LG>
+template <int LEN>
 static int run_t(const TOp& op, int nimg, const float2* tw, cudaStream_t s) {
-  return launch_pass<LG, -1, -1>(op, nimg, tw, s);
+  return launch_pass<LEN, -1, -1>(op, nimg, tw, s);
 }
-static int p1(int lg, const P1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_p1, op, tw, s); }
-static int p2(int lg, const P2Op& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_p2, op, n, tw, s); }
-static int p3(int lg, const P3Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_p3, op, tw, s); }
-static int pt(int lg, const TOp& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_t, op, n, tw, s); }
+static int p1(int len, const P1Op& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_p1, op, tw, s); }
+static int pk1(int len, const PK1Op& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_pk1, op, tw, s); }
+static int p2(int len, const P2Op& op, int n, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_p2, op, n, tw, s); }
+static int p3(int len, const P3Op& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_p3, op, tw, s); }
+static int pt(int len, const TOp& op, int n, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_t, op, n, tw, s); }
+
+bool fft_len_supported(int L) {
+  if (L < 32 || L > 16384) return false;
+  const int c = odd_part(L);
+  if (c == 1) return true;
+  if (c == 3) return L >= 48 && L <= 6144;
+  if (c == 5) return L >= 80 && L <= 5120;
+  return false;
+}
+
+bool psf_padding_ok(int nx, int ny, int lx, int ly) {
+  return lx > nx && lx <= 2 * nx && ly > ny && ly <= 2 * ny && lx % 2 == 0 && ly % 2 == 0 &&
+         fft_len_supported(lx) && fft_len_supported(ly);
+}
 
 int psf_apply_passes(const PsfArgs& a, float2* h, float2* ht, const float2* tw_rows,
                      const float2* tw_cols, cudaStream_t s) {
-  const int nrows = a.nimg * a.nx;
-  const double px = (double)nrows * a.ny, hs = (double)nrows * (a.ny + 1);
+  const int nrows = a.nimg * a.nx, nh = a.ly / 2;
+  const double px = (double)nrows * a.ny, hs = (double)nrows * (nh + 1);
   P1Op o1;
   o1.src = a.sky;
   o1.in_len = a.ny;
@@ -204,28 +242,29 @@ int psf_apply_passes(const PsfArgs& a, float2* h, float2* ht, const float2* tw_r
   o1.ht = ht;
   o1.rows_img = a.nx;
   o1.nrows = nrows;
-  o1.nyh = a.ny;
+  o1.nh = nh;
   {
     ProfScope ps(PC_PSF_ROWS, s, px * 4.0 + hs * 8.0);
-    FR_TRY(p1(ilog2(2 * a.ny), o1, tw_rows, s));
+    FR_TRY(p1(a.ly, o1, tw_rows, s));
   }
   P2Op o2;
   o2.ht = ht;
   o2.h = h;
   o2.hp = a.hp;
   o2.nx = a.nx;
-  o2.nyh = a.ny;
+  o2.nh = nh;
   o2.nsky = a.nsky;
   o2.transfer = a.transfer;
   {
-    // half spectra in and out, transfer function (2nx x (ny+1) floats) once per image
-    ProfScope ps(PC_PSF_COLS, s, hs * 16.0 + (double)a.nimg * 2 * a.nx * (a.ny + 1) * 4.0);
-    FR_TRY(p2(ilog2(2 * a.nx), o2, a.nimg, tw_cols, s));
+    // half spectra in and out, transfer function (lx x (nh + 1) floats) once per image
+    ProfScope ps(PC_PSF_COLS, s, hs * 16.0 + (double)a.nimg * a.lx * (nh + 1) * 4.0);
+    FR_TRY(p2(a.lx, o2, a.nimg, tw_cols, s));
   }
   P3Op o3;
   o3.h = h;
   o3.hp = a.hp;
-  o3.nyh = a.ny;
+  o3.nh = nh;
+  o3.ny = a.ny;
   o3.nrows = nrows;
   o3.out = a.out;
   o3.sky = a.sky;
@@ -235,27 +274,33 @@ int psf_apply_passes(const PsfArgs& a, float2* h, float2* ht, const float2* tw_r
   o3.nsky = a.nsky;
   o3.B = 1;
   ProfScope ps(PC_PSF_ROWS, s, hs * 8.0 + px * (a.dirty ? 12.0 : 4.0));
-  return p3(ilog2(2 * a.ny), o3, tw_rows, s);
+  return p3(a.ly, o3, tw_rows, s);
 }
 
-int build_transfer(int nx, int ny, int nsky, const float* psf, float2* ht, float* transfer,
-                   const float2* tw_rows, const float2* tw_cols, cudaStream_t s) {
-  P1Op o1;
+int build_transfer(int nx, int ny, int nsky, const float* psf, int lx, int ly, float2* ht,
+                   float* transfer, const float2* tw_rows, const float2* tw_cols, cudaStream_t s) {
+  PK1Op o1;
   o1.src = psf;
-  o1.in_len = 2 * ny;
-  o1.in_pitch = 2 * ny;
+  o1.in_len = ly;
+  o1.in_pitch = 0;  // unused: rows come from at()
   o1.ht = ht;
-  o1.rows_img = 2 * nx;
-  o1.nrows = nsky * 2 * nx;
-  o1.nyh = ny;
-  FR_TRY(p1(ilog2(2 * ny), o1, tw_rows, s));
+  o1.rows_img = lx;
+  o1.nrows = nsky * lx;
+  o1.nh = ly / 2;
+  o1.nx = nx;
+  o1.ny = ny;
+  o1.lx = lx;
+  o1.ly = ly;
+  o1.hx = std::min(lx - nx, nx - 1);
+  o1.hy = std::min(ly - ny, ny - 1);
+  FR_TRY(pk1(ly, o1, tw_rows, s));
   TOp ot;
   ot.ht = ht;
-  ot.nx2 = 2 * nx;
-  ot.nyh = ny;
+  ot.lx = lx;
+  ot.nh = ly / 2;
   ot.transfer = transfer;
-  ot.scale = (float)(1.0 / (4.0 * nx * (double)ny));
-  return pt(ilog2(2 * nx), ot, nsky, tw_cols, s);
+  ot.scale = (float)(1.0 / ((double)lx * (double)ly));
+  return pt(lx, ot, nsky, tw_cols, s);
 }
 
 }  // namespace fr

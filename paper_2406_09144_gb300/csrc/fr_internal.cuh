@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -199,14 +200,16 @@ struct fr_plan {
   bool has_psf = false;
   std::vector<double> psf_norm;  // [nsky]
   float* psf_img = nullptr;      // [nsky][2nx][2ny]
-  float* transfer = nullptr;     // [nsky][2nx][ny+1], includes 1 / (4 nx ny)
+  float* transfer = nullptr;     // [nsky][psf_ly/2+1][psf_lx], includes 1 / (lx ly)
+  int psf_lx = 0, psf_ly = 0;    // padded PSF transform lengths (2nx, 2ny: the whole PSF)
   // noise model of the fast-resolve likelihood (Sec. 3.3.3): 1 / K_xi, [nsky][ny][nx]
   bool has_noise = false;
   float* noise_kinv = nullptr;
   double noise_eps = 0;
   std::vector<double> noise_logdet;  // [nsky] 1/2 sum ln(2 pi K)
-  // twiddle tables by log2 length
+  // twiddle tables by log2 length, and of the other (3 2^k, 5 2^k) lengths
   float2* tw[16] = {nullptr};
+  std::map<int, float2*> tw_mixed;
   int* status = nullptr;         // device status word
   size_t resident = 0;
   std::mutex mu;
@@ -248,20 +251,26 @@ int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, in
 // PSF-apply passes over nimg images of nx x ny; image i uses transfer + (i % nsky) * tstride
 struct PsfArgs {
   int nx, ny, nimg, nsky;
-  int hp;  // half-spectrum row pitch (complex)
+  int lx, ly;  // padded transform lengths: nx < lx <= 2nx, ny < ly <= 2ny
+  int hp;      // half-spectrum row pitch (complex), >= ly / 2 + 1
   const float* transfer;
   const float* sky;
   float* out;
   const float* dirty;   // likelihood mode (grad = conv - dirty), else null
   double* value;        // likelihood mode: [nimg / nsky] accumulators, else null
 };
-// h: [nimg][nx][hp] half spectra, ht: [nimg][ny+1][nx] transposed half spectra
+// h: [nimg][nx][hp] half spectra, ht: [nimg][ly/2+1][nx] transposed half spectra; tw_rows
+// and tw_cols are the twiddle tables of lengths ly and lx
 int psf_apply_passes(const PsfArgs& a, float2* h, float2* ht, const float2* tw_rows,
                      const float2* tw_cols, cudaStream_t s);
-// transfer function from PSF images [nsky][2nx][2ny] -> transfer TT [nsky][ny+1][2nx]
-// (ht: [nsky][ny+1][2nx] scratch)
-int build_transfer(int nx, int ny, int nsky, const float* psf, float2* ht, float* transfer,
-                   const float2* tw_rows, const float2* tw_cols, cudaStream_t s);
+// transfer function of the lx x ly periodic kernel cut from PSF images [nsky][2nx][2ny]
+// -> TT [nsky][ly/2+1][lx] (ht: [nsky][ly/2+1][lx] scratch)
+int build_transfer(int nx, int ny, int nsky, const float* psf, int lx, int ly, float2* ht,
+                   float* transfer, const float2* tw_rows, const float2* tw_cols, cudaStream_t s);
+// lengths the PSF passes take (powers of two 32..16384, 3 2^k 48..6144, 5 2^k 80..5120)
+bool fft_len_supported(int L);
+// nx < lx <= 2nx, ny < ly <= 2ny, both even and supported
+bool psf_padding_ok(int nx, int ny, int lx, int ly);
 int fft_max_log2();
 int fft_min_log2();
 // noise model passes (noise.cu): n_delta [nsky][nx][ny] -> kinv [nsky][ny][nx], logdet [nsky]

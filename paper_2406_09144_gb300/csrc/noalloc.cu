@@ -103,7 +103,7 @@ extern "C" int fr_psf_convolve_noalloc(const float* psf, const float* sky, int32
   noalloc_twiddles<<<16, 256, 0, s>>>(tw_cols, 2 * nx);
   FR_LAUNCHED();
   // every scratch element read below is written earlier in the same call: nothing needs zeroing
-  FR_TRY(build_transfer(nx, ny, 1, psf, reg, tt, tw_rows, tw_cols, s));
+  FR_TRY(build_transfer(nx, ny, 1, psf, 2 * nx, 2 * ny, reg, tt, tw_rows, tw_cols, s));
   float2* h = reg;
   float2* ht = (float2*)((unsigned char*)reg + align256(h_bytes));
   const size_t npix = (size_t)nx * ny;
@@ -111,6 +111,8 @@ extern "C" int fr_psf_convolve_noalloc(const float* psf, const float* sky, int32
     PsfArgs a;
     a.nx = nx;
     a.ny = ny;
+    a.lx = 2 * nx;
+    a.ly = 2 * ny;
     a.nimg = 1;
     a.nsky = 1;
     a.hp = ny + 2;

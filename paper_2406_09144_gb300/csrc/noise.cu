@@ -141,14 +141,14 @@ struct NKFOp : OpBase {
   }
 };
 
-template <int LG>
-static int run_nk1(const NK1Op& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, nimg, tw, s); }
-template <int LG>
-static int run_nk2(const NK2Op& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, 1>(op, nimg, tw, s); }
-template <int LG>
-static int run_nk3(const NK3Op& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LG, 1, 1>(op, nimg, tw, s); }
-template <int LG>
-static int run_nkf(const NKFOp& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LG, -1, -1>(op, nimg, tw, s); }
+template <int LEN>
+static int run_nk1(const NK1Op& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LEN, -1, -1>(op, nimg, tw, s); }
+template <int LEN>
+static int run_nk2(const NK2Op& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LEN, -1, 1>(op, nimg, tw, s); }
+template <int LEN>
+static int run_nk3(const NK3Op& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nimg, tw, s); }
+template <int LEN>
+static int run_nkf(const NKFOp& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LEN, -1, -1>(op, nimg, tw, s); }
 static int nk1(int lg, const NK1Op& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_nk1, op, n, tw, s); }
 static int nk2(int lg, const NK2Op& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_nk2, op, n, tw, s); }
 static int nk3(int lg, const NK3Op& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_nk3, op, n, tw, s); }

@@ -69,14 +69,25 @@ def test_plan_create_rejects_bad_sizes_without_gpu(lib):
     assert r == -4
 
 
-@pytest.mark.parametrize("lg", list(range(1, 15)))
+# powers of two, the 3 2^k and 5 2^k lengths of the reduced-padding PSF transforms, and odd
+# parts with several factors (radix-3 and radix-5 stages in sequence)
+FFT_LENGTHS = [1 << lg for lg in range(1, 15)] + [3, 5, 6, 10, 48, 80, 96, 1536, 1280, 12288,
+                                                  10240, 45, 225, 7200]
+
+
+@pytest.mark.parametrize("n", FFT_LENGTHS)
 @pytest.mark.parametrize("direction", [-1, 1])
-def test_host_fft_stages_match_numpy(lib, lg, direction):
-    rng = np.random.default_rng(lg)
-    n = 1 << lg
+def test_host_fft_stages_match_numpy(lib, n, direction):
+    rng = np.random.default_rng(n)
     x = (rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))).astype(np.complex64)
     got = binding.selftest_fft_host(x, direction)
     ref = np.fft.fft(x.astype(np.complex128), axis=1) if direction < 0 else \
         np.fft.ifft(x.astype(np.complex128), axis=1) * n
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err < 2e-6 * max(1, lg / 4), err
+    assert err < 2e-6 * max(1, np.log2(n) / 4), err
+
+
+def test_host_fft_rejects_other_lengths(lib):
+    for n in (7, 14, 21 * 16, 1, 32768):
+        with pytest.raises(binding.FastResolveError):
+            binding.selftest_fft_host(np.zeros((1, max(n, 1)), np.complex64), -1)
