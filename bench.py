@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="fastresolve", choices=["fastresolve", "reference"])
     ap.add_argument("--workload", default="vla", choices=["vla", "small", "meerkat", "meerkat1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sizes", action="store_true",
+                    help="skip the 3600^2 (non-power-of-two) side measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -428,6 +430,56 @@ def main():
         del skies, dirt, gb, out, ref_out
         torch.cuda.synchronize()
 
+    # an image side that is not a power of two: Tab. 2's field, 3600^2 pixels of 2", with the
+    # MeerKAT-like top channel (7,257,600 visibilities, w-stacking) on an 8192^2 grid
+    tab2 = None
+    if rank == 0 and not args.no_sizes:
+        o3 = synth.observation("meerkat1", npix=3600)
+        t0 = time.perf_counter()
+        p3 = B.Plan(o3.uvw, o3.freqs, o3.nx, o3.ny, o3.pixsize, weights=o3.weights, eps=1e-5,
+                    wterm=o3.wterm, mfs=not o3.per_channel_sky)
+        torch.cuda.synchronize()
+        p3_s = time.perf_counter() - t0
+        i3 = p3.info()
+        s3 = torch.from_numpy(synth.random_skies(o3.nsky, o3.nx, o3.ny, seed=3)
+                              .astype(np.float32)).to(dev)
+        v3 = torch.from_numpy(synth.complex_gaussian((o3.nrow, o3.nchan), seed=4)
+                              .astype(np.complex64)).to(dev)
+        m3 = torch.empty(p3.vis_shape, dtype=torch.complex64, device=dev)
+        d3 = torch.empty(p3.sky_shape, dtype=torch.float32, device=dev)
+        c3 = torch.empty_like(d3)
+        for _ in range(2):
+            p3.degrid(s3, out=m3)
+            p3.grid(v3, out=d3)
+            p3.psf_apply(s3, out=c3)
+        torch.cuda.synchronize()
+        td = tg = tp = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            p3.degrid(s3, out=m3)
+            e[1].record(stream)
+            p3.grid(v3, out=d3)
+            e[2].record(stream)
+            p3.psf_apply(s3, out=c3)
+            e[3].record(stream)
+            e[3].synchronize()
+            td += e[0].elapsed_time(e[1])
+            tg += e[1].elapsed_time(e[2])
+            tp += e[2].elapsed_time(e[3])
+        k = args.steps
+        tab2 = {"workload": "MeerKAT-like top channel (1712 MHz, 7,257,600 visibilities, w-terms) "
+                            "imaged at 3600^2 pixels of 2 arcsec (Tab. 2's field)",
+                "grid": [i3["grid_nu"], i3["grid_nv"]], "psf_padding": list(p3.psf_padding),
+                "wplanes_total": i3["wplanes_total"], "plan_s": p3_s,
+                "degrid_ms": td / k, "grid_ms": tg / k,
+                "mvis_s": o3.nvis / ((td + tg) / k * 1e-3) / 1e6,
+                "psf_apply_ms": tp / k,
+                "psf_apply_mpix_s": o3.nsky * o3.nx * o3.ny / (tp / k * 1e-3) / 1e6}
+        del p3, s3, v3, m3, d3, c3
+        torch.cuda.synchronize()
+
     # end to end through the C ABI with host buffers: H2D sky + vis, R and R^dag, D2H results
     e2e = None
     if True:
@@ -503,7 +555,8 @@ def main():
             "psf_likelihood_ms": t_psf / args.steps,
             "plan_s": plan_s,
             "plan": {k: info[k] for k in ("support", "wplanes_total", "work_items", "grid_nu")},
-            "minor_major": minor_major, "psf_reduced_padding": reduced, "roofline_alu": alu,
+            "minor_major": minor_major, "psf_reduced_padding": reduced, "size_3600": tab2,
+            "roofline_alu": alu,
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
         }

@@ -68,7 +68,9 @@ typedef struct {
  *   freqs    host float64 [nchan] Hz, all > 0
  *   weights  host float32 [nrow][nchan] (N^-1 as visibility weights, Sec. 3.1.2), >= 0;
  *            NULL means all ones; weight 0 marks flagged data
- *   nx, ny   image size; powers of two in [16, 4096]
+ *   nx, ny   image size; even, in [16, 4096]. The oversampled grid is the shortest FFT length
+ *            of at least 2 nx (2 ny) of the form 2^k, 3 2^k or 5 2^k (sigma = 2 for sides of those
+ *            forms, at most 2.56 otherwise); fr_plan_get_info reports it
  *   pixsize_x, pixsize_y  pixel size in radians (direction cosines), > 0
  *   eps      requested relative L2 accuracy of R and R^dag, in [1e-6, 1e-2]
  *   flags    FR_WTERM | FR_NTERM | FR_MFS | FR_DROP_OOB | FR_NO_PSF
@@ -112,9 +114,10 @@ int fr_psf_apply(fr_plan_t plan, const float *sky, int32_t batch, float *out, vo
  * min(ly - ny, ny - 1) (sidelobes beyond them neglected):
  *   out(p) = sum_q PSF_t(p - q) sky(q),  PSF_t(a, b) = PSF(a, b) inside the window, else 0,
  * which the lx-periodic transforms compute exactly. Smaller lx, ly move fewer bytes and lose
- * the truncated sidelobes; lx = 2nx, ly = 2ny restore the whole PSF.
- *   lx, ly  even, nx < lx <= 2nx, ny < ly <= 2ny, each 2^k (32..16384), 3 2^k (48..6144) or
- *           5 2^k (80..5120)
+ * the truncated sidelobes; lx >= 2nx - 1, ly >= 2ny - 1 keep the whole PSF.
+ *   lx, ly  even, nx < lx <= max(2nx, default lx), likewise ly; each 2^k (32..16384), 3 2^k
+ *           (48..6144) or 5 2^k (80..5120). The default (set at plan creation) is the shortest
+ *           such length >= 2nx - 1 (2nx for sides of those forms): the whole PSF.
  * Rebuilds the plan's transfer function in place on `stream` and synchronises it: no PSF call
  * on this plan may be in flight on any stream, and CUDA graphs captured before keep the old
  * lengths (capture again). Errors: FR_EINVAL (range, parity, FR_NO_PSF plan), FR_EUNSUPPORTED
@@ -153,7 +156,8 @@ int fr_major_cycle(fr_plan_t plan, const float *sky, const float *dirty, float *
  *   eps_noise  > 0, the variance of the added white noise (Eq. N_new)
  *   logdet     host float64 [nsky] or NULL: 1/2 sum_k ln(2 pi K_k), the ln|2 pi N'| / 2 term of
  *              Eq. ham_new (constant in the sky)
- * Needs nx, ny >= 32 (FR_EUNSUPPORTED otherwise). Synchronises `stream`. */
+ * The noise passes transform the unpadded image: nx and ny must each be 2^k (>= 32), 3 2^k
+ * (>= 48) or 5 2^k (>= 80) (FR_EUNSUPPORTED otherwise). Synchronises `stream`. */
 int fr_noise_fit(fr_plan_t plan, double eps_noise, double *logdet, void *stream);
 
 /* The fitted kernel K (not its inverse): device float32 [nsky][nx][ny] in numpy.fft.fft2 order
@@ -200,7 +204,7 @@ int fr_psf_convolve_noalloc(const float *psf, const float *sky, int32_t nx, int3
 typedef struct {
   int32_t nx, ny, nsky, nchan;
   int64_t nrow, nvis;
-  int32_t grid_nu, grid_nv;        /* oversampled grid (2 nx, 2 ny) */
+  int32_t grid_nu, grid_nv;        /* oversampled grid (>= 2 nx, 2 ny; see fr_plan_create) */
   int32_t support;                 /* gridding kernel support W in cells */
   double beta;                     /* exponential-of-semicircle kernel shape */
   int32_t wplanes_total;           /* sum over images of the w-planes */

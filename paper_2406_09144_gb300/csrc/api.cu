@@ -208,25 +208,20 @@ static int make_twiddles(float2** out, int L, cudaStream_t s) {
   return FR_OK;
 }
 
-int ensure_twiddles(fr_plan* p, int log2l, cudaStream_t s) {
-  if (log2l < fft_min_log2() || log2l > fft_max_log2()) {
-    set_error("FFT length 2^%d outside the supported range", log2l);
-    return FR_EUNSUPPORTED;
-  }
-  if (!p->tw[log2l]) {
-    FR_TRY(make_twiddles(&p->tw[log2l], 1 << log2l, s));
-    p->resident += ((size_t)1 << log2l) * sizeof(float2);
-  }
-  return FR_OK;
-}
-
-// twiddle table of any length the PSF passes take (power of two or 3 2^k, 5 2^k)
-static int ensure_twiddles_len(fr_plan* p, int L, cudaStream_t s) {
+// twiddle table of any length the FFT passes take (powers of two, 3 2^k, 5 2^k)
+int ensure_twiddles(fr_plan* p, int L, cudaStream_t s) {
   if (!fft_len_supported(L)) {
     set_error("FFT length %d unsupported", L);
     return FR_EUNSUPPORTED;
   }
-  if ((L & (L - 1)) == 0) return ensure_twiddles(p, ilog2(L), s);
+  if ((L & (L - 1)) == 0) {
+    float2*& t = p->tw[ilog2(L)];
+    if (!t) {
+      FR_TRY(make_twiddles(&t, L, s));
+      p->resident += (size_t)L * sizeof(float2);
+    }
+    return FR_OK;
+  }
   std::lock_guard<std::mutex> lk(p->mu);
   if (!p->tw_mixed.count(L)) {
     float2* t = nullptr;
@@ -237,7 +232,7 @@ static int ensure_twiddles_len(fr_plan* p, int L, cudaStream_t s) {
   return FR_OK;
 }
 
-static const float2* twiddles_of(fr_plan* p, int L) {
+const float2* twiddles_of(fr_plan* p, int L) {
   if ((L & (L - 1)) == 0) return p->tw[ilog2(L)];
   std::lock_guard<std::mutex> lk(p->mu);
   auto it = p->tw_mixed.find(L);
@@ -435,8 +430,8 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
       PlaneArgs a = plane_args(geo, lay, g, 0);
       FR_TRY(degrid_prepass_terms(a, P, sky + g * img, w->b1_terms, (size_t)geo.nx * geo.Nv,
-                                  w->grid_terms, term_grid_count(geo), pl->tw[ilog2(geo.Nv)],
-                                  pl->tw[ilog2(geo.Nu)], s));
+                                  w->grid_terms, term_grid_count(geo), twiddles_of(pl, geo.Nv),
+                                  twiddles_of(pl, geo.Nu), s));
       FR_TRY(degrid_terms(geo, lay, g, w->tmap_terms, vis, pl->status, s));
       continue;
     }
@@ -444,8 +439,8 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
       const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
       PlaneArgs a = plane_args(geo, lay, g, p);
-      FR_TRY(degrid_prepass(a, sky + g * img, w->b1, w->grid, pl->tw[ilog2(geo.Nv)],
-                            pl->tw[ilog2(geo.Nu)], s));
+      FR_TRY(degrid_prepass(a, sky + g * img, w->b1, w->grid, twiddles_of(pl, geo.Nv),
+                            twiddles_of(pl, geo.Nu), s));
       w->grid_zero = false;
       FR_TRY(degrid_plane(geo, lay, g, p, w->tmap, w->vbuf, vis, pl->status, s));
     }
@@ -473,8 +468,8 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
       FR_TRY(grid_terms(geo, lay, g, vis, apply_weights, w->grid_terms_g, s));
       PlaneArgs a = plane_args(geo, lay, g, 0);
       FR_TRY(grid_postpass_terms(a, geo.nterms, w->grid_terms_g, plane, w->b1g_terms,
-                                 (size_t)geo.nx * geo.Nv, dirty + g * img, pl->tw[ilog2(geo.Nu)],
-                                 pl->tw[ilog2(geo.Nv)], s));
+                                 (size_t)geo.nx * geo.Nv, dirty + g * img, twiddles_of(pl, geo.Nu),
+                                 twiddles_of(pl, geo.Nv), s));
       w->terms_g_zero = true;  // the post-pass zeroes the band it reads
     }
     return FR_OK;
@@ -490,8 +485,8 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
       FR_TRY(grid_plane(geo, lay, g, p, ybuf, grid, s));
       PlaneArgs a = plane_args(geo, lay, g, p);
-      FR_TRY(grid_postpass(a, grid, b1, dirty + g * img, written ? 1 : 0, pl->tw[ilog2(geo.Nu)],
-                           pl->tw[ilog2(geo.Nv)], s));
+      FR_TRY(grid_postpass(a, grid, b1, dirty + g * img, written ? 1 : 0, twiddles_of(pl, geo.Nu),
+                           twiddles_of(pl, geo.Nv), s));
       written = true;
     }
     if (!written) FR_CUDA_TRY(cudaMemsetAsync(dirty + g * img, 0, img * sizeof(float), s));
@@ -520,16 +515,16 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
   Geometry pg;
   pg.nx = 2 * p->geo.nx;
   pg.ny = 2 * p->geo.ny;
-  pg.Nu = 2 * pg.nx;
-  pg.Nv = 2 * pg.ny;
+  pg.Nu = fft_len_at_least(2 * pg.nx);
+  pg.Nv = fft_len_at_least(2 * pg.ny);
   pg.dl = p->geo.dl;
   pg.dm = p->geo.dm;
   set_kernel(&pg, p->geo.kern.W);
   pg.wterm = false;
   pg.nterm = false;
   pg.async = s;  // the PSF geometry and layout are transients of plan creation
-  FR_TRY(ensure_twiddles(p, ilog2(pg.Nu), s));
-  FR_TRY(ensure_twiddles(p, ilog2(pg.Nv), s));
+  FR_TRY(ensure_twiddles(p, pg.Nu, s));
+  FR_TRY(ensure_twiddles(p, pg.Nv, s));
   std::vector<double> iu, iv;
   kernel_ft_tables(pg, iu, iv);
   FR_TRY(make_tables(&pg, iu, iv, s));
@@ -541,7 +536,12 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
                        true, &pl, s);
   float2 *grid = nullptr, *b1 = nullptr, *y = nullptr, *h = nullptr;
   const size_t nimg2 = (size_t)pg.nx * pg.ny;
-  const int hp = p->geo.ny + 2;
+  // default padded PSF lengths: the shortest transforms that hold every offset |a| <= nx - 1
+  // of the cropped product (2nx, 2ny for powers of two)
+  const int lx = fft_len_at_least(2 * p->geo.nx - 1), ly = fft_len_at_least(2 * p->geo.ny - 1);
+  const size_t tsize = (size_t)p->nsky * lx * (ly / 2 + 1);
+  if (r == FR_OK) r = ensure_twiddles(p, lx, s);
+  if (r == FR_OK) r = ensure_twiddles(p, ly, s);
   if (r == FR_OK) {
     // transients are stream-ordered: building a plan does not synchronise the device
     cudaError_t e = cudaSuccess;
@@ -549,13 +549,13 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
     if (e == cudaSuccess) e = cudaMallocAsync(&b1, (size_t)pg.nx * pg.Nv * sizeof(float2), s);
     if (e == cudaSuccess)
       e = cudaMallocAsync(&y, (size_t)std::max<int64_t>(pl.nsorted, 1) * sizeof(float2), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&h, (size_t)p->nsky * pg.nx * hp * sizeof(float2), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h, tsize * sizeof(float2), s);
     if (e == cudaSuccess && grid) e = cudaMemsetAsync(grid, 0, (size_t)pg.Nu * pg.Nv * sizeof(float2), s);
     // the gridding half plane must be zero outside the band of the PSF layout
     if (e == cudaSuccess && b1) e = cudaMemsetAsync(b1, 0, (size_t)pg.nx * pg.Nv * sizeof(float2), s);
     if (e == cudaSuccess) e = cudaMalloc(&p->psf_img, (size_t)p->nsky * nimg2 * sizeof(float));
-    if (e == cudaSuccess)
-      e = cudaMalloc(&p->transfer, (size_t)p->nsky * pg.nx * (p->geo.ny + 1) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&p->transfer, tsize * sizeof(float));
+    p->transfer_cap = tsize;
     if (e != cudaSuccess) {
       set_error("PSF allocation failed: %s", cudaGetErrorString(e));
       r = FR_ENOMEM;
@@ -567,10 +567,10 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
   }
   if (r == FR_OK) r = zero_psf_edges(p->psf_img, p->nsky, pg.nx, pg.ny, s);
   if (r == FR_OK)
-    r = build_transfer(p->geo.nx, p->geo.ny, p->nsky, p->psf_img, pg.nx, pg.ny, h, p->transfer,
-                       p->tw[ilog2(pg.ny)], p->tw[ilog2(pg.nx)], s);
-  p->psf_lx = pg.nx;
-  p->psf_ly = pg.ny;
+    r = build_transfer(p->geo.nx, p->geo.ny, p->nsky, p->psf_img, lx, ly, h, p->transfer,
+                       twiddles_of(p, ly), twiddles_of(p, lx), s);
+  p->psf_lx = lx;
+  p->psf_ly = ly;
   // psf_norm = sum of the kept weights per image (FP64)
   double* d_norm = nullptr;
   if (r == FR_OK) {
@@ -598,13 +598,11 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
   cudaStreamSynchronize(s);
   if (r == FR_OK) {
     p->has_psf = true;
-    p->resident += (size_t)p->nsky * nimg2 * sizeof(float) +
-                   (size_t)p->nsky * pg.nx * (p->geo.ny + 1) * sizeof(float);
+    p->resident += (size_t)p->nsky * nimg2 * sizeof(float) + tsize * sizeof(float);
   }
   return r;
 }
 
-static bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int32_t nchan,
                        const float* weights, int32_t nx, int32_t ny, double dx, double dy,
@@ -613,8 +611,8 @@ static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int
     set_error("uvw/freqs must be non-null with nrow > 0 and nchan > 0");
     return FR_EINVAL;
   }
-  if (!pow2(nx) || !pow2(ny) || nx < 16 || ny < 16 || nx > 4096 || ny > 4096) {
-    set_error("nx, ny must be powers of two in [16, 4096] (got %d x %d)", nx, ny);
+  if ((nx & 1) || (ny & 1) || nx < 16 || ny < 16 || nx > 4096 || ny > 4096) {
+    set_error("nx, ny must be even and in [16, 4096] (got %d x %d)", nx, ny);
     return FR_EUNSUPPORTED;
   }
   if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy)) {
@@ -664,8 +662,10 @@ static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int
   Geometry& g = p->geo;
   g.nx = nx;
   g.ny = ny;
-  g.Nu = 2 * nx;
-  g.Nv = 2 * ny;
+  // oversampled grid: the shortest FFT length of at least twice the image (sigma = 2 for
+  // powers of two, 3 2^k and 5 2^k; a little above 2 for other sides)
+  g.Nu = fft_len_at_least(2 * nx);
+  g.Nv = fft_len_at_least(2 * ny);
   g.dl = dx;
   g.dm = dy;
   set_kernel(&g, choose_support(eps));
@@ -714,7 +714,7 @@ static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int
       for (int k = 0; k < p->nsky; ++k) planes[k] = n_terms;
     }
   }
-  for (int L : {g.Nu, g.Nv}) FR_TRY(ensure_twiddles(p, ilog2(L), s));
+  for (int L : {g.Nu, g.Nv}) FR_TRY(ensure_twiddles(p, L, s));
 
   // device copies of the inputs (plan-time only)
   double *d_uvw = nullptr, *d_freqs = nullptr;
@@ -916,6 +916,15 @@ int fr_dirty_psf(fr_plan_t p, const fr_cf32* vis, float* dirty, float* psf, doub
   return FR_OK;
 }
 
+// half-spectrum row pitch of the PSF passes: ly/2 + 1 bins rounded up to a multiple of 4
+// (32-byte group stores)
+static int psf_pitch(int ly) { return (ly / 2 + 1 + 3) & ~3; }
+
+// complex scratch of one PSF convolution of nimg images: H [nimg][nx][hp], HT [nimg][ly/2+1][nx]
+static size_t psf_h_need(const fr_plan* p, int nimg) {
+  return (size_t)nimg * p->geo.nx * (psf_pitch(p->psf_ly) + p->psf_ly / 2 + 1);
+}
+
 static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, const float* dirty,
                       double* value, cudaStream_t s) {
   if (!p->has_psf) {
@@ -926,9 +935,9 @@ static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, 
   FR_TRY(get_ws(p, s, &w));
   const int nimg = batch * p->nsky;
   const int lx = p->psf_lx, ly = p->psf_ly, nq = ly / 2 + 1;
-  const int hp = (nq + 3) & ~3;  // ly/2 + 1 bins, pitch a multiple of 4 (32-byte group stores)
+  const int hp = psf_pitch(ly);
   const size_t hsize = (size_t)nimg * p->geo.nx * hp;  // H, then HT ([nimg][ly/2+1][nx])
-  FR_TRY(ws_reserve_h(w, hsize + (size_t)nimg * nq * p->geo.nx));
+  FR_TRY(ws_reserve_h(w, psf_h_need(p, nimg)));
   PsfArgs a;
   a.nx = p->geo.nx;
   a.ny = p->geo.ny;
@@ -973,21 +982,33 @@ int fr_psf_set_padding(fr_plan_t p, int32_t lx, int32_t ly, void* stream) {
     return FR_EINVAL;
   }
   const int nx = p->geo.nx, ny = p->geo.ny;
-  if (lx <= nx || lx > 2 * nx || ly <= ny || ly > 2 * ny || (lx & 1) || (ly & 1)) {
-    set_error("padded PSF lengths %d x %d: need even nx < lx <= 2nx, ny < ly <= 2ny (%d x %d image)",
-              lx, ly, nx, ny);
+  const int mx = std::max(2 * nx, fft_len_at_least(2 * nx - 1));
+  const int my = std::max(2 * ny, fft_len_at_least(2 * ny - 1));
+  if (lx <= nx || lx > mx || ly <= ny || ly > my || (lx & 1) || (ly & 1)) {
+    set_error("padded PSF lengths %d x %d: need even nx < lx <= %d, ny < ly <= %d (%d x %d image)",
+              lx, ly, mx, my, nx, ny);
     return FR_EINVAL;
   }
-  if (!psf_padding_ok(nx, ny, lx, ly)) {
+  if (!fft_len_supported(lx) || !fft_len_supported(ly)) {
     set_error("padded PSF lengths %d x %d: each must be 2^k (32..16384), 3 2^k (48..6144) or "
               "5 2^k (80..5120)", lx, ly);
     return FR_EUNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  FR_TRY(ensure_twiddles_len(p, lx, s));
-  FR_TRY(ensure_twiddles_len(p, ly, s));
+  FR_TRY(ensure_twiddles(p, lx, s));
+  FR_TRY(ensure_twiddles(p, ly, s));
+  const size_t tsize = (size_t)p->nsky * (ly / 2 + 1) * lx;
+  if (tsize > p->transfer_cap) {  // a longer padding than the default: grow the transfer
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+    float* t = nullptr;
+    FR_CUDA_TRY(cudaMalloc(&t, tsize * sizeof(float)));
+    cudaFree(p->transfer);
+    p->resident += (tsize - p->transfer_cap) * sizeof(float);
+    p->transfer = t;
+    p->transfer_cap = tsize;
+  }
   float2* ht = nullptr;
-  FR_CUDA_TRY(cudaMallocAsync(&ht, (size_t)p->nsky * (ly / 2 + 1) * lx * sizeof(float2), s));
+  FR_CUDA_TRY(cudaMallocAsync(&ht, tsize * sizeof(float2), s));
   const int r = build_transfer(nx, ny, p->nsky, p->psf_img, lx, ly, ht, p->transfer,
                                twiddles_of(p, ly), twiddles_of(p, lx), s);
   cudaFreeAsync(ht, s);
@@ -1061,10 +1082,11 @@ __global__ void kernel_from_inverse(const float* kinv, int nsky, int nx, int ny,
   }
 }
 
+// the noise passes transform the unpadded image: nx and ny must themselves be FFT lengths
 static int noise_sizes_ok(const fr_plan* p) {
-  const int lx = ilog2(p->geo.nx), ly = ilog2(p->geo.ny);
-  if (lx < fft_min_log2() || ly < fft_min_log2()) {
-    set_error("the noise model needs nx, ny >= %d", 1 << fft_min_log2());
+  if (!fft_len_supported(p->geo.nx) || !fft_len_supported(p->geo.ny)) {
+    set_error("the noise model needs nx, ny of the form 2^k (>= 32), 3 2^k (>= 48) or 5 2^k "
+              "(>= 80) (got %d x %d)", p->geo.nx, p->geo.ny);
     return FR_EUNSUPPORTED;
   }
   return FR_OK;
@@ -1078,8 +1100,8 @@ int fr_noise_fit(fr_plan_t p, double eps_noise, double* logdet, void* stream) {
   FR_TRY(noise_sizes_ok(p));
   cudaStream_t s = (cudaStream_t)stream;
   const Geometry& g = p->geo;
-  FR_TRY(ensure_twiddles(p, ilog2(g.nx), s));
-  FR_TRY(ensure_twiddles(p, ilog2(g.ny), s));
+  FR_TRY(ensure_twiddles(p, g.nx, s));
+  FR_TRY(ensure_twiddles(p, g.ny, s));
   Workspace* w;
   FR_TRY(get_ws(p, s, &w));
   FR_TRY(ws_reserve_tmp(p, w));
@@ -1102,7 +1124,7 @@ int fr_noise_fit(fr_plan_t p, double eps_noise, double* logdet, void* stream) {
   FR_LAUNCHED();
   FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, p->nsky * sizeof(double), s));
   FR_TRY(noise_kernel_passes(w->img_b, g.nx, g.ny, p->nsky, (float)eps_noise, w->h,
-                             p->noise_kinv, w->red, p->tw[ilog2(g.ny)], p->tw[ilog2(g.nx)], s));
+                             p->noise_kinv, w->red, twiddles_of(p, g.ny), twiddles_of(p, g.nx), s));
   p->noise_logdet.assign(p->nsky, 0.0);
   FR_CUDA_TRY(cudaMemcpyAsync(p->noise_logdet.data(), w->red, p->nsky * sizeof(double),
                               cudaMemcpyDeviceToHost, s));
@@ -1146,7 +1168,7 @@ int fr_noise_apply_inverse(fr_plan_t p, const float* x, int32_t batch, float* ou
   const size_t n = (size_t)nimg * g.nx * g.ny;
   FR_TRY(ws_reserve_h(w, 2 * n));
   return noise_inverse_passes(x, g.nx, g.ny, nimg, p->nsky, p->noise_kinv, w->h, w->h + n, out,
-                              1.f, nullptr, nullptr, p->tw[ilog2(g.ny)], p->tw[ilog2(g.nx)], s);
+                              1.f, nullptr, nullptr, twiddles_of(p, g.ny), twiddles_of(p, g.nx), s);
 }
 
 int fr_fast_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, int32_t batch,
@@ -1166,16 +1188,16 @@ int fr_fast_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, i
   const int nimg = batch * p->nsky;
   const size_t n = (size_t)nimg * g.nx * g.ny;
   FR_TRY(ws_reserve_imgs(w, n));
-  // spectra scratch for both the PSF passes and the noise passes (the PSF's is the larger)
-  FR_TRY(ws_reserve_h(w, (size_t)nimg * g.nx * (2 * (size_t)g.ny + 5)));
+  // spectra scratch for both the PSF passes and the noise passes (2 nimg nx ny complex)
+  FR_TRY(ws_reserve_h(w, std::max(psf_h_need(p, nimg), 2 * n)));
   FR_TRY(ws_reserve_red(w, (size_t)std::max(batch, 4)));
   // t = PSF * sky - dirty = -r (Sec. 3.3.2 response)
   FR_TRY(psf_common(p, sky, batch, w->img_a, dirty, nullptr, s));
   FR_CUDA_TRY(cudaMemsetAsync(w->red, 0, batch * sizeof(double), s));
   // u = N'^-1 t = -N'^-1 r and H = 1/2 t . u = 1/2 r^T N'^-1 r (Eq. ham_new)
   FR_TRY(noise_inverse_passes(w->img_a, g.nx, g.ny, nimg, p->nsky, p->noise_kinv, w->h,
-                              w->h + n, w->img_b, 1.f, w->img_a, w->red, p->tw[ilog2(g.ny)],
-                              p->tw[ilog2(g.nx)], s));
+                              w->h + n, w->img_b, 1.f, w->img_a, w->red, twiddles_of(p, g.ny),
+                              twiddles_of(p, g.nx), s));
   // grad = -PSF * (N'^-1 r) = PSF * u (the PSF passes without a dirty image leave red alone)
   FR_TRY(psf_common(p, w->img_b, batch, grad, nullptr, nullptr, s));
   if (value) {

@@ -51,6 +51,9 @@ __device__ __forceinline__ float taylor_factor(int32_t tq, int n, float inv_fact
   return p;
 }
 
+// index i in [-N, N) taken modulo the grid length N (any even N, not only powers of two)
+__device__ __forceinline__ int wrap(int i, int N) { return i < 0 ? i + N : i; }
+
 struct D1Op : OpBase {
   static constexpr bool TRANSPOSED = true;
   const float* sky;
@@ -218,13 +221,12 @@ struct G1Op : OpBase {
     }
   }
   __device__ double store(int q, int o, SeqView s) const {
-    const int i = (o - (nx >> 1) + Nu) & (Nu - 1);
-    b1[blockIdx.y * b1_stride + (size_t)o * Nv + vb0 + q] = s[i];
+    b1[blockIdx.y * b1_stride + (size_t)o * Nv + vb0 + q] = s[wrap(o - (nx >> 1), Nu)];
     return 0.0;
   }
   static constexpr bool GROUP = true;
   __device__ float2 pick(int, int o, SeqView s) const {
-    return s[(o - (nx >> 1) + Nu) & (Nu - 1)];
+    return s[wrap(o - (nx >> 1), Nu)];
   }
   __device__ void store_group(int q0, int o, const float2* v, int n) const {
     store_run(b1 + blockIdx.y * b1_stride + (size_t)o * Nv + vb0 + q0, v, n);
@@ -249,8 +251,7 @@ struct G2Op : OpBase {
     return b1[(size_t)jx * Nv + i];
   }
   __device__ double store(int jx, int jy, SeqView s) const {
-    const int i = (jy - (ny >> 1) + Nv) & (Nv - 1);
-    const float2 z = s[i];
+    const float2 z = s[wrap(jy - (ny >> 1), Nv)];
     const int pix = jx * ny + jy;
     float val;
     if (wterm && taylor) {
@@ -288,7 +289,7 @@ struct G2TermsAddOp : OpBase {
     return b1[blockIdx.y * b1_stride + (size_t)jx * Nv + i];
   }
   __device__ double store(int jx, int jy, SeqView s) const {
-    const int i = (jy - (ny >> 1) + Nv) & (Nv - 1);
+    const int i = wrap(jy - (ny >> 1), Nv);
     const int pix = jx * ny + jy;
     const int t = blockIdx.y;
     atomicAdd(&dirty[pix],
@@ -306,22 +307,22 @@ static int run_g1(const G1Op& op, const float2* tw, cudaStream_t s) { return lau
 template <int LEN>
 static int run_g2(const G2Op& op, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, 1, tw, s); }
 
-static int d1(int lg, const D1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1, op, tw, s); }
-static int d2(int lg, const D2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2, op, tw, s); }
-static int g1(int lg, const G1Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1, op, tw, s); }
-static int g2(int lg, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2, op, tw, s); }
+static int d1(int len, const D1Op& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_d1, op, tw, s); }
+static int d2(int len, const D2Op& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_d2, op, tw, s); }
+static int g1(int len, const G1Op& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_g1, op, tw, s); }
+static int g2(int len, const G2Op& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_g2, op, tw, s); }
 template <int LEN>
 static int run_d1m(const D1TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass_multi<LEN, -1>(op, tw, s); }
-static int d1m(int lg, const D1TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d1m, op, tw, s); }
+static int d1m(int len, const D1TermsOp& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_d1m, op, tw, s); }
 template <int LEN>
 static int run_d2i(const D2TermsOp& op, const float2* tw, cudaStream_t s) { return launch_pass<LEN, -1, -1>(op, 1, tw, s); }
-static int d2i(int lg, const D2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_d2i, op, tw, s); }
+static int d2i(int len, const D2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_d2i, op, tw, s); }
 template <int LEN>
 static int run_g1t(const G1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nt, tw, s); }
 template <int LEN>
 static int run_g2a(const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nt, tw, s); }
-static int g2a(int lg, const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g2a, op, nt, tw, s); }
-static int g1t(int lg, const G1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_g1t, op, nt, tw, s); }
+static int g2a(int len, const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_g2a, op, nt, tw, s); }
+static int g1t(int len, const G1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_g1t, op, nt, tw, s); }
 
 
 int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,
@@ -347,7 +348,7 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
   {
     // sky + corr (+ tq) in, half-transformed plane out
     ProfScope ps(PC_FFT_ROWS, s, img * (8.0 + (a.wterm ? 4.0 : 0.0)) + half * 8.0);
-    FR_TRY(d1(ilog2(a.Nv), o1, twv, s));
+    FR_TRY(d1(a.Nv, o1, twv, s));
   }
   D2Op o2;
   o2.b1t = b1;
@@ -361,7 +362,7 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
   o2.ub0 = a.bu0;
   o2.nub = nub;
   ProfScope ps(PC_FFT_COLS, s, half * 8.0 + full * 8.0);
-  return d2(ilog2(a.Nu), o2, twu, s);
+  return d2(a.Nu, o2, twu, s);
 }
 
 int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
@@ -385,7 +386,7 @@ int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, in
     // band rows in, band zeroed, cropped band columns of the half plane out
     ProfScope ps(PC_FFT_COLS, s, band * 16.0 + (double)a.nx * nvb * 8.0);
     (void)band_rows;
-    FR_TRY(g1(ilog2(a.Nu), o1, twu, s));
+    FR_TRY(g1(a.Nu, o1, twu, s));
   }
   G2Op o2;
   o2.b1 = b1;
@@ -406,7 +407,7 @@ int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, in
   ProfScope ps(PC_FFT_ROWS, s,
                (double)a.nx * nvb * 8.0 +
                    img * (4.0 + (a.wterm ? 4.0 : 0.0) + (accumulate ? 8.0 : 4.0)));
-  return g2(ilog2(a.Nv), o2, twv, s);
+  return g2(a.Nv, o2, twv, s);
 }
 
 int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float2* b1,
@@ -430,7 +431,7 @@ int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float
   {
     // sky + corr + tq in once, one half plane out per term
     ProfScope ps(PC_FFT_ROWS, s, img * 12.0 + nterms * half * 8.0);
-    FR_TRY(d1m(ilog2(a.Nv), o1, twv, s));
+    FR_TRY(d1m(a.Nv, o1, twv, s));
   }
   D2TermsOp o2;
   o2.b1t = b1;
@@ -446,7 +447,7 @@ int degrid_prepass_terms(const PlaneArgs& a, int nterms, const float* sky, float
   o2.ub0 = a.bu0;
   o2.nub = nub;
   ProfScope ps(PC_FFT_COLS, s, nterms * (half * 8.0 + full * 8.0));
-  return d2i(ilog2(a.Nu), o2, twu, s);
+  return d2i(a.Nu, o2, twu, s);
 }
 
 int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t grid_stride,
@@ -470,7 +471,7 @@ int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t gri
   o1.nub = nub;
   {
     ProfScope ps(PC_FFT_COLS, s, nterms * (band * 16.0 + (double)a.nx * nvb * 8.0));
-    FR_TRY(g1t(ilog2(a.Nu), o1, nterms, twu, s));
+    FR_TRY(g1t(a.Nu, o1, nterms, twu, s));
   }
   G2TermsAddOp o2;
   o2.b1 = b1;
@@ -486,10 +487,8 @@ int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t gri
   FR_CUDA_TRY(cudaMemsetAsync(dirty, 0, (size_t)a.nx * a.ny * sizeof(float), s));
   // per term the band of a half plane in, corr + tq in and the image added to
   ProfScope ps(PC_FFT_ROWS, s, nterms * ((double)a.nx * nvb * 8.0 + img * 16.0));
-  return g2a(ilog2(a.Nv), o2, nterms, twv, s);
+  return g2a(a.Nv, o2, nterms, twv, s);
 }
 
-int fft_max_log2() { return 14; }
-int fft_min_log2() { return 5; }
 
 }  // namespace fr

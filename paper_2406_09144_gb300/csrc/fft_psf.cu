@@ -226,9 +226,12 @@ bool fft_len_supported(int L) {
   return false;
 }
 
-bool psf_padding_ok(int nx, int ny, int lx, int ly) {
-  return lx > nx && lx <= 2 * nx && ly > ny && ly <= 2 * ny && lx % 2 == 0 && ly % 2 == 0 &&
-         fft_len_supported(lx) && fft_len_supported(ly);
+int fft_len_at_least(int m) {
+  int best = 16384;
+  for (int c : {1, 3, 5})
+    for (int L = 16 * c; L <= 16384; L *= 2)
+      if (L >= m && L < best && fft_len_supported(L)) best = L;
+  return best;
 }
 
 int psf_apply_passes(const PsfArgs& a, float2* h, float2* ht, const float2* tw_rows,

@@ -201,7 +201,8 @@ struct fr_plan {
   std::vector<double> psf_norm;  // [nsky]
   float* psf_img = nullptr;      // [nsky][2nx][2ny]
   float* transfer = nullptr;     // [nsky][psf_ly/2+1][psf_lx], includes 1 / (lx ly)
-  int psf_lx = 0, psf_ly = 0;    // padded PSF transform lengths (2nx, 2ny: the whole PSF)
+  int psf_lx = 0, psf_ly = 0;    // padded PSF transform lengths (>= 2nx - 1: the whole PSF)
+  size_t transfer_cap = 0;       // floats allocated for the transfer function
   // noise model of the fast-resolve likelihood (Sec. 3.3.3): 1 / K_xi, [nsky][ny][nx]
   bool has_noise = false;
   float* noise_kinv = nullptr;
@@ -219,7 +220,8 @@ struct fr_plan {
 namespace fr {
 
 // twiddle tables
-int ensure_twiddles(fr_plan* p, int log2l, cudaStream_t s);
+int ensure_twiddles(fr_plan* p, int L, cudaStream_t s);
+const float2* twiddles_of(fr_plan* p, int L);
 
 // -------- FFT passes (fft_*.cu) --------
 struct PlaneArgs {
@@ -269,10 +271,8 @@ int build_transfer(int nx, int ny, int nsky, const float* psf, int lx, int ly, f
                    float* transfer, const float2* tw_rows, const float2* tw_cols, cudaStream_t s);
 // lengths the PSF passes take (powers of two 32..16384, 3 2^k 48..6144, 5 2^k 80..5120)
 bool fft_len_supported(int L);
-// nx < lx <= 2nx, ny < ly <= 2ny, both even and supported
-bool psf_padding_ok(int nx, int ny, int lx, int ly);
-int fft_max_log2();
-int fft_min_log2();
+// the shortest supported length >= m (m <= 16384)
+int fft_len_at_least(int m);
 // noise model passes (noise.cu): n_delta [nsky][nx][ny] -> kinv [nsky][ny][nx], logdet [nsky]
 // (accumulated); ht scratch [nsky][ny][nx]
 int noise_kernel_passes(const float* n_delta, int nx, int ny, int nsky, float eps, float2* ht,

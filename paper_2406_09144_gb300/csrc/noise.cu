@@ -149,10 +149,10 @@ template <int LEN>
 static int run_nk3(const NK3Op& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nimg, tw, s); }
 template <int LEN>
 static int run_nkf(const NKFOp& op, int nimg, const float2* tw, cudaStream_t s) { return launch_pass<LEN, -1, -1>(op, nimg, tw, s); }
-static int nk1(int lg, const NK1Op& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_nk1, op, n, tw, s); }
-static int nk2(int lg, const NK2Op& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_nk2, op, n, tw, s); }
-static int nk3(int lg, const NK3Op& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_nk3, op, n, tw, s); }
-static int nkf(int lg, const NKFOp& op, int n, const float2* tw, cudaStream_t s) { FR_LOG2_DISPATCH(lg, run_nkf, op, n, tw, s); }
+static int nk1(int len, const NK1Op& op, int n, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_nk1, op, n, tw, s); }
+static int nk2(int len, const NK2Op& op, int n, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_nk2, op, n, tw, s); }
+static int nk3(int len, const NK3Op& op, int n, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_nk3, op, n, tw, s); }
+static int nkf(int len, const NKFOp& op, int n, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_nkf, op, n, tw, s); }
 
 int noise_kernel_passes(const float* n_delta, int nx, int ny, int nsky, float eps, float2* ht,
                         float* kinv, double* logdet, const float2* tw_y, const float2* tw_x,
@@ -165,7 +165,7 @@ int noise_kernel_passes(const float* n_delta, int nx, int ny, int nsky, float ep
   o1.ny = ny;
   {
     ProfScope ps(PC_PSF_ROWS, s, px * 4.0 + px * 8.0);
-    FR_TRY(nk1(ilog2(ny), o1, nsky, tw_y, s));
+    FR_TRY(nk1(ny, o1, nsky, tw_y, s));
   }
   NKFOp of;
   of.ht = ht;
@@ -175,7 +175,7 @@ int noise_kernel_passes(const float* n_delta, int nx, int ny, int nsky, float ep
   of.nx = nx;
   of.ny = ny;
   ProfScope ps(PC_PSF_COLS, s, px * 8.0 + px * 4.0);
-  return nkf(ilog2(nx), of, nsky, tw_x, s);
+  return nkf(nx, of, nsky, tw_x, s);
 }
 
 int noise_inverse_passes(const float* x, int nx, int ny, int nimg, int nsky, const float* kinv,
@@ -189,7 +189,7 @@ int noise_inverse_passes(const float* x, int nx, int ny, int nimg, int nsky, con
   o1.ny = ny;
   {
     ProfScope ps(PC_PSF_ROWS, s, px * 4.0 + px * 8.0);
-    FR_TRY(nk1(ilog2(ny), o1, nimg, tw_y, s));
+    FR_TRY(nk1(ny, o1, nimg, tw_y, s));
   }
   NK2Op o2;
   o2.ht = ht;
@@ -200,7 +200,7 @@ int noise_inverse_passes(const float* x, int nx, int ny, int nimg, int nsky, con
   o2.nsky = nsky;
   {
     ProfScope ps(PC_PSF_COLS, s, px * 16.0 + (double)nsky * nx * ny * 4.0);
-    FR_TRY(nk2(ilog2(nx), o2, nimg, tw_x, s));
+    FR_TRY(nk2(nx, o2, nimg, tw_x, s));
   }
   NK3Op o3;
   o3.h = h;
@@ -213,7 +213,7 @@ int noise_inverse_passes(const float* x, int nx, int ny, int nimg, int nsky, con
   o3.ny = ny;
   o3.nsky = nsky;
   ProfScope ps(PC_PSF_ROWS, s, px * 8.0 + px * 4.0 + (t ? px * 4.0 : 0.0));
-  return nk3(ilog2(ny), o3, nimg, tw_y, s);
+  return nk3(ny, o3, nimg, tw_y, s);
 }
 
 }  // namespace fr

@@ -158,13 +158,15 @@ def _pixsize_from_uv(uvw: np.ndarray, fmax: float, factor: float = 2.2) -> float
 
 
 def observation(name: str, seed_array: int = 1, seed_noise: int = 2, hours=None,
-                step_s=None) -> Observation:
+                step_s=None, npix=None) -> Observation:
     """Preset workloads.
 
     small   : 128^2, 1 ch at 1.4 GHz, VLA-like 27 antennas, 4 h at 10 s (505,440 rows), w = 0
     vla     : 1024^2 at 0.1", 1 ch 1.4 GHz, 27 antennas, 8 h at 2 s (5,054,400 rows), w-terms
     meerkat : 4096^2 at 2", 8 ch 909.5 + 107 i MHz, 64 antennas, 8 h at 8 s (7,257,600 rows)
     tiny    : 32^2, VLA-like, 20 min at 60 s, w-terms; for brute-force checks
+    npix overrides the image side at the preset's pixel size (e.g. 3600 with the MeerKAT-like
+    array: Tab. 2's 2 degree field of 3600^2 pixels of 2").
     """
     if name in ("small", "tiny"):
         enu = vla_like_enu(seed_array)
@@ -206,6 +208,8 @@ def observation(name: str, seed_array: int = 1, seed_noise: int = 2, hours=None,
     else:
         raise ValueError(f"unknown observation preset {name!r}")
     sig = np.broadcast_to(sig, (uvw.shape[0], len(freqs))).astype(np.float64)
+    if npix is not None:
+        nx = ny = int(npix)
     return Observation(name=name, uvw=uvw, freqs=freqs, weights=1.0 / sig ** 2, sigma=sig,
                        nx=nx, ny=ny, pixsize=pix, wterm=wterm, per_channel_sky=per_chan)
 
