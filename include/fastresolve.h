@@ -157,7 +157,8 @@ int fr_major_cycle(fr_plan_t plan, const float *sky, const float *dirty, float *
  *   logdet     host float64 [nsky] or NULL: 1/2 sum_k ln(2 pi K_k), the ln|2 pi N'| / 2 term of
  *              Eq. ham_new (constant in the sky)
  * The noise passes transform the unpadded image: nx and ny must each be 2^k (>= 32), 3 2^k
- * (>= 48) or 5 2^k (>= 80) (FR_EUNSUPPORTED otherwise). Synchronises `stream`. */
+ * (>= 48), 5 2^k (>= 80) or c 2^k (a multiple of 16, >= 144) with c in {9, 15, 25, 45, 75,
+ * 225}, which includes 3600 (FR_EUNSUPPORTED otherwise). Synchronises `stream`. */
 int fr_noise_fit(fr_plan_t plan, double eps_noise, double *logdet, void *stream);
 
 /* The fitted kernel K (not its inverse): device float32 [nsky][nx][ny] in numpy.fft.fft2 order

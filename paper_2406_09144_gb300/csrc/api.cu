@@ -210,7 +210,7 @@ static int make_twiddles(float2** out, int L, cudaStream_t s) {
 
 // twiddle table of any length the FFT passes take (powers of two, 3 2^k, 5 2^k)
 int ensure_twiddles(fr_plan* p, int L, cudaStream_t s) {
-  if (!fft_len_supported(L)) {
+  if (!fft_len_supported(L) && !noise_len_supported(L)) {
     set_error("FFT length %d unsupported", L);
     return FR_EUNSUPPORTED;
   }
@@ -1084,9 +1084,10 @@ __global__ void kernel_from_inverse(const float* kinv, int nsky, int nx, int ny,
 
 // the noise passes transform the unpadded image: nx and ny must themselves be FFT lengths
 static int noise_sizes_ok(const fr_plan* p) {
-  if (!fft_len_supported(p->geo.nx) || !fft_len_supported(p->geo.ny)) {
-    set_error("the noise model needs nx, ny of the form 2^k (>= 32), 3 2^k (>= 48) or 5 2^k "
-              "(>= 80) (got %d x %d)", p->geo.nx, p->geo.ny);
+  if (!noise_len_supported(p->geo.nx) || !noise_len_supported(p->geo.ny)) {
+    set_error("the noise model needs nx, ny of the form 2^k (>= 32), 3 2^k (>= 48), 5 2^k "
+              "(>= 80) or c 2^k (a multiple of 16, >= 144) with c in {9, 15, 25, 45, 75, 225} "
+              "(got %d x %d)", p->geo.nx, p->geo.ny);
     return FR_EUNSUPPORTED;
   }
   return FR_OK;

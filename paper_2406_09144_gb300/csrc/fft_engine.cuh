@@ -349,36 +349,98 @@ struct OpBase {
 // Dispatch on a runtime length: the powers of two 32 .. 16384, 3 2^k for 48 .. 6144 and
 // 5 2^k for 80 .. 5120 (the reduced-padding PSF transforms of images up to 4096 a side);
 // fft_len_supported() agrees.
-#define FR_LEN_DISPATCH(len, F, ...)                                   \
-  switch (len) {                                                       \
-    case 32: return F<32>(__VA_ARGS__);                                \
-    case 64: return F<64>(__VA_ARGS__);                                \
-    case 128: return F<128>(__VA_ARGS__);                              \
-    case 256: return F<256>(__VA_ARGS__);                              \
-    case 512: return F<512>(__VA_ARGS__);                              \
-    case 1024: return F<1024>(__VA_ARGS__);                            \
-    case 2048: return F<2048>(__VA_ARGS__);                            \
-    case 4096: return F<4096>(__VA_ARGS__);                            \
-    case 8192: return F<8192>(__VA_ARGS__);                            \
-    case 16384: return F<16384>(__VA_ARGS__);                          \
-    case 48: return F<48>(__VA_ARGS__);                                \
-    case 96: return F<96>(__VA_ARGS__);                                \
-    case 192: return F<192>(__VA_ARGS__);                              \
-    case 384: return F<384>(__VA_ARGS__);                              \
-    case 768: return F<768>(__VA_ARGS__);                              \
-    case 1536: return F<1536>(__VA_ARGS__);                            \
-    case 3072: return F<3072>(__VA_ARGS__);                            \
-    case 6144: return F<6144>(__VA_ARGS__);                            \
-    case 80: return F<80>(__VA_ARGS__);                                \
-    case 160: return F<160>(__VA_ARGS__);                              \
-    case 320: return F<320>(__VA_ARGS__);                              \
-    case 640: return F<640>(__VA_ARGS__);                              \
-    case 1280: return F<1280>(__VA_ARGS__);                            \
-    case 2560: return F<2560>(__VA_ARGS__);                            \
-    case 5120: return F<5120>(__VA_ARGS__);                            \
-    default:                                                           \
-      ::fr::set_error("FFT length %d unsupported", (int)(len));        \
-      return FR_EUNSUPPORTED;                                          \
+#define FR_LEN_CASES(F, ...)                      \
+  case 32: return F<32>(__VA_ARGS__);             \
+  case 64: return F<64>(__VA_ARGS__);             \
+  case 128: return F<128>(__VA_ARGS__);           \
+  case 256: return F<256>(__VA_ARGS__);           \
+  case 512: return F<512>(__VA_ARGS__);           \
+  case 1024: return F<1024>(__VA_ARGS__);         \
+  case 2048: return F<2048>(__VA_ARGS__);         \
+  case 4096: return F<4096>(__VA_ARGS__);         \
+  case 8192: return F<8192>(__VA_ARGS__);         \
+  case 16384: return F<16384>(__VA_ARGS__);       \
+  case 48: return F<48>(__VA_ARGS__);             \
+  case 96: return F<96>(__VA_ARGS__);             \
+  case 192: return F<192>(__VA_ARGS__);           \
+  case 384: return F<384>(__VA_ARGS__);           \
+  case 768: return F<768>(__VA_ARGS__);           \
+  case 1536: return F<1536>(__VA_ARGS__);         \
+  case 3072: return F<3072>(__VA_ARGS__);         \
+  case 6144: return F<6144>(__VA_ARGS__);         \
+  case 80: return F<80>(__VA_ARGS__);             \
+  case 160: return F<160>(__VA_ARGS__);           \
+  case 320: return F<320>(__VA_ARGS__);           \
+  case 640: return F<640>(__VA_ARGS__);           \
+  case 1280: return F<1280>(__VA_ARGS__);         \
+  case 2560: return F<2560>(__VA_ARGS__);         \
+  case 5120: return F<5120>(__VA_ARGS__);
+
+#define FR_LEN_DISPATCH(len, F, ...)                            \
+  switch (len) {                                                \
+    FR_LEN_CASES(F, __VA_ARGS__)                                \
+    default:                                                    \
+      ::fr::set_error("FFT length %d unsupported", (int)(len)); \
+      return FR_EUNSUPPORTED;                                   \
   }
+
+// The noise passes transform the unpadded image, so they also take the image sides whose odd
+// part has several factors 3 and 5: c 2^k <= 4096 with c in {9, 15, 25, 45, 75, 225}, 16 | L
+// (3600 = 225 x 16 is Tab. 2's side); noise_len_supported() agrees. These lengths run CTAs
+// whose thread count need not be a multiple of 32 (225 threads at 3600). They are compiled in
+// a translation unit of their own (noise_extra.cu).
+#define FR_NOISE_EXTRA_DISPATCH(len, F, ...)                          \
+  switch (len) {                                                      \
+    case 144: return F<144>(__VA_ARGS__);                             \
+    case 288: return F<288>(__VA_ARGS__);                             \
+    case 576: return F<576>(__VA_ARGS__);                             \
+    case 1152: return F<1152>(__VA_ARGS__);                           \
+    case 2304: return F<2304>(__VA_ARGS__);                           \
+    case 240: return F<240>(__VA_ARGS__);                             \
+    case 480: return F<480>(__VA_ARGS__);                             \
+    case 960: return F<960>(__VA_ARGS__);                             \
+    case 1920: return F<1920>(__VA_ARGS__);                           \
+    case 3840: return F<3840>(__VA_ARGS__);                           \
+    case 400: return F<400>(__VA_ARGS__);                             \
+    case 800: return F<800>(__VA_ARGS__);                             \
+    case 1600: return F<1600>(__VA_ARGS__);                           \
+    case 3200: return F<3200>(__VA_ARGS__);                           \
+    case 720: return F<720>(__VA_ARGS__);                             \
+    case 1440: return F<1440>(__VA_ARGS__);                           \
+    case 2880: return F<2880>(__VA_ARGS__);                           \
+    case 1200: return F<1200>(__VA_ARGS__);                           \
+    case 2400: return F<2400>(__VA_ARGS__);                           \
+    case 3600: return F<3600>(__VA_ARGS__);                           \
+    default:                                                          \
+      ::fr::set_error("noise-pass length %d unsupported", (int)(len)); \
+      return FR_EUNSUPPORTED;                                         \
+  }
+
+// Sum of one double per thread over the CTA into *dst (atomicAdd), for any blockDim.x (the
+// last warp may be partial: its shuffles name only the lanes that exist, and values read from
+// lanes past the end are discarded).
+__device__ __forceinline__ void block_sum_atomic(double* dst, double acc) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  const int nl = min(32, (int)blockDim.x - 32 * wid);  // lanes in this warp
+  const unsigned mask = nl == 32 ? 0xffffffffu : ((1u << nl) - 1u);
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v = __shfl_down_sync(mask, acc, o);
+    if (lane + o < nl) acc += v;
+  }
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (wid == 0) {
+    acc = lane < nw ? red[lane] : 0.0;
+    const int nl0 = min(32, (int)blockDim.x);
+    const unsigned mask0 = nl0 == 32 ? 0xffffffffu : ((1u << nl0) - 1u);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v = __shfl_down_sync(mask0, acc, o);
+      if (lane + o < nl0) acc += v;
+    }
+    if (lane == 0) atomicAdd(dst, acc);
+  }
+}
 
 }  // namespace fr

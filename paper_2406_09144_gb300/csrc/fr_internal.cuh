@@ -273,6 +273,9 @@ int build_transfer(int nx, int ny, int nsky, const float* psf, int lx, int ly, f
 bool fft_len_supported(int L);
 // the shortest supported length >= m (m <= 16384)
 int fft_len_at_least(int m);
+// lengths the noise passes take: fft_len_supported() ones and c 2^k <= 4096, 16 | L, with c in
+// {9, 15, 25, 45, 75, 225}
+bool noise_len_supported(int L);
 // noise model passes (noise.cu): n_delta [nsky][nx][ny] -> kinv [nsky][ny][nx], logdet [nsky]
 // (accumulated); ht scratch [nsky][ny][nx]
 int noise_kernel_passes(const float* n_delta, int nx, int ny, int nsky, float eps, float2* ht,

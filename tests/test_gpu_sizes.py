@@ -126,6 +126,43 @@ def test_noise_model_at_mixed_radix_size():
         p2.noise_fit(1.0)
 
 
+def test_noise_model_at_sides_with_several_odd_factors():
+    """Noise passes at 144 = 9 x 16 (two radix-3 stages, 144-thread CTAs: a partial warp in the
+    reductions) against the oracle's argmin fit; N'^-1 and the fast-resolve likelihood at
+    144 x 240 (240 = 15 x 16) against the oracle with the GPU's kernel."""
+    nx, ny = 144, 32
+    obs = synth.random_observation(500, 1, nx, ny, 3e-3, seed=99)
+    plan = make_plan(obs, mfs=True)
+    w = obs.weights.astype(np.float32).astype(np.float64)
+    eps_noise = 1e-3 * float(w.sum())
+    logdet = plan.noise_fit(eps_noise)
+    K = plan.noise_kernel().cpu().numpy()
+    n_delta = noise.noise_cov_of_delta(obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, nx, ny,
+                                       eps_noise, weights=w, wterm=obs.wterm)
+    K_ref = noise.fit_noise_kernel(n_delta, eps_noise)
+    assert rel(K, K_ref) <= 5e-5, rel(K, K_ref)
+    assert np.allclose(logdet, 0.5 * np.log(2 * np.pi * K_ref).sum(), rtol=1e-5)
+    nx, ny = 144, 240
+    obs = synth.random_observation(800, 1, nx, ny, 2e-3, seed=100)
+    plan = make_plan(obs, mfs=True)
+    plan.noise_fit(5.0)
+    K = plan.noise_kernel().cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(101)
+    x = rng.standard_normal((2, 1, nx, ny))
+    got = plan.noise_apply_inverse(dev(x)).cpu().numpy()
+    ref = np.stack([noise.noise_inverse(x[b], K) for b in range(2)])
+    assert rel(got, ref) <= 2e-6, rel(got, ref)
+    _, psf, _ = plan.dirty_psf(want_dirty=False)
+    P = psf.cpu().numpy().astype(np.float64)
+    sky = synth.random_skies(2, nx, ny, seed=102)[:, None]
+    d = rng.standard_normal(sky.shape) * 40.0
+    val, grad = plan.fast_likelihood_grad(dev(sky), dev(d))
+    for b in range(2):
+        H, _, g = noise.fast_hamiltonian(P, sky[b], d[b], K)
+        assert abs(val[b] - H[0]) <= 1e-5 * abs(H[0]), (val[b], H[0])
+        assert rel(grad[b].cpu().numpy(), g) <= 1e-5
+
+
 @pytest.mark.slow
 def test_tab2_field_3600_full_size_sampled():
     """Tab. 2's field: 3600^2 pixels of 2" (8192^2 grid, sigma 2.28) with the MeerKAT-like top
@@ -160,3 +197,23 @@ def test_tab2_field_3600_full_size_sampled():
     refc = np.array([np.sum(P[px + 1:px + n + 1, py + 1:py + n + 1][::-1, ::-1] * s)
                      for px, py in pts])
     assert rel(np.array([out[q] for q in pts]), refc) <= 2e-6
+    # the noise model at 3600 (225 x 16: radix 5, 5, 3, 3, 16; 225-thread CTAs): the fitted
+    # kernel is real, bounded below by eps and even (the PSF is), N'^-1 matches the oracle's
+    # FFT definition with that kernel, and the likelihood's gradient a central difference
+    eps_noise = 1e-4 * float(w32.astype(np.float64).sum())
+    plan.noise_fit(eps_noise)
+    K = plan.noise_kernel().cpu().numpy()[0].astype(np.float64)
+    assert np.all(K >= np.float32(eps_noise) * (1 - 1e-6))
+    flip = K[(-np.arange(n)) % n][:, (-np.arange(n)) % n]
+    assert rel(K, flip) <= 1e-4
+    x = rng.standard_normal((1, 1, n, n))
+    got = plan.noise_apply_inverse(dev(x)).cpu().numpy()[0]
+    assert rel(got, noise.noise_inverse(x[0], K[None])) <= 2e-6
+    dd = d[None, None] if d.ndim == 2 else d[None]
+    val, g = plan.fast_likelihood_grad(dev(sky[None]), dev(dd))
+    dirn = rng.standard_normal(sky[None].shape)
+    h = 0.5
+    vp = plan.fast_likelihood_grad(dev(sky[None] + h * dirn), dev(dd))[0][0]
+    vm = plan.fast_likelihood_grad(dev(sky[None] - h * dirn), dev(dd))[0][0]
+    gd = float(np.sum(g.cpu().numpy().astype(np.float64) * dirn))
+    assert abs((vp - vm) / (2 * h) - gd) <= 1e-2 * abs(gd) + 1e-6 * abs(val[0])
