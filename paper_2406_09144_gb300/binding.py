@@ -136,6 +136,20 @@ def selftest_fft_host(x: np.ndarray, direction: int) -> np.ndarray:
     return a
 
 
+def fft_len_at_least(m: int) -> int:
+    """The shortest transform length the library takes that is >= m: 2^k (32..16384),
+    3 2^k (48..6144) or 5 2^k (80..5120). The oversampled grid of an n-pixel side is
+    fft_len_at_least(2 n) (plan info grid_nu reports it)."""
+    best = 16384
+    for c, lo, hi in ((1, 32, 16384), (3, 48, 6144), (5, 80, 5120)):
+        L = c * 16
+        while L <= hi:
+            if L >= max(m, lo) and L < best:
+                best = L
+            L *= 2
+    return best
+
+
 def padded_lengths(n: int):
     """The padded PSF transform lengths fr_psf_set_padding takes for an image side n: even
     L in (n, 2n] of the form 2^k (32..16384), 3 2^k (48..6144) or 5 2^k (80..5120)."""

@@ -67,12 +67,17 @@ class Request:
 def estimate_bytes(req: Request) -> int:
     """HBM footprint of a job while it is admitted: plan-resident data, the per-stream workspace,
     the inputs and outputs, and the PSF-build transients during plan creation."""
+    from .binding import fft_len_at_least
     n = req.nx * req.ny
     m = req.nvis
+    # oversampled grid and PSF-build grid cells (4 n and 16 n for sides of FFT form, more when
+    # the grid rounds up to the next transform length)
+    g = fft_len_at_least(2 * req.nx) * fft_len_at_least(2 * req.ny)
+    gp = fft_len_at_least(4 * req.nx) * fft_len_at_least(4 * req.ny)
     plan = m * 28 + n * 8 + req.nsky * (4 * n * 4 + 2 * n * 4)     # sorted vis, tables, PSF, T
-    work = n * 4 * 8 + n * 4 * 8 + m * 8                           # grid, half planes, vis buffer
-    work += 2 * 4 * n * 4 * 8                                      # small-w expansion term grids
-    build = 16 * n * 8 + 8 * n * 8 + m * 32                        # PSF-build grid and sort temps
+    work = g * 8 + n * 4 * 8 + m * 8                               # grid, half planes, vis buffer
+    work += 2 * 4 * g * 8                                          # small-w expansion term grids
+    build = gp * 8 + 8 * n * 8 + m * 32                            # PSF-build grid and sort temps
     io = req.sky.size * 4 * 2 + (m * 8 * 2 if req.kind == "major" else 0)
     if req.kind == "psf":
         work += req.sky.shape[0] * req.nsky * n * 8 * 2            # half spectra

@@ -13,13 +13,15 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_results_alone_equal_results_in_the_mix():
+# powers of two, and sides on 3 2^k / 5 2^k grids or with a grid above sigma = 2 (100 -> 256)
+@pytest.mark.parametrize("sizes", [(64, 128, 256), (96, 160, 100)])
+def test_results_alone_equal_results_in_the_mix(sizes):
     from paper_2406_09144_gb300 import build
     from paper_2406_09144_gb300.serve import (GpuExecutor, Scheduler, _copy_requests,
                                               estimate_bytes, make_requests, poisson_arrivals,
                                               run_sequential)
     build.build()
-    base = make_requests(12, seed=300, sizes=(64, 128, 256), nvis_range=(2e3, 6e4), nchan_max=3,
+    base = make_requests(12, seed=300, sizes=sizes, nvis_range=(2e3, 6e4), nchan_max=3,
                          ncalls=3)
     alone = run_sequential(_copy_requests(base))
     mix = poisson_arrivals(_copy_requests(base), rate_per_s=400.0, seed=1)

@@ -93,3 +93,20 @@ def test_host_fft_rejects_other_lengths(lib):
     for n in (7, 14, 21 * 16, 1, 32768):
         with pytest.raises(binding.FastResolveError):
             binding.selftest_fft_host(np.zeros((1, max(n, 1)), np.complex64), -1)
+
+
+def test_grid_length_rule():
+    """The Python mirror of the library's transform-length rule (the oversampled grid of a side n
+    is the shortest length >= 2n of the form 2^k, 3 2^k or 5 2^k; tests/test_gpu_sizes.py checks
+    plans against it on the GPU)."""
+    f = binding.fft_len_at_least
+    assert [f(2 * n) for n in (16, 48, 80, 100, 34, 60, 1024, 3600, 4096)] == \
+        [32, 96, 160, 256, 80, 128, 2048, 8192, 8192]
+    for m in range(17, 16385, 37):
+        L = f(m)
+        assert L >= m
+        c = L
+        while c % 2 == 0:
+            c //= 2
+        assert c in (1, 3, 5)
+
