@@ -18,15 +18,26 @@ import numpy as np
 
 
 def reconstruct(plan, vis, n_major=3, n_minor=25, eps_noise=None, prior_mean=None,
-                prior_sigma=3.0, stream=None):
+                prior_sigma=3.0, psf_padding=None, stream=None):
     """Run Alg. 1. vis: device complex64 [nrow, nchan] (user order). Returns (sky, history),
     history = [{"major": i, "resid_norm2": |d_{i+1}|^2, "minor_value": last H + prior}].
 
     eps_noise: the white-noise variance of Eq. N_new (default: 1e-4 of the PSF peak, i.e. of
     the summed weights per image). prior_mean: mu of the log-sky (default: ln of 1e-3 of the
-    dirty image's maximum over the PSF peak).
+    dirty image's maximum over the PSF peak). psf_padding: (lx, ly) for the minor cycles' PSF
+    convolutions (reduced padding, Sec. 3.3.2; the plan's setting is restored afterwards);
+    the major cycles stay exact, so they correct what the truncated PSF misses.
     """
     import torch
+
+    if psf_padding is not None:
+        saved = plan.psf_padding
+        plan.set_psf_padding(*psf_padding, stream=stream)
+        try:
+            return reconstruct(plan, vis, n_major, n_minor, eps_noise, prior_mean, prior_sigma,
+                               None, stream)
+        finally:
+            plan.set_psf_padding(*saved, stream=stream)
 
     dirty = plan.grid(vis, stream=stream)
     _, psf, norm = plan.dirty_psf(want_dirty=False, stream=stream)
