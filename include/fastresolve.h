@@ -62,6 +62,14 @@ typedef struct {
 #define FR_MFS 4u            /* one sky image for all channels (nsky = 1) */
 #define FR_DROP_OOB 8u       /* drop visibilities whose kernel footprint leaves the grid instead of failing */
 #define FR_NO_PSF 16u        /* skip building the PSF (fr_psf_apply / approximate likelihood unavailable) */
+/* bitwise reproducible outputs: the gridders (R^dag, the PSF build, the exact likelihood and
+ * major cycle) accumulate in 64-bit fixed point, whose integer sums do not depend on the order
+ * of the atomic adds, and the expansion terms are added to the image one after the other.
+ * Every contribution is rounded once to a multiple of 2^-61 M n (M the call's largest
+ * contribution, n its visibility count): far below FP32 resolution. Slower gridding (fixed-point
+ * shared memory holds fewer CTAs per SM); FP64 scalar outputs (likelihood values, norms) still
+ * sum per-CTA partials in arrival order and may differ in the last bits. */
+#define FR_DETERMINISTIC 32u
 
 /* Build a plan (plan time, Sec. 3.3.4: done once per observation).
  *   uvw      host float64 [nrow][3] metres
@@ -73,7 +81,8 @@ typedef struct {
  *            forms, at most 2.56 otherwise); fr_plan_get_info reports it
  *   pixsize_x, pixsize_y  pixel size in radians (direction cosines), > 0
  *   eps      requested relative L2 accuracy of R and R^dag, in [1e-6, 1e-2]
- *   flags    FR_WTERM | FR_NTERM | FR_MFS | FR_DROP_OOB | FR_NO_PSF
+ *   flags    FR_WTERM | FR_NTERM | FR_MFS | FR_DROP_OOB | FR_NO_PSF | FR_DETERMINISTIC
+ *            (other bits: FR_EINVAL)
  *   stream   stream for the plan's device work; the call synchronises it before returning
  *   out      receives the plan handle
  * Errors: FR_EINVAL for bad sizes/pointers, non-finite uvw or freqs, negative weights, or a

@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfastresolve.so")
 
-FR_WTERM, FR_NTERM, FR_MFS, FR_DROP_OOB, FR_NO_PSF = 1, 2, 4, 8, 16
+FR_WTERM, FR_NTERM, FR_MFS, FR_DROP_OOB, FR_NO_PSF, FR_DETERMINISTIC = 1, 2, 4, 8, 16, 32
 ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EUNSUPPORTED", -5: "FR_ETIMEOUT"}
 
 EXPORTS = ["fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
@@ -192,7 +192,8 @@ class Plan:
     """A measurement-operator plan: R, R^dagger N^-1, PSF convolution, likelihood."""
 
     def __init__(self, uvw, freqs, nx, ny, pixsize_x, pixsize_y=None, weights=None, eps=1e-5,
-                 wterm=True, nterm=True, mfs=False, drop_oob=False, no_psf=False, stream=None):
+                 wterm=True, nterm=True, mfs=False, drop_oob=False, no_psf=False,
+                 deterministic=False, stream=None):
         lib = load()
         uvw = np.ascontiguousarray(uvw, dtype=np.float64)
         freqs = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
@@ -206,7 +207,8 @@ class Plan:
             wptr = weights.ctypes.data
         self._weights_host = weights  # kept for the adjoint of the weighted gridder
         flags = ((FR_WTERM if wterm else 0) | (FR_NTERM if nterm else 0) | (FR_MFS if mfs else 0)
-                 | (FR_DROP_OOB if drop_oob else 0) | (FR_NO_PSF if no_psf else 0))
+                 | (FR_DROP_OOB if drop_oob else 0) | (FR_NO_PSF if no_psf else 0)
+                 | (FR_DETERMINISTIC if deterministic else 0))
         self.nx, self.ny = int(nx), int(ny)
         self.nsky = 1 if mfs else self.nchan
         h = ctypes.c_void_p()

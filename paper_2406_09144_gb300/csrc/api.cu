@@ -255,6 +255,9 @@ static void free_ws(Workspace* w) {
   cudaFree(w->tmp_img);
   cudaFree(w->tmp_vis);
   cudaFree(w->red);
+  cudaFree(w->gridq);
+  cudaFree(w->det_max);
+  cudaFree(w->det_inv);
   delete w;
 }
 
@@ -342,6 +345,21 @@ static int ws_reserve_terms_g(const Geometry& g, Workspace* w, cudaStream_t s) {
     FR_CUDA_TRY(cudaMemsetAsync(w->grid_terms_g, 0, n * sizeof(float2), s));
     w->terms_g_zero = true;
   }
+  return FR_OK;
+}
+
+// FR_DETERMINISTIC scratch: a zeroed fixed-point grid of n cells and the scale words
+static int ws_reserve_det(Workspace* w, size_t n, cudaStream_t s) {
+  if (w->gridq_n < n) {
+    cudaFree(w->gridq);
+    w->gridq = nullptr;
+    w->gridq_n = 0;
+    FR_TRY(ws_alloc(&w->gridq, n, w));
+    FR_CUDA_TRY(cudaMemsetAsync(w->gridq, 0, n * sizeof(longlong2), s));
+    w->gridq_n = n;
+  }
+  if (!w->det_max) FR_TRY(ws_alloc(&w->det_max, 1, w));
+  if (!w->det_inv) FR_TRY(ws_alloc(&w->det_inv, 1, w));
   return FR_OK;
 }
 
@@ -449,24 +467,49 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
 }
 
 // R^dag (N^-1) for all images of a layout; vis == null grids ones (PSF)
+// R^dag (N^-1) for all images of a layout. With FR_DETERMINISTIC the gridders accumulate in
+// fixed point (the workspace's grids, or det_in's for the PSF build, which has no workspace).
 static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Workspace* w,
                     const float2* vis, int apply_weights, float* dirty, float2* grid, float2* b1,
-                    float2* ybuf, cudaStream_t s, bool* grid_zero) {
+                    float2* ybuf, cudaStream_t s, bool* grid_zero, const DetArgs* det_in = nullptr) {
   const size_t img = (size_t)geo.nx * geo.ny;
+  const size_t plane = (size_t)geo.Nu * geo.Nv;
+  const bool det = (pl->flags & FR_DETERMINISTIC) != 0;
+  DetArgs d;
+  if (det) {
+    if (det_in) {
+      d = *det_in;
+    } else {
+      FR_TRY(ws_reserve_det(w, use_term_grids(geo) ? geo.nterms * plane : plane, s));
+      d.gridq = w->gridq;
+      d.maxbits = w->det_max;
+      d.inv = w->det_inv;
+    }
+    d.n = lay.nsorted;
+  }
   if (w && use_term_grids(geo)) {
     // small-w expansion: one spreading pass fills every term grid, then each term is transformed
     // and accumulated into the image with its own pixel factor
     FR_TRY(ws_reserve_terms_g(geo, w, s));
-    const size_t plane = (size_t)geo.Nu * geo.Nv;
+    if (det)
+      FR_TRY(det_max(lay, nullptr, vis, apply_weights, geo.nterms - 1,
+                     const_cast<unsigned*>(d.maxbits), s));
     for (int g = 0; g < lay.ngroups; ++g) {
       const int q = lay.plane_base[g];
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) {
         FR_CUDA_TRY(cudaMemsetAsync(dirty + g * img, 0, img * sizeof(float), s));
         continue;
       }
-      w->terms_g_zero = false;
-      FR_TRY(grid_terms(geo, lay, g, vis, apply_weights, w->grid_terms_g, s));
       PlaneArgs a = plane_args(geo, lay, g, 0);
+      if (det) {
+        FR_TRY(grid_terms(geo, lay, g, vis, apply_weights, w->grid_terms_g, d, s));
+        FR_TRY(grid_postpass_terms_q(a, geo.nterms, d, plane, w->b1g_terms,
+                                     (size_t)geo.nx * geo.Nv, dirty + g * img,
+                                     twiddles_of(pl, geo.Nu), twiddles_of(pl, geo.Nv), s));
+        continue;
+      }
+      w->terms_g_zero = false;
+      FR_TRY(grid_terms(geo, lay, g, vis, apply_weights, w->grid_terms_g, d, s));
       FR_TRY(grid_postpass_terms(a, geo.nterms, w->grid_terms_g, plane, w->b1g_terms,
                                  (size_t)geo.nx * geo.Nv, dirty + g * img, twiddles_of(pl, geo.Nu),
                                  twiddles_of(pl, geo.Nv), s));
@@ -475,18 +518,28 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
     return FR_OK;
   }
   FR_TRY(grid_prepare(geo, lay, vis, apply_weights, ybuf, s));
-  if (!*grid_zero) FR_CUDA_TRY(cudaMemsetAsync(grid, 0, (size_t)geo.Nu * geo.Nv * sizeof(float2), s));
-  *grid_zero = true;
+  if (det) {
+    FR_TRY(det_max(lay, ybuf, nullptr, 0, geo.taylor ? geo.nterms - 1 : 0,
+                   const_cast<unsigned*>(d.maxbits), s));
+  } else {
+    if (!*grid_zero)
+      FR_CUDA_TRY(cudaMemsetAsync(grid, 0, plane * sizeof(float2), s));
+    *grid_zero = true;
+  }
   for (int g = 0; g < lay.ngroups; ++g) {
     const int P = geo.wterm ? lay.planes[g] : 1;
     bool written = false;
     for (int p = 0; p < P; ++p) {
       const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
-      FR_TRY(grid_plane(geo, lay, g, p, ybuf, grid, s));
+      FR_TRY(grid_plane(geo, lay, g, p, ybuf, grid, d, s));
       PlaneArgs a = plane_args(geo, lay, g, p);
-      FR_TRY(grid_postpass(a, grid, b1, dirty + g * img, written ? 1 : 0, twiddles_of(pl, geo.Nu),
-                           twiddles_of(pl, geo.Nv), s));
+      if (det)
+        FR_TRY(grid_postpass_q(a, d, b1, dirty + g * img, written ? 1 : 0,
+                               twiddles_of(pl, geo.Nu), twiddles_of(pl, geo.Nv), s));
+      else
+        FR_TRY(grid_postpass(a, grid, b1, dirty + g * img, written ? 1 : 0,
+                             twiddles_of(pl, geo.Nu), twiddles_of(pl, geo.Nv), s));
       written = true;
     }
     if (!written) FR_CUDA_TRY(cudaMemsetAsync(dirty + g * img, 0, img * sizeof(float), s));
@@ -561,9 +614,26 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
       r = FR_ENOMEM;
     }
   }
+  // FR_DETERMINISTIC: a transient fixed-point grid and scale words for the PSF's gridding
+  DetArgs pdet;
+  void* detbuf = nullptr;
+  if (r == FR_OK && (p->flags & FR_DETERMINISTIC)) {
+    const size_t cells = (size_t)pg.Nu * pg.Nv;
+    cudaError_t e = cudaMallocAsync(&detbuf, cells * sizeof(longlong2) + 256, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(detbuf, 0, cells * sizeof(longlong2), s);
+    if (e != cudaSuccess) {
+      set_error("PSF allocation failed: %s", cudaGetErrorString(e));
+      r = FR_ENOMEM;
+    } else {
+      pdet.gridq = (longlong2*)detbuf;
+      pdet.maxbits = (unsigned*)((char*)detbuf + cells * sizeof(longlong2));
+      pdet.inv = (double*)((char*)detbuf + cells * sizeof(longlong2) + 128);
+    }
+  }
   if (r == FR_OK) {
     bool zero = true;  // zeroed above
-    r = run_grid(p, pg, pl, nullptr, nullptr, 1, p->psf_img, grid, b1, y, s, &zero);
+    r = run_grid(p, pg, pl, nullptr, nullptr, 1, p->psf_img, grid, b1, y, s, &zero,
+                 (p->flags & FR_DETERMINISTIC) ? &pdet : nullptr);
   }
   if (r == FR_OK) r = zero_psf_edges(p->psf_img, p->nsky, pg.nx, pg.ny, s);
   if (r == FR_OK)
@@ -592,7 +662,7 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
     }
   }
   for (void* q : {(void*)d_norm, (void*)grid, (void*)b1, (void*)y, (void*)h, (void*)pg.corr,
-                  (void*)pg.tq})
+                  (void*)pg.tq, detbuf})
     if (q) cudaFreeAsync(q, s);
   free_layout(&pl);
   cudaStreamSynchronize(s);
@@ -607,6 +677,11 @@ static int build_psf(fr_plan* p, const double* d_uvw, const double* freqs, const
 static int plan_create(const double* uvw, int64_t nrow, const double* freqs, int32_t nchan,
                        const float* weights, int32_t nx, int32_t ny, double dx, double dy,
                        double eps, uint32_t flags, cudaStream_t s, fr_plan* p) {
+  if (flags & ~(FR_WTERM | FR_NTERM | FR_MFS | FR_DROP_OOB | FR_NO_PSF | FR_DETERMINISTIC)) {
+    set_error("unknown flag bits 0x%x", flags & ~(FR_WTERM | FR_NTERM | FR_MFS | FR_DROP_OOB |
+                                                  FR_NO_PSF | FR_DETERMINISTIC));
+    return FR_EINVAL;
+  }
   if (!uvw || !freqs || nrow <= 0 || nchan <= 0) {
     set_error("uvw/freqs must be non-null with nrow > 0 and nchan > 0");
     return FR_EINVAL;

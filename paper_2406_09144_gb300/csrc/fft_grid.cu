@@ -18,6 +18,7 @@
 //   G2 (B1 rows, along v): inverse FFT, keep ny outputs, Re(Z conj(c_p(j))) accumulated into the
 //      dirty image.
 #include "fft_engine.cuh"
+#include "vis_common.cuh"
 
 namespace fr {
 
@@ -233,6 +234,30 @@ struct G1Op : OpBase {
   }
 };
 
+// G1 on the fixed-point grids of FR_DETERMINISTIC: each cell is converted back to float with the
+// call's inverse scale (one value in device memory) and the band is zeroed as in G1Op.
+struct G1QOp : G1Op {
+  longlong2* gridq;
+  const double* inv;
+  __device__ float2 load(int q, int i) const {
+    if (i < ub0 || i >= ub0 + nub) return make_float2(0.f, 0.f);
+    const longlong2 c = gridq[blockIdx.y * grid_stride + (size_t)(vb0 + q) * Nu + i];
+    const double f = __ldg(inv);
+    return make_float2((float)((double)c.x * f), (float)((double)c.y * f));
+  }
+  __device__ void after_load(int seq0, int nb) const {
+    const int n = nb * nub;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int r = i / nub, c = i - (i / nub) * nub;
+      gridq[blockIdx.y * grid_stride + (size_t)(vb0 + seq0 + r) * Nu + ub0 + c] = longlong2{0, 0};
+    }
+  }
+};
+
+__global__ void det_inv_kernel(const unsigned* maxbits, long long n, double* inv) {
+  *inv = 1.0 / det_scale(maxbits, n);
+}
+
 struct G2Op : OpBase {
   const float2* b1;
   float* dirty;
@@ -319,6 +344,9 @@ static int run_d2i(const D2TermsOp& op, const float2* tw, cudaStream_t s) { retu
 static int d2i(int len, const D2TermsOp& op, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_d2i, op, tw, s); }
 template <int LEN>
 static int run_g1t(const G1Op& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nt, tw, s); }
+template <int LEN>
+static int run_g1q(const G1QOp& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nt, tw, s); }
+static int g1q(int len, const G1QOp& op, int nt, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_g1q, op, nt, tw, s); }
 template <int LEN>
 static int run_g2a(const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nt, tw, s); }
 static int g2a(int len, const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_g2a, op, nt, tw, s); }
@@ -490,5 +518,102 @@ int grid_postpass_terms(const PlaneArgs& a, int nterms, float2* grid, size_t gri
   return g2a(a.Nv, o2, nterms, twv, s);
 }
 
+
+// ------------------------------------------------------------ FR_DETERMINISTIC post-passes
+static float host_inv_fact(int t) {
+  double f = 1.0;
+  for (int k = 2; k <= t; ++k) f *= k;
+  return (float)(1.0 / f);
+}
+
+static G1QOp g1q_op(const PlaneArgs& a, const DetArgs& det, double* inv, float2* b1,
+                    size_t grid_stride, size_t b1_stride) {
+  G1QOp o;
+  o.grid = nullptr;
+  o.gridq = det.gridq;
+  o.inv = inv;
+  o.b1 = b1;
+  o.grid_stride = grid_stride;
+  o.b1_stride = b1_stride;
+  o.nx = a.nx;
+  o.Nu = a.Nu;
+  o.Nv = a.Nv;
+  o.vb0 = a.bv0;
+  o.nvb = a.bv1 - a.bv0 + 1;
+  o.ub0 = a.bu0;
+  o.nub = a.bu1 - a.bu0 + 1;
+  return o;
+}
+
+int grid_postpass_q(const PlaneArgs& a, const DetArgs& det, float2* b1, float* dirty,
+                    int accumulate, const float2* twu, const float2* twv, cudaStream_t s) {
+  const int nvb = a.bv1 - a.bv0 + 1, nub = a.bu1 - a.bu0 + 1;
+  if (nvb <= 0 || nub <= 0) return FR_OK;
+  double* inv = det.inv;
+  det_inv_kernel<<<1, 1, 0, s>>>(det.maxbits, det.n, inv);
+  FR_LAUNCHED();
+  {
+    ProfScope ps(PC_FFT_COLS, s, (double)nvb * nub * 32.0 + (double)a.nx * nvb * 8.0);
+    FR_TRY(g1q(a.Nu, g1q_op(a, det, inv, b1, 0, 0), 1, twu, s));
+  }
+  G2Op o2;
+  o2.b1 = b1;
+  o2.dirty = dirty;
+  o2.corr = a.corr;
+  o2.tq = a.tq;
+  o2.k64 = a.k64;
+  o2.wterm = a.wterm;
+  o2.taylor = a.taylor;
+  o2.n = a.n;
+  o2.inv_fact = a.inv_fact;
+  o2.accumulate = accumulate;
+  o2.nx = a.nx;
+  o2.ny = a.ny;
+  o2.Nv = a.Nv;
+  o2.vb0 = a.bv0;
+  o2.nvb = nvb;
+  ProfScope ps(PC_FFT_ROWS, s,
+               (double)a.nx * nvb * 8.0 +
+                   (double)a.nx * a.ny * (4.0 + (a.wterm ? 4.0 : 0.0) + (accumulate ? 8.0 : 4.0)));
+  return g2(a.Nv, o2, twv, s);
+}
+
+int grid_postpass_terms_q(const PlaneArgs& a, int nterms, const DetArgs& det, size_t grid_stride,
+                          float2* b1, size_t b1_stride, float* dirty, const float2* twu,
+                          const float2* twv, cudaStream_t s) {
+  const int nvb = a.bv1 - a.bv0 + 1, nub = a.bu1 - a.bu0 + 1;
+  if (nvb <= 0 || nub <= 0 || nterms <= 0) return FR_OK;
+  double* inv = det.inv;
+  det_inv_kernel<<<1, 1, 0, s>>>(det.maxbits, det.n, inv);
+  FR_LAUNCHED();
+  {
+    ProfScope ps(PC_FFT_COLS, s,
+                 nterms * ((double)nvb * nub * 32.0 + (double)a.nx * nvb * 8.0));
+    FR_TRY(g1q(a.Nu, g1q_op(a, det, inv, b1, grid_stride, b1_stride), nterms, twu, s));
+  }
+  // the terms one after the other (no atomics): term t adds corr Re(Z_t) tau^t / t!
+  for (int t = 0; t < nterms; ++t) {
+    G2Op o2;
+    o2.b1 = b1 + t * b1_stride;
+    o2.dirty = dirty;
+    o2.corr = a.corr;
+    o2.tq = a.tq;
+    o2.k64 = a.k64;
+    o2.wterm = 1;
+    o2.taylor = 1;
+    o2.n = t;
+    o2.inv_fact = host_inv_fact(t);
+    o2.accumulate = t > 0;
+    o2.nx = a.nx;
+    o2.ny = a.ny;
+    o2.Nv = a.Nv;
+    o2.vb0 = a.bv0;
+    o2.nvb = nvb;
+    ProfScope ps(PC_FFT_ROWS, s,
+                 (double)a.nx * nvb * 8.0 + (double)a.nx * a.ny * (t > 0 ? 20.0 : 16.0));
+    FR_TRY(g2(a.Nv, o2, twv, s));
+  }
+  return FR_OK;
+}
 
 }  // namespace fr

@@ -184,6 +184,12 @@ struct Workspace {
   size_t img_n = 0;
   float2* b1_terms = nullptr;   // [nterms][band v][nx] degridding half planes
   float2* b1g_terms = nullptr;  // [nterms][nx][Nv] gridding half planes (zero off-band)
+  // FR_DETERMINISTIC: fixed-point grid(s) (kept zero), the call's largest contribution (float
+  // bits) and 1 / scale
+  longlong2* gridq = nullptr;
+  size_t gridq_n = 0;
+  unsigned* det_max = nullptr;
+  double* det_inv = nullptr;
   size_t bytes = 0;
 };
 
@@ -224,6 +230,15 @@ int ensure_twiddles(fr_plan* p, int L, cudaStream_t s);
 const float2* twiddles_of(fr_plan* p, int L);
 
 // -------- FFT passes (fft_*.cu) --------
+// FR_DETERMINISTIC gridding (vis_common.cuh): with gridq set, the gridders add into 64-bit
+// fixed-point grids (longlong2 per cell, same layout as the float2 grids) at the scale derived
+// from *maxbits (det_max) and n
+struct DetArgs {
+  longlong2* gridq = nullptr;
+  const unsigned* maxbits = nullptr;
+  double* inv = nullptr;  // 1 / scale, written before the post-pass reads the fixed-point grid
+  long long n = 0;
+};
 struct PlaneArgs {
   // geometry
   int nx, ny, Nu, Nv;
@@ -250,6 +265,13 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
                    const float2* twv, const float2* twu, cudaStream_t s);
 int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
                   const float2* twu, const float2* twv, cudaStream_t s);
+// the same from fixed-point grids (FR_DETERMINISTIC); the terms are added to the image one
+// after the other instead of with atomics
+int grid_postpass_q(const PlaneArgs& a, const DetArgs& det, float2* b1, float* dirty,
+                    int accumulate, const float2* twu, const float2* twv, cudaStream_t s);
+int grid_postpass_terms_q(const PlaneArgs& a, int nterms, const DetArgs& det, size_t grid_stride,
+                          float2* b1, size_t b1_stride, float* dirty, const float2* twu,
+                          const float2* twv, cudaStream_t s);
 // PSF-apply passes over nimg images of nx x ny; image i uses transfer + (i % nsky) * tstride
 struct PsfArgs {
   int nx, ny, nimg, nsky;
@@ -304,10 +326,12 @@ int term_grid_count(const Geometry& geo);  // T: terms per cell of the interleav
 int make_tmap_terms(CUtensorMap* m, float2* grid, int Nu, int Nv, int T, int W);
 int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtensorMap& tmap,
                  float2* vis_out, int* status, cudaStream_t s);
+int det_max(const VisLayout& lay, const float2* ysorted, const float2* vis, int apply_weights,
+            int pw, unsigned* maxbits, cudaStream_t s);
 int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* vis,
-               int apply_weights, float2* grid_terms, cudaStream_t s);
+               int apply_weights, float2* grid_terms, const DetArgs& det, cudaStream_t s);
 int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const float2* ysorted,
-               float2* grid, cudaStream_t s);
+               float2* grid, const DetArgs& det, cudaStream_t s);
 int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, int apply_weights,
                  float2* ysorted, cudaStream_t s);
 int make_tables(Geometry* geo, const std::vector<double>& inv_phi_u,

@@ -1115,13 +1115,13 @@ static int presort_items(VisLayout* lay, int64_t N, bool wterm, cudaStream_t s) 
 // shared-memory counting sort, so each warp walks runs of visibilities that share an origin;
 // a run is accumulated in registers and added to the warp's sub-grid once, when the origin
 // changes.
-template <int W>
+template <int W, bool DET>
 __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __restrict__ items,
                                                                MetaPtrs m, EsKernel kern, int p,
                                                                int wmode, bool presorted,
                                                                const float2* __restrict__ y,
                                                                float2* __restrict__ grid, int Nu,
-                                                               int Nv) {
+                                                               int Nv, DetArgs det) {
   constexpr int BU = TILE + W - 1;
   constexpr int BV = (TILE + W - 1 + 1) & ~1;
   constexpr int SUB = BU * BV;
@@ -1129,7 +1129,9 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   constexpr int NIT = (CELLS + 31) / 32;
   constexpr int NT = GRID_WARPS * 32;
   constexpr int NKEY = TILE * TILE;
-  extern __shared__ float2 sub[];  // [GRID_WARPS][SUB]
+  // [GRID_WARPS][SUB] per-warp sub-grids; DET: one fixed-point sub-grid [SUB] (longlong2)
+  extern __shared__ __align__(16) float2 sub[];
+  longlong2* subq = reinterpret_cast<longlong2*>(sub);
   __shared__ int hist[NKEY];
   __shared__ short order[STACK_CHUNK];  // only w-stacking items are sorted here
   __shared__ int wsum[GRID_WARPS];
@@ -1140,7 +1142,12 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   // each warp takes a contiguous segment of the sorted order, a multiple of 32 long
   const int seg = (((n + GRID_WARPS - 1) / GRID_WARPS) + 31) & ~31;
   const int nused = n > 0 ? (n + seg - 1) / seg : 0;
-  for (int i = threadIdx.x; i < nused * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
+  if constexpr (DET) {
+    for (int i = threadIdx.x; i < SUB; i += NT) subq[i] = longlong2{0, 0};
+  } else {
+    for (int i = threadIdx.x; i < nused * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
+  }
+  const float scalef = DET ? (float)det_scale(det.maxbits, det.n) : 0.f;
   if (presorted)
     __syncthreads();
   else
@@ -1165,8 +1172,27 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   float2* mv = vals[warp];
   int cur = -1;  // current origin offset rv * BV + ru, uniform across the warp
   float2 acc[NIT];
+  longlong2 accq[NIT];  // DET: each visibility's share rounded to fixed point on its own
 #pragma unroll
-  for (int k = 0; k < NIT; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < NIT; ++k) {
+    acc[k] = make_float2(0.f, 0.f);
+    accq[k] = longlong2{0, 0};
+  }
+  auto run_flush = [&]() {
+#pragma unroll
+    for (int k = 0; k < NIT; ++k)
+      if (lane + 32 * k < CELLS) {
+        if constexpr (DET) {
+          fixed_add_q(subq + cur + off[k], accq[k]);
+        } else {
+          float2* c = mysub + cur + off[k];
+          float2 g = *c;
+          g.x += acc[k].x;
+          g.y += acc[k].y;
+          *c = g;
+        }
+      }
+  };
   for (int base = s0; base < s1; base += 32) {
     const int nb = min(32, s1 - base);
     int org = -2;
@@ -1199,19 +1225,12 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
     while (j < nb) {
       if ((starts >> j) & 1u) {
         const int oj = __shfl_sync(0xffffffffu, org, j);
-        if (cur >= 0) {
+        if (cur >= 0) run_flush();
 #pragma unroll
-          for (int k = 0; k < NIT; ++k)
-            if (lane + 32 * k < CELLS) {
-              float2* c = mysub + cur + off[k];
-              float2 g = *c;
-              g.x += acc[k].x;
-              g.y += acc[k].y;
-              *c = g;
-            }
+        for (int k = 0; k < NIT; ++k) {
+          acc[k] = make_float2(0.f, 0.f);
+          accq[k] = longlong2{0, 0};
         }
-#pragma unroll
-        for (int k = 0; k < NIT; ++k) acc[k] = make_float2(0.f, 0.f);
         cur = oj;
       }
       const unsigned rest = j < 31 ? (starts & ~((2u << j) - 1u)) : 0u;
@@ -1222,38 +1241,83 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
 #pragma unroll
         for (int k = 0; k < NIT; ++k) {
           const float wgt = wj[cu[k]] * wj[W + (cv[k] < W ? cv[k] : 0)];
-          acc[k].x = fmaf(wgt, v.x, acc[k].x);
-          acc[k].y = fmaf(wgt, v.y, acc[k].y);
+          if constexpr (DET) {
+            accq[k].x += to_fixed_f(wgt * v.x, scalef);
+            accq[k].y += to_fixed_f(wgt * v.y, scalef);
+          } else {
+            acc[k].x = fmaf(wgt, v.x, acc[k].x);
+            acc[k].y = fmaf(wgt, v.y, acc[k].y);
+          }
         }
       }
     }
     __syncwarp();
   }
-  if (cur >= 0) {
-#pragma unroll
-    for (int k = 0; k < NIT; ++k)
-      if (lane + 32 * k < CELLS) {
-        float2* c = mysub + cur + off[k];
-        float2 g = *c;
-        g.x += acc[k].x;
-        g.y += acc[k].y;
-        *c = g;
-      }
-  }
+  if (cur >= 0) run_flush();
   __syncthreads();
   for (int idx = threadIdx.x; idx < SUB; idx += blockDim.x) {
     const int r = idx / BV, c = idx - (idx / BV) * BV;
     if (c >= BU) continue;
-    float2 acc = sub[idx];
-    for (int w = 1; w < nused; ++w) {
-      const float2 o = sub[w * SUB + idx];
-      acc.x += o.x;
-      acc.y += o.y;
-    }
-    if (acc.x == 0.f && acc.y == 0.f) continue;
     const int gv = tv * TILE + r, gu = tu * TILE + c;
-    if (gu < Nu && gv < Nv) atomicAdd(&grid[(size_t)gv * Nu + gu], acc);
+    if (gu >= Nu || gv >= Nv) continue;
+    if constexpr (DET) {
+      // integer sums: the same whatever order the warps and CTAs added in
+      const longlong2 q = subq[idx];
+      if (q.x != 0 || q.y != 0) fixed_add_q(&det.gridq[(size_t)gv * Nu + gu], q);
+    } else {
+      // the warps' sub-grids are summed in warp order
+      float2 acc = sub[idx];
+      for (int w = 1; w < nused; ++w) {
+        const float2 o = sub[w * SUB + idx];
+        acc.x += o.x;
+        acc.y += o.y;
+      }
+      if (acc.x == 0.f && acc.y == 0.f) continue;
+      atomicAdd(&grid[(size_t)gv * Nu + gu], acc);
+    }
   }
+}
+
+// Largest contribution magnitude of a gridding call for FR_DETERMINISTIC: |y| over the sorted
+// visibilities (y sorted and weighted, or vis[perm] times the weight), times max(1, |a|)^pw
+// for the expansion terms (a = dw). Positive floats order like their bit patterns.
+__global__ void det_max_kernel(const float2* __restrict__ ysorted, const float2* __restrict__ vis,
+                               const uint32_t* __restrict__ perm, const float* __restrict__ wgt,
+                               int apply_weights, const float* __restrict__ dw, int pw,
+                               long long n, unsigned* maxbits) {
+  float mx = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float2 v;
+    if (ysorted) {
+      v = ysorted[i];
+    } else {
+      v = vis ? vis[perm[i] & 0x7fffffffu] : make_float2(1.f, 0.f);
+      if (apply_weights) {
+        v.x *= wgt[i];
+        v.y *= wgt[i];
+      }
+    }
+    float a = hypotf(v.x, v.y);
+    if (pw > 0) {
+      const float f = fmaxf(1.f, fabsf(dw[i]));
+      for (int k = 0; k < pw; ++k) a *= f;
+    }
+    mx = fmaxf(mx, a * 1.000001f);  // above the float rounding of |y| and of the products
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(maxbits, __float_as_uint(mx));
+}
+
+int det_max(const VisLayout& lay, const float2* ysorted, const float2* vis, int apply_weights,
+            int pw, unsigned* maxbits, cudaStream_t s) {
+  FR_CUDA_TRY(cudaMemsetAsync(maxbits, 0, sizeof(unsigned), s));
+  if (lay.nsorted <= 0) return FR_OK;
+  det_max_kernel<<<grid1d(lay.nsorted), 256, 0, s>>>(ysorted, vis, lay.perm, lay.wgt,
+                                                      apply_weights, lay.dw, pw, lay.nsorted,
+                                                      maxbits);
+  FR_LAUNCHED();
+  return FR_OK;
 }
 
 struct GridPrepArgs {
@@ -1302,22 +1366,28 @@ static int launch_degrid(const Geometry& geo, const VisLayout& lay, int64_t i0, 
   return FR_OK;
 }
 
-template <int W>
-static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n, int p,
-                       const float2* y, float2* grid, cudaStream_t s) {
+template <int W, bool DET>
+static int launch_grid_det(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n, int p,
+                           const float2* y, float2* grid, const DetArgs& det, cudaStream_t s) {
   MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
   constexpr size_t smem = grid_smem_bytes<W>();
   static bool attr = false;
   if (!attr) {
-    FR_CUDA_TRY(cudaFuncSetAttribute(grid_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    FR_CUDA_TRY(cudaFuncSetAttribute(grid_kernel<W, DET>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  grid_kernel<W><<<(unsigned)n, GRID_WARPS * 32, smem, s>>>(lay.items + i0, m, geo.kern, p,
-                                                            wmode_of(geo), lay.presorted, y, grid,
-                                                            geo.Nu, geo.Nv);
+  grid_kernel<W, DET><<<(unsigned)n, GRID_WARPS * 32, smem, s>>>(
+      lay.items + i0, m, geo.kern, p, wmode_of(geo), lay.presorted, y, grid, geo.Nu, geo.Nv, det);
   FR_LAUNCHED();
   return FR_OK;
+}
+
+template <int W>
+static int launch_grid(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n, int p,
+                       const float2* y, float2* grid, const DetArgs& det, cudaStream_t s) {
+  if (det.gridq) return launch_grid_det<W, true>(geo, lay, i0, n, p, y, grid, det, s);
+  return launch_grid_det<W, false>(geo, lay, i0, n, p, y, grid, det, s);
 }
 
 
@@ -1334,14 +1404,14 @@ int degrid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const 
 }
 
 int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const float2* ysorted,
-               float2* grid, cudaStream_t s) {
+               float2* grid, const DetArgs& det, cudaStream_t s) {
   const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);  // expansion terms share one layout
   const int64_t i0 = lay.plane_items[q], i1 = lay.plane_items[q + 1];
   if (i1 <= i0) return FR_OK;
   // each band cell written once, per visit: metadata + weighted visibility
   ProfScope ps(PC_GRID, s,
                band_cells(lay) * 8.0 + (double)lay.plane_visits[q] * (meta_bytes(geo) + 8.0));
-  FR_W_DISPATCH(geo.kern.W, launch_grid, geo, lay, i0, i1 - i0, p, ysorted, grid, s);
+  FR_W_DISPATCH(geo.kern.W, launch_grid, geo, lay, i0, i1 - i0, p, ysorted, grid, det, s);
 }
 
 }  // namespace fr

@@ -116,4 +116,40 @@ inline double band_cells(const VisLayout& lay) {
   return (double)std::max(0, lay.bu1 - lay.bu0 + 1) * std::max(0, lay.bv1 - lay.bv0 + 1);
 }
 
+// ---------------------------------------------------------------- deterministic gridding
+// With FR_DETERMINISTIC the gridders accumulate in 64-bit fixed point: every contribution
+// (one visibility's share of one cell) is rounded once to a multiple of 1/S before any sum, and
+// the integer sums do not depend on the order of the adds, so the grids (and everything computed
+// from them) are the same bit for bit on every run, whatever order the plan sorted the
+// visibilities into. S = 2^e is the largest power of two with S * M * n <= 2^61, M the largest
+// contribution magnitude of the call (max |y| times the largest expansion factor), n the
+// number of visibilities: no cell can overflow, and the rounding error of a cell is at most
+// (number of its contributions) * 2^-62 * M * n.
+__device__ __forceinline__ double det_scale(const unsigned* maxbits, long long n) {
+  const double bound = (double)__uint_as_float(*maxbits) * (double)(n > 0 ? n : 1);
+  if (!(bound > 0.0)) return 1.0;
+  int e;
+  frexp(bound, &e);  // bound < 2^e
+  return ldexp(1.0, 61 - e);
+}
+
+__device__ __forceinline__ long long to_fixed(float v, double scale) {
+  return __double2ll_rn((double)v * scale);
+}
+
+// one contribution in fixed point: v * scale is exact (scale a power of two), then rounded once
+__device__ __forceinline__ long long to_fixed_f(float v, float scalef) {
+  return __float2ll_rn(v * scalef);
+}
+
+__device__ __forceinline__ void fixed_add_q(longlong2* c, longlong2 q) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(&c->x), (unsigned long long)q.x);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&c->y), (unsigned long long)q.y);
+}
+
+__device__ __forceinline__ void fixed_add(longlong2* c, float2 v, double scale) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(&c->x), (unsigned long long)to_fixed(v.x, scale));
+  atomicAdd(reinterpret_cast<unsigned long long*>(&c->y), (unsigned long long)to_fixed(v.y, scale));
+}
+
 }  // namespace fr

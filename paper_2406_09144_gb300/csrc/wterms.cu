@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "fr_internal.cuh"
 #include "vis_common.cuh"
@@ -166,33 +167,41 @@ struct TermsLanes {
   static constexpr int WS = (NV + W + 1) & ~1;          // staged floats per visibility (even)
 };
 
-// dynamic shared memory: NC term sub-grids, then per-warp staged values and kernel weights
+// dynamic shared memory: NC term sub-grids (float2, or longlong2 fixed point with
+// FR_DETERMINISTIC), then per-warp staged values and kernel weights
 template <int W>
-constexpr size_t grid_terms_smem_bytes(int nc) {
-  return (size_t)nc * (TILE + W - 1) * ((TILE + W) & ~1) * sizeof(float2) +
+constexpr size_t grid_terms_smem_bytes(int nc, bool det = false) {
+  return (size_t)nc * (TILE + W - 1) * ((TILE + W) & ~1) *
+             (det ? sizeof(longlong2) : sizeof(float2)) +
          (size_t)TERMS_WARPS * nc * 32 * sizeof(float2) +
          (size_t)TERMS_WARPS * 32 * TermsLanes<W>::WS * sizeof(float);
 }
 
-template <int W, int NC>
-__global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
+// DET (FR_DETERMINISTIC): the runs are added to fixed-point sub-grids and flushed to the
+// fixed-point term grids with integer atomics, so no sum depends on the order of the adds.
+template <int W, int NC, bool DET>
+__global__ void __launch_bounds__(TERMS_WARPS * 32, DET ? 2 : 3) grid_terms_kernel(
     const int4* __restrict__ items, MetaPtrs m, const float* __restrict__ wgt, EsKernel kern,
     int t0, const float2* __restrict__ vis, int apply_weights, float2* __restrict__ grid_terms,
-    int Nu, int Nv) {
+    int Nu, int Nv, DetArgs det) {
   using L = TermsLanes<W>;
+  using Cell = typename std::conditional<DET, longlong2, float2>::type;
   constexpr int BU = TILE + W - 1;
   constexpr int BV = (TILE + W - 1 + 1) & ~1;
   constexpr int SUB = BU * BV;
   constexpr int NT = TERMS_WARPS * 32;
   constexpr int K = L::K, WS = L::WS;
-  extern __shared__ float2 sub[];  // [NC][SUB], then vals [warp][32][NC], then wts [warp][32][WS]
-  float2* vals_all = sub + NC * SUB;
+  // [NC][SUB] sub-grids, then vals [warp][32][NC], then wts [warp][32][WS]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cell* sub = reinterpret_cast<Cell*>(smem_raw);
+  float2* vals_all = reinterpret_cast<float2*>(sub + NC * SUB);
   float* wts = reinterpret_cast<float*>(vals_all + TERMS_WARPS * 32 * NC);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int4 it = items[blockIdx.x];
   const int tu = it.z >> 16, tv = it.z & 0xffff;
   const int n = it.y;
-  for (int i = threadIdx.x; i < NC * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
+  const float scalef = DET ? (float)det_scale(det.maxbits, det.n) : 0.f;
+  for (int i = threadIdx.x; i < NC * SUB; i += NT) sub[i] = Cell{};
   __syncthreads();
 
   const bool active = lane < L::R * W;
@@ -210,20 +219,31 @@ __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
   float* mw = wts + warp * 32 * WS;
   float2* mv = vals_all + warp * 32 * NC;
   int cur = -1;
-  float2 acc[NC][K];
+  float2 acc[NC][K];     // run accumulators
+  longlong2 accq[NC][K]; // the same in fixed point (DET)
+  auto clear = [&]() {
 #pragma unroll
-  for (int t = 0; t < NC; ++t)
+    for (int t = 0; t < NC; ++t)
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[t][k] = make_float2(0.f, 0.f);
+      for (int k = 0; k < K; ++k) {
+        acc[t][k] = make_float2(0.f, 0.f);
+        accq[t][k] = longlong2{0, 0};
+      }
+  };
+  clear();
   auto flush = [&]() {
 #pragma unroll
     for (int t = 0; t < NC; ++t)
 #pragma unroll
       for (int k = 0; k < K; ++k)
         if (valid[k]) {
-          float* c = reinterpret_cast<float*>(sub + t * SUB + cur + off[k]);
-          atomicAdd(c, acc[t][k].x);
-          atomicAdd(c + 1, acc[t][k].y);
+          if constexpr (DET) {
+            fixed_add_q(sub + t * SUB + cur + off[k], accq[t][k]);
+          } else {
+            float* c = reinterpret_cast<float*>(sub + t * SUB + cur + off[k]);
+            atomicAdd(c, acc[t][k].x);
+            atomicAdd(c + 1, acc[t][k].y);
+          }
         }
   };
   auto add = [&](int j) {
@@ -253,9 +273,18 @@ __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const float g = wu * wv[k];
-      const float2 gg = make_float2(g, g);
+      if constexpr (DET) {
+        // each visibility's share rounded to fixed point on its own: order-independent sums
 #pragma unroll
-      for (int t = 0; t < NC; ++t) acc[t][k] = ffma2(gg, vt[t], acc[t][k]);
+        for (int t = 0; t < NC; ++t) {
+          accq[t][k].x += to_fixed_f(g * vt[t].x, scalef);
+          accq[t][k].y += to_fixed_f(g * vt[t].y, scalef);
+        }
+      } else {
+        const float2 gg = make_float2(g, g);
+#pragma unroll
+        for (int t = 0; t < NC; ++t) acc[t][k] = ffma2(gg, vt[t], acc[t][k]);
+      }
     }
   };
   // the next batch's metadata is loaded while the current batch is processed; the gridding
@@ -308,10 +337,7 @@ __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
       if ((starts >> j) & 1u) {
         const int oj = __shfl_sync(0xffffffffu, org, j);
         if (cur >= 0) flush();
-#pragma unroll
-        for (int t = 0; t < NC; ++t)
-#pragma unroll
-          for (int k = 0; k < K; ++k) acc[t][k] = make_float2(0.f, 0.f);
+        clear();
         cur = oj;
       }
       const unsigned rest = j < 31 ? (starts & ~((2u << j) - 1u)) : 0u;
@@ -328,14 +354,20 @@ __global__ void __launch_bounds__(TERMS_WARPS * 32, 3) grid_terms_kernel(
   __syncthreads();
   const size_t plane = (size_t)Nu * Nv;
   for (int t = 0; t < NC; ++t) {
-    float2* g = grid_terms + (size_t)(t0 + t) * plane;
     for (int idx = threadIdx.x; idx < SUB; idx += NT) {
       const int r = idx / BV, c = idx - r * BV;
       if (c >= BU) continue;
-      const float2 v = sub[t * SUB + idx];
-      if (v.x == 0.f && v.y == 0.f) continue;
+      const Cell v = sub[t * SUB + idx];
+      if (v.x == 0 && v.y == 0) continue;
       const int gv = tv * TILE + r, gu = tu * TILE + c;
-      if (gu < Nu && gv < Nv) atomicAdd(&g[(size_t)gv * Nu + gu], v);
+      if (gu >= Nu || gv >= Nv) continue;
+      const size_t a = (size_t)(t0 + t) * plane + (size_t)gv * Nu + gu;
+      if constexpr (DET) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&det.gridq[a].x), (unsigned long long)v.x);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&det.gridq[a].y), (unsigned long long)v.y);
+      } else {
+        atomicAdd(&grid_terms[a], v);
+      }
     }
   }
 }
@@ -376,34 +408,44 @@ static int launch_degrid_terms(const Geometry& geo, const VisLayout& lay, int64_
   }
 }
 
-template <int W, int NC>
+template <int W, int NC, bool DET>
 static int launch_grid_terms_nc(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
                                 int t0, const float2* vis, int apply_weights, float2* grid_terms,
-                                cudaStream_t s) {
+                                const DetArgs& det, cudaStream_t s) {
   MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
-  constexpr size_t smem = grid_terms_smem_bytes<W>(NC);
+  constexpr size_t smem = grid_terms_smem_bytes<W>(NC, DET);
   static bool attr = false;
   if (!attr) {
-    FR_CUDA_TRY(cudaFuncSetAttribute(grid_terms_kernel<W, NC>,
+    FR_CUDA_TRY(cudaFuncSetAttribute(grid_terms_kernel<W, NC, DET>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  grid_terms_kernel<W, NC><<<(unsigned)n, TERMS_WARPS * 32, smem, s>>>(
-      lay.items + i0, m, lay.wgt, geo.kern, t0, vis, apply_weights, grid_terms, geo.Nu, geo.Nv);
+  grid_terms_kernel<W, NC, DET><<<(unsigned)n, TERMS_WARPS * 32, smem, s>>>(
+      lay.items + i0, m, lay.wgt, geo.kern, t0, vis, apply_weights, grid_terms, geo.Nu, geo.Nv,
+      det);
   FR_LAUNCHED();
   return FR_OK;
+}
+
+template <int W, bool DET>
+static int launch_grid_terms_det(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
+                                 int t0, int nc, const float2* vis, int apply_weights,
+                                 float2* grid_terms, const DetArgs& det, cudaStream_t s) {
+  switch (nc) {
+    case 1: return launch_grid_terms_nc<W, 1, DET>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, det, s);
+    case 2: return launch_grid_terms_nc<W, 2, DET>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, det, s);
+    case 3: return launch_grid_terms_nc<W, 3, DET>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, det, s);
+    default: return launch_grid_terms_nc<W, 4, DET>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, det, s);
+  }
 }
 
 template <int W>
 static int launch_grid_terms(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n,
                              int t0, int nc, const float2* vis, int apply_weights,
-                             float2* grid_terms, cudaStream_t s) {
-  switch (nc) {
-    case 1: return launch_grid_terms_nc<W, 1>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, s);
-    case 2: return launch_grid_terms_nc<W, 2>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, s);
-    case 3: return launch_grid_terms_nc<W, 3>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, s);
-    default: return launch_grid_terms_nc<W, 4>(geo, lay, i0, n, t0, vis, apply_weights, grid_terms, s);
-  }
+                             float2* grid_terms, const DetArgs& det, cudaStream_t s) {
+  if (det.gridq)
+    return launch_grid_terms_det<W, true>(geo, lay, i0, n, t0, nc, vis, apply_weights, grid_terms, det, s);
+  return launch_grid_terms_det<W, false>(geo, lay, i0, n, t0, nc, vis, apply_weights, grid_terms, det, s);
 }
 
 bool degrid_terms_fits(const Geometry& geo) {
@@ -428,7 +470,7 @@ int degrid_terms(const Geometry& geo, const VisLayout& lay, int g, const CUtenso
 }
 
 int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* vis,
-               int apply_weights, float2* grid_terms, cudaStream_t s) {
+               int apply_weights, float2* grid_terms, const DetArgs& det, cudaStream_t s) {
   if (!lay.presorted) {
     set_error("internal: the multi-term gridder needs origin-ordered work items");
     return FR_EUNSUPPORTED;
@@ -447,7 +489,7 @@ int grid_terms(const Geometry& geo, const VisLayout& lay, int g, const float2* v
     int r;
     auto launch = [&](int W) -> int {
       FR_W_DISPATCH(W, launch_grid_terms, geo, lay, i0, i1 - i0, t0, nc, vis, apply_weights,
-                    grid_terms, s);
+                    grid_terms, det, s);
     };
     if ((r = launch(geo.kern.W))) return r;
   }

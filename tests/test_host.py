@@ -46,6 +46,10 @@ def test_plan_create_rejects_bad_sizes_without_gpu(lib):
     h = ctypes.c_void_p()
     uvw = np.zeros((4, 3))
     f = np.array([1e9])
+    # unknown flag bits
+    r = lib.fr_plan_create(uvw.ctypes.data, 4, f.ctypes.data, 1, None, 64, 64, 1e-5, 1e-5, 1e-5,
+                           64, None, ctypes.byref(h))
+    assert r == -1 and not h.value
     # odd or out-of-range sides (any even side in [16, 4096] is accepted)
     for nx, ny in [(101, 64), (64, 33), (8192, 64), (64, 14)]:
         r = lib.fr_plan_create(uvw.ctypes.data, 4, f.ctypes.data, 1, None, nx, ny, 1e-5, 1e-5,
