@@ -430,6 +430,33 @@ def main():
         del skies, dirt, gb, out, ref_out
         torch.cuda.synchronize()
 
+    # FR_DETERMINISTIC on the same workload: R^dag with fixed-point accumulation (bitwise
+    # reproducible) against the default float atomics
+    det = None
+    if rank == 0:
+        pd = B.Plan(obs.uvw, obs.freqs, obs.nx, obs.ny, obs.pixsize, weights=w32, eps=1e-5,
+                    wterm=obs.wterm, nterm=True, mfs=not obs.per_channel_sky, no_psf=True,
+                    deterministic=True)
+        dd = torch.empty_like(dirty)
+        for _ in range(2):
+            pd.grid(vis, out=dd)
+        torch.cuda.synchronize()
+        tdet = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pd.grid(vis, out=dd)
+            b.record(stream)
+            b.synchronize()
+            tdet += a.elapsed_time(b)
+        ref = plan.grid(vis)
+        det = {"grid_ms": tdet / args.steps, "default_grid_ms": t_grd / args.steps,
+               "rel_diff_vs_default": float(torch.linalg.vector_norm((dd - ref).double()) /
+                                            torch.linalg.vector_norm(ref.double()))}
+        del pd, dd, ref
+        torch.cuda.synchronize()
+
     # an image side that is not a power of two: Tab. 2's field, 3600^2 pixels of 2", with the
     # MeerKAT-like top channel (7,257,600 visibilities, w-stacking) on an 8192^2 grid
     tab2 = None
@@ -556,6 +583,7 @@ def main():
             "plan_s": plan_s,
             "plan": {k: info[k] for k in ("support", "wplanes_total", "work_items", "grid_nu")},
             "minor_major": minor_major, "psf_reduced_padding": reduced, "size_3600": tab2,
+            "deterministic": det,
             "roofline_alu": alu,
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
