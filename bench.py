@@ -80,6 +80,26 @@ def workload_desc(obs, name):
 
 
 # ------------------------------------------------------------------------------ CPU oracle
+def cpu_psf_fft_rate(nx, ny, psf, sky, reps=3):
+    """CPU comparison of the PSF convolution: FP64 scipy.fft on all host cores, the padded
+    2nx x 2ny real transforms of Sec. 3.3.2 (transfer function precomputed, as in the plan).
+    Returns (Mpix/s, cores)."""
+    import scipy.fft as sf
+    cores = os.cpu_count() or 1
+    P = np.asarray(psf, dtype=np.float64)
+    T = sf.rfft2(np.fft.ifftshift(P), workers=cores)
+    s = np.asarray(sky, dtype=np.float64)
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        out = sf.irfft2(T * sf.rfft2(s, s=(2 * nx, 2 * ny), workers=cores),
+                        s=(2 * nx, 2 * ny), workers=cores)[:nx, :ny]
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    del out
+    return nx * ny / best / 1e6, cores
+
+
 def oracle_rate(obs, sky, seconds, seed=0):
     """Time the FP64 direct-sum oracle on a bounded sample; return (Mvis/s, sample text, cores).
 
@@ -411,6 +431,7 @@ def main():
             B.profile_enable(False)
             pms = sum(pc[k][0] for k in ("psf_rows", "psf_cols") if k in pc)
             pby = sum(pc[k][1] for k in ("psf_rows", "psf_cols") if k in pc)
+            npx_all = nb * obs.nsky * obs.nx * obs.ny * args.steps
             if ref_out is None:
                 ref_out = out.clone()
             err = float(torch.linalg.vector_norm((out - ref_out).double()) /
@@ -423,10 +444,41 @@ def main():
                          "psf_passes_GBps": pby / (pms * 1e-3) / 1e9 if pms else None,
                          "psf_passes_frac_of_measured_hbm": (pby / (pms * 1e-3) / 1e9 / peak)
                          if pms else None,
-                         "rel_err_vs_full_padding": err})
+                         "rel_err_vs_full_padding": err,
+                         # bytes the three passes move per sky pixel, against the 16 B/px
+                         # minimum of a PSF convolution (4 in, 4 out, 8 transfer)
+                         "psf_bytes_per_px": pby / npx_all if npx_all else None})
         plan.set_psf_padding(2 * obs.nx, 2 * obs.ny)
+        # library comparison (not the product path): the same batch of PSF convolutions with
+        # cuFFT through torch.fft on the 2nx x 2ny padded grid, against fr_psf_apply
+        Pimg = plan.dirty_psf(want_dirty=False)[1]
+        Tc = torch.fft.rfft2(torch.fft.ifftshift(Pimg, dim=(-2, -1)))
+        outp = torch.empty_like(skies)
+
+        def cufft_apply():
+            F = torch.fft.rfft2(skies, s=(2 * obs.nx, 2 * obs.ny))
+            return torch.fft.irfft2(F * Tc, s=(2 * obs.nx, 2 * obs.ny))[..., :obs.nx, :obs.ny]
+
+        cmp = {}
+        for name, fn in (("fr_psf_apply", lambda: plan.psf_apply(skies, out=outp)),
+                         ("cufft_torch", cufft_apply)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            t = 0.0
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r = fn()
+                b.record(stream)
+                b.synchronize()
+                t += a.elapsed_time(b)
+            cmp[name + "_ms"] = t / args.steps
+        cmp["rel_diff"] = float(torch.linalg.vector_norm((outp - r).double()) /
+                                torch.linalg.vector_norm(r.double()))
         reduced = {"batch": nb, "sky": "point+blob skies, one per batch element",
-                   "rows": rows}
+                   "rows": rows, "psf_apply_vs_cufft": cmp}
         del skies, dirt, gb, out, ref_out
         torch.cuda.synchronize()
 
@@ -567,6 +619,11 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         r, sample, cores = oracle_rate(obs, sky_h.astype(np.float64), args.cpu_seconds)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        psf_np = plan.dirty_psf(want_dirty=False)[1][0].cpu().numpy()
+        pr, pc_ = cpu_psf_fft_rate(obs.nx, obs.ny, psf_np, sky_h[0])
+        cpu["psf_apply_fft"] = {"value": pr, "unit": "Mpix/s", "cores": pc_,
+                                "kind": "FP64 scipy.fft on the padded grid (comparison)",
+                                "sample": f"one {obs.nx}x{obs.ny} sky, best of 3"}
 
     if rank == 0:
         out = {
