@@ -1009,7 +1009,7 @@ static int psf_common(fr_plan_t p, const float* sky, int32_t batch, float* out, 
   Workspace* w;
   FR_TRY(get_ws(p, s, &w));
   const int nimg = batch * p->nsky;
-  const int lx = p->psf_lx, ly = p->psf_ly, nq = ly / 2 + 1;
+  const int lx = p->psf_lx, ly = p->psf_ly;
   const int hp = psf_pitch(ly);
   const size_t hsize = (size_t)nimg * p->geo.nx * hp;  // H, then HT ([nimg][ly/2+1][nx])
   FR_TRY(ws_reserve_h(w, psf_h_need(p, nimg)));
@@ -1376,6 +1376,8 @@ int fr_plan_footprint(fr_plan_t p, size_t* resident_bytes, size_t* workspace_byt
           sizeof(float2);
       if (use_term_grids(g))
         m += 2 * (size_t)g.nterms * (g.Nu + g.nx) * g.Nv * sizeof(float2);
+      if (p->flags & FR_DETERMINISTIC)  // fixed-point grid(s)
+        m += (use_term_grids(g) ? (size_t)g.nterms : 1) * g.Nu * g.Nv * sizeof(longlong2);
     }
     *workspace_bytes = m;
   }
