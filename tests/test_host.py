@@ -78,7 +78,8 @@ def test_plan_create_rejects_bad_sizes_without_gpu(lib):
 # powers of two, the 3 2^k and 5 2^k lengths of the reduced-padding PSF transforms, and odd
 # parts with several factors (radix-3 and radix-5 stages in sequence)
 FFT_LENGTHS = [1 << lg for lg in range(1, 15)] + [3, 5, 6, 10, 48, 80, 96, 1536, 1280, 12288,
-                                                  10240, 45, 225, 7200]
+                                                  10240, 45, 225, 7200, 144, 240, 400, 720,
+                                                  1200, 3600]
 
 
 @pytest.mark.parametrize("n", FFT_LENGTHS)
