@@ -136,8 +136,12 @@ def oracle_rate(obs, sky, seconds, seed=0):
     tau_v, tau_p = measure(nv, npx)
     total = obs.nvis * tau_v + npix * tau_p
     rate = obs.nvis / total / 1e6
+    # direct-DFT terms per second (one term = one visibility-pixel phase and product)
+    terms = {"degrid_terms_per_s": npix / tau_v, "grid_terms_per_s": obs.nvis / tau_p}
     sample = (f"{nv} visibilities (each a {npix}-pixel FP64 direct sum) and {npx} pixels (each a "
-              f"{obs.nvis}-visibility sum) of the workload; rate = N_vis / (N_vis t_vis + N_pix t_pix)")
+              f"{obs.nvis}-visibility sum) of the workload; rate = N_vis / (N_vis t_vis + N_pix t_pix); "
+              f"direct-DFT terms/s: degrid {terms['degrid_terms_per_s']:.3g}, "
+              f"grid {terms['grid_terms_per_s']:.3g}")
     return rate, sample, cores
 
 
