@@ -1,15 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the fast-resolve measurement-operator hot path on synthetic data.
 
-One step = one major cycle plus one minor-cycle likelihood evaluation on the VLA-like
-single-channel workload (1024^2 sky at 0.1", 27 antennas, 8 h at 2 s = 5,054,400 visibilities,
-w-terms, natural weights, eps = 1e-5):
-    R      (degrid the sky to model visibilities)
-    R^dag N^-1 (grid the data visibilities to a residual/dirty image)
-    likelihood + gradient with the PSF convolution on the 2048^2 padded grid.
+Default workload: MeerKAT-like multi-channel, 8 channels of 4096^2 skies at 2" (64 antennas,
+856-1712 MHz, 8 h at 8 s = 58,060,800 visibilities, w-terms, natural weights, eps = 1e-5;
+PSF convolutions on 8192^2 padded grids). One step is
+    R          (degrid the 8 skies to model visibilities)
+    R^dag N^-1 (grid the data visibilities to 8 dirty images)
+    the PSF likelihood and its gradient (8 PSF convolutions on the padded grids).
 Inputs are resident in HBM before timing; L2 is flushed (512 MB write) between timed steps,
-outside the timed events. value = grid+degrid Mvis/s = N_vis / (t_degrid + t_grid), summed
-over all ranks (weak scaling: every rank runs its own copy of the workload, no collective).
+outside the timed events. value = grid+degrid Mvis/s = N_vis / (t_degrid + t_grid) over the
+whole job. With --gpus N the channels are split over the ranks (per-channel skies are
+independent imaging problems, so nothing is exchanged; strong scaling); a single-channel
+workload runs one copy per rank (weak scaling).
+
+Side legs on the same JSON line: the PSF passes against the HBM roofline, the fast-resolve
+likelihood and one exact major cycle, reduced PSF padding, FR_DETERMINISTIC gridding, Tab. 2's
+3600^2 field, a bounded serving run (p50/p99 latency and throughput against plain per-request
+launches), the end-to-end rate through host buffers, and the FP64 oracle on the host cores.
 
 --impl reference times the FP64 CPU oracle (direct sums) on the host cores on a bounded
 sample of the same workload and reports the same metric.
@@ -42,7 +49,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fastresolve", choices=["fastresolve", "reference"])
-    ap.add_argument("--workload", default="vla", choices=["vla", "small", "meerkat", "meerkat1"])
+    ap.add_argument("--workload", default="meerkat", choices=["meerkat", "vla", "small", "meerkat1"])
+    ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving leg")
+    ap.add_argument("--serving-jobs", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sizes", action="store_true",
                     help="skip the 3600^2 (non-power-of-two) side measurement")
@@ -276,7 +285,18 @@ def main():
     build.build()
     B.load()
 
-    obs = synth.observation(args.workload)
+    from paper_2406_09144_gb300 import shard
+    obs_full = synth.observation(args.workload)
+    # per-channel skies split by channel over the ranks (no exchange); a single-channel
+    # workload runs one copy per rank
+    sharded = ws > 1 and obs_full.per_channel_sky and obs_full.nchan >= ws
+    if sharded:
+        c0, c1 = shard.channel_shard(obs_full.nchan, ws, rank)
+        obs = shard.channel_slice(obs_full, c0, c1)
+        job_vis, job_pix = obs_full.nvis, obs_full.nsky * obs_full.nx * obs_full.ny
+    else:
+        obs = obs_full
+        job_vis, job_pix = ws * obs.nvis, ws * obs.nsky * obs.nx * obs.ny
     w32 = obs.weights.astype(np.float32)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -343,8 +363,8 @@ def main():
     if ws > 1:
         dist.all_reduce(times, op=dist.ReduceOp.MAX)
     t_dg, t_psf, t_step = (float(x) for x in times.cpu())
-    value = ws * obs.nvis * args.steps / (t_dg * 1e-3) / 1e6
-    psf_mpix = ws * obs.nsky * obs.nx * obs.ny * args.steps / (t_psf * 1e-3) / 1e6
+    value = job_vis * args.steps / (t_dg * 1e-3) / 1e6
+    psf_mpix = job_pix * args.steps / (t_psf * 1e-3) / 1e6
 
     # roofline of the dominant kernel class
     dom = max(cats, key=lambda k: cats[k][0])
@@ -357,6 +377,16 @@ def main():
                 "algorithmic_bytes_per_launch": dby / max(dn, 1),
                 "avg_launch_ms": dms / max(dn, 1), "launches": int(dn),
                 "share_of_step": dms / max(t_step, 1e-9)}
+    # the PSF path (P1/P2/P3 of the likelihood call in the step) against the same HBM peak,
+    # with the bytes it moves per sky pixel against the 16 B/px minimum of a PSF convolution
+    psf_ms = sum(cats[k][0] for k in ("psf_rows", "psf_cols") if k in cats)
+    psf_by = sum(cats[k][1] for k in ("psf_rows", "psf_cols") if k in cats)
+    psf_ach = psf_by / (psf_ms * 1e-3) / 1e9 if psf_ms else 0.0
+    roofline_psf = {"bound": "hbm", "kernel": "PSF passes P1, P2, P3 (likelihood and gradient)",
+                    "achieved": psf_ach, "peak": peak, "peak_source": f"{peak_kind} hbm_gbs",
+                    "unit": "GB/s", "frac": psf_ach / peak,
+                    "bytes_per_px": psf_by / (obs.nsky * obs.nx * obs.ny * args.steps),
+                    "min_bytes_per_px": 16.0, "passes_ms_per_step": psf_ms / args.steps}
     # the visibility kernels are bound by FP32 issue, not HBM: their multiply-add rate against
     # the FP32 peak (152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s, nominal unit counts
     # and the maximum SM clock). Flops: 4 per footprint cell (a complex times a real weight,
@@ -612,12 +642,30 @@ def main():
         if ws > 1:
             dist.all_reduce(tt_t, op=dist.ReduceOp.MAX)
         tt = float(tt_t.item())
-        e2e = {"value": ws * obs.nvis * args.steps / (tt * 1e-3) / 1e6, "unit": UNIT,
+        e2e = {"value": job_vis * args.steps / (tt * 1e-3) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(sky_h.nbytes + vis_h.nbytes),
                "d2h_bytes_per_step": int(model.numel() * 8 + dirty.numel() * 4),
                "path": "pinned host sky + visibilities -> fr_degrid, fr_grid -> pinned host model "
                        "visibilities + dirty image; the visibility upload and the model download "
                        "overlap the kernels on a second stream"}
+
+    # serving (continuous batching): a bounded mix of imaging jobs through the server against
+    # plain per-request launches, closed-loop throughput and p50/p99 latency under Poisson
+    # arrivals at 80 % of the per-request capacity
+    serving = None
+    if rank == 0 and not args.no_serving:
+        from paper_2406_09144_gb300 import serve
+        del model, grad, resid
+        torch.cuda.empty_cache()
+        sv = serve.bench(args.serving_jobs, sizes=(256, 512, 1024, 2048), nvis_range=(1e4, 5e6))
+        pa = sv["server_poisson"]
+        serving = {"workload": sv["workload"], "throughput_gain": sv["throughput_gain"],
+                   "server_jobs_per_s": sv["server_closed"]["req_per_s"],
+                   "per_request_jobs_per_s": sv["sequential"]["req_per_s"],
+                   "p50_ms": pa.get("p50_ms"), "p99_ms": pa.get("p99_ms"),
+                   "arrival_rate_per_s": sv["arrival_rate_per_s"],
+                   "max_rel_diff_alone_vs_mix": sv["max_rel_diff_alone_vs_mix"], "detail": sv}
+        torch.cuda.synchronize()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -633,8 +681,8 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded VLA-like array, Earth-rotation tracks, point+blob sky, "
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded antenna layout, Earth-rotation tracks, point+blob skies, "
                     "Gaussian visibilities)",
             "config": workload_desc(obs, args.workload),
             "psf_apply_mpix_s": psf_mpix,
@@ -646,7 +694,8 @@ def main():
             "minor_major": minor_major, "psf_reduced_padding": reduced, "size_3600": tab2,
             "deterministic": det,
             "roofline_alu": alu,
-            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "roofline_psf": roofline_psf, "serving": serving,
+            "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(out), flush=True)

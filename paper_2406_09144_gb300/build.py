@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfastresolve.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "gridder.cu", "wterms.cu", "fft_grid.cu", "fft_psf.cu", "noise.cu", "noise_extra.cu",
+SOURCES = ["api.cu", "gridder.cu", "wterms.cu", "fft_grid.cu", "fft_stack.cu", "fft_psf.cu", "noise.cu",
+           "noise_extra.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -246,6 +246,7 @@ static void free_ws(Workspace* w) {
   cudaFree(w->grid);
   cudaFree(w->grid_terms);
   cudaFree(w->grid_terms_g);
+  cudaFree(w->b1_stack);
   cudaFree(w->b1_terms);
   cudaFree(w->b1g_terms);
   cudaFree(w->img_a);
@@ -363,6 +364,57 @@ static int ws_reserve_det(Workspace* w, size_t n, cudaStream_t s) {
   return FR_OK;
 }
 
+// w-stacking over the planes' occupied tiles (grids of whole tiles)
+static bool use_stack(const fr_plan* p) {
+  return p->lay.occ_ok && p->geo.wterm && !p->geo.taylor;
+}
+
+// STACK_K compact half planes, each holding the most occupied tile rows of any plane
+static int ws_reserve_stack(const fr_plan* p, Workspace* w) {
+  const size_t n = std::max<size_t>((size_t)p->lay.occ_max_rows * TILE * p->geo.nx, 1);
+  if (w->b1_stack && w->b1_stack_n >= n) return FR_OK;
+  if (w->b1_stack) {
+    cudaFree(w->b1_stack);
+    w->bytes -= STACK_K * w->b1_stack_n * sizeof(float2);
+    w->b1_stack = nullptr;
+    w->b1_stack_n = 0;
+  }
+  FR_TRY(ws_alloc(&w->b1_stack, STACK_K * n, w));
+  w->b1_stack_n = n;
+  return FR_OK;
+}
+
+// the planes of group g that hold visibilities, ascending
+static std::vector<int> busy_planes(const Geometry& geo, const VisLayout& lay, int g) {
+  std::vector<int> ps;
+  const int P = geo.wterm ? lay.planes[g] : 1;
+  for (int p = 0; p < P; ++p) {
+    const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);
+    if (lay.plane_items[q + 1] > lay.plane_items[q]) ps.push_back(p);
+  }
+  return ps;
+}
+
+// one batch of up to STACK_K planes of the stacked passes
+struct StackBatch {
+  int nk = 0;
+  long long k64[STACK_K] = {0};
+  PlaneOcc occ[STACK_K];
+  float2* buf[STACK_K] = {nullptr};
+};
+static StackBatch stack_batch(const fr_plan* pl, const Workspace* w, int g,
+                              const std::vector<int>& ps, size_t b) {
+  StackBatch sb;
+  sb.nk = (int)std::min<size_t>(STACK_K, ps.size() - b);
+  for (int k = 0; k < sb.nk; ++k) {
+    const int p = ps[b + k];
+    sb.k64[k] = plane_k64(pl->geo, plane_w(pl->geo, pl->lay, g, p));
+    sb.occ[k] = plane_occ(pl->lay, pl->lay.plane_base[g] + p);
+    sb.buf[k] = w->b1_stack + (size_t)k * w->b1_stack_n;
+  }
+  return sb;
+}
+
 // the small-w expansion keeps all its term grids resident when they fit
 static bool use_term_grids(const Geometry& g) {
   return g.wterm && g.taylor && degrid_terms_fits(g) &&
@@ -453,6 +505,24 @@ static int run_degrid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Wo
       FR_TRY(degrid_terms(geo, lay, g, w->tmap_terms, vis, pl->status, s));
       continue;
     }
+    if (use_stack(pl)) {
+      // STACK_K planes' half planes from one pass over the image, then per plane the column
+      // pass into its occupied tiles and the interpolation
+      FR_TRY(ws_reserve_stack(pl, w));
+      const std::vector<int> ps = busy_planes(geo, lay, g);
+      for (size_t b = 0; b < ps.size(); b += STACK_K) {
+        const StackBatch sb = stack_batch(pl, w, g, ps, b);
+        const PlaneArgs a = plane_args(geo, lay, g, ps[b]);
+        FR_TRY(degrid_d1_stack(a, sb.nk, sb.k64, sb.occ, sky + g * img, sb.buf,
+                               twiddles_of(pl, geo.Nv), s));
+        for (int k = 0; k < sb.nk; ++k) {
+          FR_TRY(degrid_d2_sparse(a, sb.occ[k], sb.buf[k], w->grid, twiddles_of(pl, geo.Nu), s));
+          w->grid_zero = false;
+          FR_TRY(degrid_plane(geo, lay, g, ps[b + k], w->tmap, w->vbuf, vis, pl->status, s));
+        }
+      }
+      continue;
+    }
     for (int p = 0; p < P; ++p) {
       const int q = lay.plane_base[g] + (geo.taylor ? 0 : p);
       if (lay.plane_items[q + 1] <= lay.plane_items[q]) continue;
@@ -525,6 +595,26 @@ static int run_grid(fr_plan* pl, const Geometry& geo, const VisLayout& lay, Work
     if (!*grid_zero)
       FR_CUDA_TRY(cudaMemsetAsync(grid, 0, plane * sizeof(float2), s));
     *grid_zero = true;
+  }
+  if (w && !det && use_stack(pl)) {
+    // per plane the gridder and the column pass out of its occupied tiles; STACK_K planes'
+    // half planes then summed into the image by one row pass
+    FR_TRY(ws_reserve_stack(pl, w));
+    for (int g = 0; g < lay.ngroups; ++g) {
+      const std::vector<int> ps = busy_planes(geo, lay, g);
+      if (ps.empty()) FR_CUDA_TRY(cudaMemsetAsync(dirty + g * img, 0, img * sizeof(float), s));
+      for (size_t b = 0; b < ps.size(); b += STACK_K) {
+        const StackBatch sb = stack_batch(pl, w, g, ps, b);
+        const PlaneArgs a = plane_args(geo, lay, g, ps[b]);
+        for (int k = 0; k < sb.nk; ++k) {
+          FR_TRY(grid_plane(geo, lay, g, ps[b + k], ybuf, grid, d, s));
+          FR_TRY(grid_g1_sparse(a, sb.occ[k], grid, sb.buf[k], twiddles_of(pl, geo.Nu), s));
+        }
+        FR_TRY(grid_g2_stack(a, sb.nk, sb.k64, sb.occ, sb.buf, dirty + g * img, b > 0 ? 1 : 0,
+                             twiddles_of(pl, geo.Nv), s));
+      }
+    }
+    return FR_OK;
   }
   for (int g = 0; g < lay.ngroups; ++g) {
     const int P = geo.wterm ? lay.planes[g] : 1;
@@ -1378,6 +1468,9 @@ int fr_plan_footprint(fr_plan_t p, size_t* resident_bytes, size_t* workspace_byt
         m += 2 * (size_t)g.nterms * (g.Nu + g.nx) * g.Nv * sizeof(float2);
       if (p->flags & FR_DETERMINISTIC)  // fixed-point grid(s)
         m += (use_term_grids(g) ? (size_t)g.nterms : 1) * g.Nu * g.Nv * sizeof(longlong2);
+      if (use_stack(p))  // compact half planes of the stacked w-plane passes
+        m += (size_t)STACK_K * std::max<size_t>((size_t)p->lay.occ_max_rows * TILE * g.nx, 1) *
+             sizeof(float2);
     }
     *workspace_bytes = m;
   }

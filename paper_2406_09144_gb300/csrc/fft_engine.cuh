@@ -128,7 +128,8 @@ __device__ __forceinline__ const float2* cluster_map(const float2* p, uint32_t r
 }
 
 // Generic pass. blockIdx.x selects B consecutive sequences, blockIdx.y an image (ops that batch
-// images use it). Op provides:
+// images use it); ops with SEQ_Y swap the two, so that the CTAs of one sequence block for all
+// images run next to each other and share the block's input through L2. Op provides:
 //   static constexpr bool TRANSPOSED   store mapping (see above)
 //   static constexpr bool TWO          second transform (DIR2) after mid()
 //   int nseq() const, int nout() const      (host and device)
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT,
   constexpr int PER = B * L / NT;
   extern __shared__ float2 smem[];
   const int nseq = op.nseq();
-  const int seq0 = blockIdx.x * B;
+  const int seq0 = (Op::SEQ_Y ? blockIdx.y : blockIdx.x) * B;
   float2 r[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT,
     smem[(idx / L) * LP + spad(idx % L)] = r[k];
   }
   __syncthreads();
-  op.after_load(seq0, min(B, nseq - seq0));
+  if (seq0 < nseq) op.after_load(seq0, min(B, nseq - seq0));
   fft_stages<L, 0, DIR>(smem, tw);
   if constexpr (Op::TWO) {
     op.template mid<B, NT, L, LP>(smem, seq0);
@@ -225,21 +226,112 @@ int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
   if constexpr (CL > 1) {
     // whole clusters: the CTAs past the last sequence transform zeros and store nothing
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((nblk + CL - 1) / CL * CL, nimg);
+    const unsigned nb = (nblk + CL - 1) / CL * CL;
+    cfg.gridDim = Op::SEQ_Y ? dim3(nimg, nb) : dim3(nb, nimg);
     cfg.blockDim = dim3(C::NT);
     cfg.dynamicSmemBytes = C::SMEM;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CL;
-    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.x = Op::SEQ_Y ? 1 : CL;
+    at[0].val.clusterDim.y = Op::SEQ_Y ? CL : 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     FR_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, op, tw));
   } else {
-    kern<<<dim3(nblk, nimg), C::NT, C::SMEM, s>>>(op, tw);
+    kern<<<Op::SEQ_Y ? dim3(nimg, nblk) : dim3(nblk, nimg), C::NT, C::SMEM, s>>>(op, tw);
   }
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
+// Multi-input pass: op.ntrans() transforms per sequence, each of its own input, whose outputs
+// are combined per output element in registers and written once (row-major mapping;
+// blockIdx.x selects B sequences). The next transform's loads are issued before the current
+// transform's outputs are combined, so they are in flight meanwhile.
+//   float2 load(int t, int seq, int i)            element i of transform t's input
+//   Ctx ctx(int seq, int o)                       per-output context, read once
+//   float term(int t, const Ctx&, int o, SeqView v)   transform t's contribution to output o
+//   void store(int seq, int o, const Ctx&, float acc)
+// Outputs per sequence nout() <= L / 2 (each thread owns at most PER / 2 of them).
+template <int LEN, int DIR, class Op>
+__global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB)
+    fft_pass_accum_kernel(Op op, const float2* __restrict__ tw) {
+  using C = FftCfg<LEN>;
+  constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
+  constexpr int PER = B * L / NT;
+  constexpr int MAXO = PER / 2;
+  extern __shared__ float2 smem[];
+  const int nseq = op.nseq(), nout = op.nout(), ntr = op.ntrans();
+  const int seq0 = blockIdx.x * B;
+  typename Op::Ctx ctx[MAXO];
+  float acc[MAXO];
+#pragma unroll
+  for (int m = 0; m < MAXO; ++m) {
+    const int idx = threadIdx.x + m * NT;
+    acc[m] = 0.f;
+    if (idx < B * nout) {
+      const int b = idx / nout, o = idx % nout;
+      if (seq0 + b < nseq) ctx[m] = op.ctx(seq0 + b, o);
+    }
+  }
+  float2 r[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + k * NT;
+    const int b = idx / L, i = idx % L;
+    r[k] = (seq0 + b < nseq && ntr > 0) ? op.load(0, seq0 + b, i) : make_float2(0.f, 0.f);
+  }
+  for (int t = 0; t < ntr; ++t) {
+    if (t > 0) __syncthreads();  // the previous transform's outputs have been read
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = threadIdx.x + k * NT;
+      smem[(idx / L) * LP + spad(idx % L)] = r[k];
+    }
+    __syncthreads();
+    fft_stages<L, 0, DIR>(smem, tw);
+    if (t + 1 < ntr) {
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int idx = threadIdx.x + k * NT;
+        const int b = idx / L, i = idx % L;
+        r[k] = (seq0 + b < nseq) ? op.load(t + 1, seq0 + b, i) : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < MAXO; ++m) {
+      const int idx = threadIdx.x + m * NT;
+      if (idx < B * nout) {
+        const int b = idx / nout, o = idx % nout;
+        if (seq0 + b < nseq) acc[m] += op.term(t, ctx[m], o, SeqView{smem + b * LP});
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MAXO; ++m) {
+    const int idx = threadIdx.x + m * NT;
+    if (idx < B * nout) {
+      const int b = idx / nout, o = idx % nout;
+      if (seq0 + b < nseq) op.store(seq0 + b, o, ctx[m], acc[m]);
+    }
+  }
+}
+
+template <int LEN, int DIR, class Op>
+int launch_pass_accum(const Op& op, const float2* tw, cudaStream_t s) {
+  using C = FftCfg<LEN>;
+  const int nblk = (op.nseq() + C::B - 1) / C::B;
+  if (nblk == 0) return FR_OK;
+  auto kern = fft_pass_accum_kernel<LEN, DIR, Op>;
+  static bool attr = false;
+  if (!attr) {
+    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    attr = true;
+  }
+  kern<<<nblk, C::NT, C::SMEM, s>>>(op, tw);
   FR_LAUNCHED();
   return FR_OK;
 }
@@ -322,6 +414,7 @@ struct OpBase {
   static constexpr bool TRANSPOSED = false;
   static constexpr bool TWO = false;
   static constexpr bool GROUP = false;
+  static constexpr bool SEQ_Y = false;
   __device__ void after_load(int, int) const {}
   template <int B, int NT, int L, int LP>
   __device__ void mid(float2*, int) const {}

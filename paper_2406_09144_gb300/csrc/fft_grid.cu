@@ -17,19 +17,10 @@
 //      zeroed once loaded (the grid stays zero between calls);
 //   G2 (B1 rows, along v): inverse FFT, keep ny outputs, Re(Z conj(c_p(j))) accumulated into the
 //      dirty image.
-#include "fft_engine.cuh"
+#include "fft_grid_common.cuh"
 #include "vis_common.cuh"
 
 namespace fr {
-
-__device__ __forceinline__ void plane_phase(int32_t tq, long long k64, float* c, float* s) {
-  // frac(w_p (t - t_c)) from a wrapping 64-bit fixed-point product; the top 32 bits are the
-  // signed fraction of a cycle in [-1/2, 1/2).
-  unsigned long long prod = (unsigned long long)(long long)tq * (unsigned long long)k64;
-  int hi = (int)(unsigned)(prod >> 32);
-  float f = (float)hi * 2.3283064365386963e-10f;
-  sincospif(2.f * f, s, c);
-}
 
 // 1 / k! for the expansion terms
 __constant__ float c_inv_fact[MAX_TERMS] = {
@@ -51,9 +42,6 @@ __device__ __forceinline__ float taylor_factor(int32_t tq, int n, float inv_fact
   for (int i = 0; i < n; ++i) p *= tau;
   return p;
 }
-
-// index i in [-N, N) taken modulo the grid length N (any even N, not only powers of two)
-__device__ __forceinline__ int wrap(int i, int N) { return i < 0 ? i + N : i; }
 
 struct D1Op : OpBase {
   static constexpr bool TRANSPOSED = true;
@@ -351,6 +339,7 @@ template <int LEN>
 static int run_g2a(const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { return launch_pass<LEN, 1, 1>(op, nt, tw, s); }
 static int g2a(int len, const G2TermsAddOp& op, int nt, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_g2a, op, nt, tw, s); }
 static int g1t(int len, const G1Op& op, int nt, const float2* tw, cudaStream_t s) { FR_LEN_DISPATCH(len, run_g1t, op, nt, tw, s); }
+
 
 
 int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* grid,

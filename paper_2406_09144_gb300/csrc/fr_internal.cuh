@@ -153,6 +153,17 @@ struct VisLayout {
   uint32_t* perm = nullptr;  // user index (row * nchan + chan) | conj flag << 31
   float* wgt = nullptr;
   int4* items = nullptr;     // {vis_begin, vis_count, tu << 16 | tv, 0}
+  // w-stacking: tiles each plane's footprints reach, per plane q (index of plane_items):
+  // occ_bits [q][ntv][occ_ntw] bitmap, occ_comp [q][ntv] compact tile-row index or -1,
+  // occ_rows the occupied tile rows of every plane (ascending) from occ_row_off[q]
+  bool occ_ok = false;
+  int occ_ntw = 0;
+  uint32_t* occ_bits = nullptr;
+  int* occ_comp = nullptr;
+  int* occ_rows = nullptr;
+  std::vector<int64_t> occ_row_off;  // [nq + 1]
+  std::vector<int64_t> occ_tiles;    // [nq] occupied tiles
+  int occ_max_rows = 0;              // most occupied tile rows of any plane
   bool presorted = false;    // each item's visibilities ordered by footprint origin
   int64_t nitems = 0;
   size_t bytes = 0;
@@ -182,6 +193,8 @@ struct Workspace {
   float* img_a = nullptr;  // [n] image scratch of the fast-resolve likelihood
   float* img_b = nullptr;
   size_t img_n = 0;
+  float2* b1_stack = nullptr;   // STACK_K compact half planes of the w-stacking passes
+  size_t b1_stack_n = 0;        // complex values per compact half plane
   float2* b1_terms = nullptr;   // [nterms][band v][nx] degridding half planes
   float2* b1g_terms = nullptr;  // [nterms][nx][Nv] gridding half planes (zero off-band)
   // FR_DETERMINISTIC: fixed-point grid(s) (kept zero), the call's largest contribution (float
@@ -239,6 +252,17 @@ struct DetArgs {
   double* inv = nullptr;  // 1 / scale, written before the post-pass reads the fixed-point grid
   long long n = 0;
 };
+// Occupied tiles of one w-plane (VisLayout occ_*): the tile rows, the compact index of every
+// tile row (-1 if empty), the bitmap, and the cells of the occupied tiles.
+constexpr int STACK_K = 8;  // w-planes per launch of the stacked row passes
+struct PlaneOcc {
+  const int* rows = nullptr;
+  const int* comp = nullptr;
+  const uint32_t* bits = nullptr;
+  int nrows = 0, ntw = 0;
+  double ncells = 0.0;
+};
+PlaneOcc plane_occ(const VisLayout& lay, int q);
 struct PlaneArgs {
   // geometry
   int nx, ny, Nu, Nv;
@@ -265,6 +289,19 @@ int degrid_prepass(const PlaneArgs& a, const float* sky, float2* b1, float2* gri
                    const float2* twv, const float2* twu, cudaStream_t s);
 int grid_postpass(const PlaneArgs& a, float2* grid, float2* b1, float* dirty, int accumulate,
                   const float2* twu, const float2* twv, cudaStream_t s);
+// w-stacking over occupied tiles (fft_grid.cu): D1 for nk <= STACK_K planes (plane k's phase
+// k64[k], compact half plane b1t[k], [occ[k].nrows * TILE][nx]); D2 of one plane into its
+// occupied tiles of `grid`; G1 of one plane from its occupied tiles (zeroed) into the compact
+// half plane b1 [nx][nrows * TILE]; G2 summing nk planes' half planes into `dirty`
+int degrid_d1_stack(const PlaneArgs& a, int nk, const long long* k64, const PlaneOcc* occ,
+                    const float* sky, float2* const* b1t, const float2* twv, cudaStream_t s);
+int degrid_d2_sparse(const PlaneArgs& a, const PlaneOcc& occ, const float2* b1t, float2* grid,
+                     const float2* twu, cudaStream_t s);
+int grid_g1_sparse(const PlaneArgs& a, const PlaneOcc& occ, float2* grid, float2* b1,
+                   const float2* twu, cudaStream_t s);
+int grid_g2_stack(const PlaneArgs& a, int nk, const long long* k64, const PlaneOcc* occ,
+                  float2* const* b1, float* dirty, int accumulate, const float2* twv,
+                  cudaStream_t s);
 // the same from fixed-point grids (FR_DETERMINISTIC); the terms are added to the image one
 // after the other instead of with atomics
 int grid_postpass_q(const PlaneArgs& a, const DetArgs& det, float2* b1, float* dirty,

@@ -387,7 +387,8 @@ static int dalloc(T** p, size_t n, size_t* acc, cudaStream_t async = nullptr) {
 
 void free_layout(VisLayout* lay) {
   for (void* q : {(void*)lay->cell, (void*)lay->du, (void*)lay->dv, (void*)lay->dw, (void*)lay->ph,
-                  (void*)lay->perm, (void*)lay->wgt, (void*)lay->items}) {
+                  (void*)lay->perm, (void*)lay->wgt, (void*)lay->items, (void*)lay->occ_bits,
+                  (void*)lay->occ_comp, (void*)lay->occ_rows}) {
     if (!q) continue;
     if (lay->async)
       cudaFreeAsync(q, lay->async);
@@ -398,6 +399,97 @@ void free_layout(VisLayout* lay) {
   lay->du = lay->dv = lay->dw = lay->wgt = nullptr;
   lay->ph = lay->perm = nullptr;
   lay->items = nullptr;
+  lay->occ_bits = nullptr;
+  lay->occ_comp = nullptr;
+  lay->occ_rows = nullptr;
+  lay->occ_ok = false;
+}
+
+PlaneOcc plane_occ(const VisLayout& lay, int q) {
+  PlaneOcc o;
+  if (!lay.occ_ok) return o;
+  o.rows = lay.occ_rows + lay.occ_row_off[q];
+  o.comp = lay.occ_comp + (size_t)q * lay.ntv;
+  o.bits = lay.occ_bits + (size_t)q * lay.ntv * lay.occ_ntw;
+  o.nrows = (int)(lay.occ_row_off[q + 1] - lay.occ_row_off[q]);
+  o.ntw = lay.occ_ntw;
+  o.ncells = (double)lay.occ_tiles[q] * TILE * TILE;
+  return o;
+}
+
+// w-stacking: the tiles plane q's footprints reach. A work item of tile (tu, tv) holds
+// footprints whose origin lies in that tile; a footprint of W <= TILE cells reaches at most the
+// next tile in u and in v, so the item marks the 2 x 2 tiles from its own (clipped to the grid).
+__global__ void occupancy_kernel(const int4* __restrict__ items, int64_t nitems,
+                                 const int* __restrict__ pitems, int nplanes, int ntu, int ntv,
+                                 int ntw, uint32_t* bits) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nitems;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nplanes - 1;  // plane q: pitems[q] <= i < pitems[q + 1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pitems[mid] <= i)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int4 it = items[i];
+    if (it.y <= 0) continue;
+    const int tu = it.z >> 16, tv = it.z & 0xffff;
+    uint32_t* b = bits + (size_t)lo * ntv * ntw;
+    for (int dv = 0; dv < 2; ++dv)
+      for (int du = 0; du < 2; ++du) {
+        const int u = tu + du, v = tv + dv;
+        if (u < ntu && v < ntv) atomicOr(&b[v * ntw + (u >> 5)], 1u << (u & 31));
+      }
+  }
+}
+
+static int build_occupancy(VisLayout* lay, const int* d_pitems, int nplanes, size_t* acc,
+                           cudaStream_t s) {
+  const int ntw = (lay->ntu + 31) / 32;
+  const size_t nbits = (size_t)nplanes * lay->ntv * ntw;
+  lay->occ_ntw = ntw;
+  FR_TRY(dalloc(&lay->occ_bits, nbits, acc, lay->async));
+  FR_CUDA_TRY(cudaMemsetAsync(lay->occ_bits, 0, nbits * sizeof(uint32_t), s));
+  if (lay->nitems > 0) {
+    occupancy_kernel<<<grid1d(lay->nitems), 256, 0, s>>>(lay->items, lay->nitems, d_pitems,
+                                                          nplanes, lay->ntu, lay->ntv, ntw,
+                                                          lay->occ_bits);
+    FR_LAUNCHED();
+  }
+  std::vector<uint32_t> hb(nbits);
+  FR_CUDA_TRY(cudaMemcpyAsync(hb.data(), lay->occ_bits, nbits * sizeof(uint32_t),
+                              cudaMemcpyDeviceToHost, s));
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int> comp((size_t)nplanes * lay->ntv, -1), rows;
+  lay->occ_row_off.assign(nplanes + 1, 0);
+  lay->occ_tiles.assign(nplanes, 0);
+  lay->occ_max_rows = 0;
+  for (int q = 0; q < nplanes; ++q) {
+    int n = 0;
+    for (int v = 0; v < lay->ntv; ++v) {
+      int64_t c = 0;
+      for (int w = 0; w < ntw; ++w) c += __builtin_popcount(hb[((size_t)q * lay->ntv + v) * ntw + w]);
+      if (c == 0) continue;
+      comp[(size_t)q * lay->ntv + v] = n++;
+      rows.push_back(v);
+      lay->occ_tiles[q] += c;
+    }
+    lay->occ_row_off[q + 1] = (int64_t)rows.size();
+    lay->occ_max_rows = std::max(lay->occ_max_rows, n);
+  }
+  FR_TRY(dalloc(&lay->occ_comp, comp.size(), acc, lay->async));
+  FR_TRY(dalloc(&lay->occ_rows, std::max<size_t>(rows.size(), 1), acc, lay->async));
+  FR_CUDA_TRY(cudaMemcpyAsync(lay->occ_comp, comp.data(), comp.size() * sizeof(int),
+                              cudaMemcpyHostToDevice, s));
+  if (!rows.empty())
+    FR_CUDA_TRY(cudaMemcpyAsync(lay->occ_rows, rows.data(), rows.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, s));
+  // the host vectors are read by the copies above: finish them before they go out of scope
+  FR_CUDA_TRY(cudaStreamSynchronize(s));
+  lay->occ_ok = true;
+  return FR_OK;
 }
 
 namespace {
@@ -687,6 +779,9 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
       lay->bu1 = lay->bv1 = -1;
     }
   }
+  // w-stacking on grids of whole tiles: the occupied tiles of every plane
+  if (stack && geo.Nu % TILE == 0 && geo.Nv % TILE == 0)
+    FR_TRY(build_occupancy(lay, d_pitems, nq - 1, &acc, s));
   lay->plane_visits.assign(nq - 1, 0);
   if (nq > 1 && lay->nitems > 0) {
     long long* d_visits;

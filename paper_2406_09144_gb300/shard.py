@@ -72,3 +72,15 @@ def max_over_ranks(value: float, world: int, group=None) -> float:
         t = t.cuda()
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return float(t.item())
+
+
+def channel_slice(obs, start: int, stop: int):
+    """The observation restricted to channels [start, stop): the rows and uvw stay, the
+    frequencies, weights and noise levels keep only those channels (per-channel skies, so the
+    slice is a complete imaging problem of its own)."""
+    import dataclasses
+    if not 0 <= start < stop <= len(obs.freqs):
+        raise ValueError(f"channel range [{start}, {stop}) outside 0..{len(obs.freqs)}")
+    return dataclasses.replace(obs, freqs=np.asarray(obs.freqs)[start:stop],
+                               weights=np.ascontiguousarray(np.asarray(obs.weights)[:, start:stop]),
+                               sigma=np.ascontiguousarray(np.asarray(obs.sigma)[:, start:stop]))
