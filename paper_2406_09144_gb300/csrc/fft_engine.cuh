@@ -86,6 +86,63 @@ __device__ __forceinline__ void fft_stages(float2* s, const float2* __restrict__
   }
 }
 
+// The first stage of the power-of-two lengths whose schedule opens with radix 16 runs on the
+// values a thread loaded itself: thread t takes sequence b = t / (L/16) and task j = t % (L/16),
+// loads x[j + k L/16] (k < 16, consecutive threads on consecutive elements), transforms them
+// in registers and writes the stage's outputs, so that stage costs no shared-memory round trip
+// and no barrier. Other lengths load idx = t + k NT (sequence idx / L, element idx % L) and run
+// every stage in shared memory.
+template <int L>
+constexpr bool fuse_first() {
+  return FftCfg<L>::POW2 && fft_radix(L, 0) == 16 && FftCfg<L>::B * L / FftCfg<L>::NT == 16;
+}
+
+// sequence (within the CTA) and element of the k-th value a thread loads
+template <int L>
+__device__ __forceinline__ void load_pos(int k, int* b, int* i) {
+  if constexpr (fuse_first<L>()) {
+    constexpr int Q = L / 16;
+    *b = threadIdx.x / Q;
+    *i = threadIdx.x % Q + k * Q;
+  } else {
+    const int idx = threadIdx.x + k * FftCfg<L>::NT;
+    *b = idx / L;
+    *i = idx % L;
+  }
+}
+
+// The transform of the loaded values r (load_pos order) into shared memory, in natural order;
+// `landed` runs once every thread's values are in shared memory (before the remaining stages).
+template <int L, int DIR, class F>
+__device__ __forceinline__ void fft_from_regs(float2* s, float2* r, const float2* __restrict__ tw,
+                                              F landed) {
+  using C = FftCfg<L>;
+  if constexpr (fuse_first<L>()) {
+    constexpr int Q = L / 16;
+    const int b = threadIdx.x / Q, j = threadIdx.x % Q;
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = r[k];
+    dft16<DIR>(v);
+    float2* dst = s + b * C::LP;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) dst[spad(16 * j + k)] = v[k];
+    __syncthreads();
+    landed();
+    fft_stages<L, 1, DIR>(s, tw);
+  } else {
+    constexpr int PER = C::B * L / C::NT;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = threadIdx.x + k * C::NT;
+      s[(idx / L) * C::LP + spad(idx % L)] = r[k];
+    }
+    __syncthreads();
+    landed();
+    fft_stages<L, 0, DIR>(s, tw);
+  }
+}
+
 // Read-only view of one sequence in shared memory.
 struct SeqView {
   const float2* p;
@@ -151,18 +208,13 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT,
   float2 r[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    const int idx = threadIdx.x + k * NT;
-    const int b = idx / L, i = idx % L;
+    int b, i;
+    load_pos<L>(k, &b, &i);
     r[k] = (seq0 + b < nseq) ? op.load(seq0 + b, i) : make_float2(0.f, 0.f);
   }
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = threadIdx.x + k * NT;
-    smem[(idx / L) * LP + spad(idx % L)] = r[k];
-  }
-  __syncthreads();
-  if (seq0 < nseq) op.after_load(seq0, min(B, nseq - seq0));
-  fft_stages<L, 0, DIR>(smem, tw);
+  fft_from_regs<L, DIR>(smem, r, tw, [&] {
+    if (seq0 < nseq) op.after_load(seq0, min(B, nseq - seq0));
+  });
   if constexpr (Op::TWO) {
     op.template mid<B, NT, L, LP>(smem, seq0);
     __syncthreads();
@@ -248,12 +300,11 @@ int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
 
 // Multi-input pass: op.ntrans() transforms per sequence, each of its own input, whose outputs
 // are combined per output element in registers and written once (row-major mapping;
-// blockIdx.x selects B sequences). The next transform's loads are issued before the current
-// transform's outputs are combined, so they are in flight meanwhile.
-//   float2 load(int t, int seq, int i)            element i of transform t's input
-//   Ctx ctx(int seq, int o)                       per-output context, read once
-//   float term(int t, const Ctx&, int o, SeqView v)   transform t's contribution to output o
-//   void store(int seq, int o, const Ctx&, float acc)
+// blockIdx.x selects B sequences).
+//   Trans trans(int t)                              transform t's parameters
+//   float2 load(const Trans&, int seq, int i)       element i of its input
+//   float term(const Trans&, int seq, int o, SeqView v)   its contribution to output o
+//   void store(int seq, int o, float acc)
 // Outputs per sequence nout() <= L / 2 (each thread owns at most PER / 2 of them).
 template <int LEN, int DIR, class Op>
 __global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB)
@@ -263,49 +314,31 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB)
   constexpr int PER = B * L / NT;
   constexpr int MAXO = PER / 2;
   extern __shared__ float2 smem[];
+  // the sums live in shared memory after the sequences (each thread its own MAXO slots), so no
+  // registers stay live across the transforms
+  float* acc = reinterpret_cast<float*>(smem + B * LP) + threadIdx.x;
   const int nseq = op.nseq(), nout = op.nout(), ntr = op.ntrans();
   const int seq0 = blockIdx.x * B;
-  typename Op::Ctx ctx[MAXO];
-  float acc[MAXO];
 #pragma unroll
-  for (int m = 0; m < MAXO; ++m) {
-    const int idx = threadIdx.x + m * NT;
-    acc[m] = 0.f;
-    if (idx < B * nout) {
-      const int b = idx / nout, o = idx % nout;
-      if (seq0 + b < nseq) ctx[m] = op.ctx(seq0 + b, o);
-    }
-  }
-  float2 r[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = threadIdx.x + k * NT;
-    const int b = idx / L, i = idx % L;
-    r[k] = (seq0 + b < nseq && ntr > 0) ? op.load(0, seq0 + b, i) : make_float2(0.f, 0.f);
-  }
+  for (int m = 0; m < MAXO; ++m) acc[m * NT] = 0.f;
+#pragma unroll 1
   for (int t = 0; t < ntr; ++t) {
+    const typename Op::Trans tp = op.trans(t);
     if (t > 0) __syncthreads();  // the previous transform's outputs have been read
+    float2 r[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      const int idx = threadIdx.x + k * NT;
-      smem[(idx / L) * LP + spad(idx % L)] = r[k];
+      int b, i;
+      load_pos<L>(k, &b, &i);
+      r[k] = (seq0 + b < nseq) ? op.load(tp, seq0 + b, i) : make_float2(0.f, 0.f);
     }
-    __syncthreads();
-    fft_stages<L, 0, DIR>(smem, tw);
-    if (t + 1 < ntr) {
-#pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const int idx = threadIdx.x + k * NT;
-        const int b = idx / L, i = idx % L;
-        r[k] = (seq0 + b < nseq) ? op.load(t + 1, seq0 + b, i) : make_float2(0.f, 0.f);
-      }
-    }
+    fft_from_regs<L, DIR>(smem, r, tw, [] {});
 #pragma unroll
     for (int m = 0; m < MAXO; ++m) {
       const int idx = threadIdx.x + m * NT;
       if (idx < B * nout) {
         const int b = idx / nout, o = idx % nout;
-        if (seq0 + b < nseq) acc[m] += op.term(t, ctx[m], o, SeqView{smem + b * LP});
+        if (seq0 + b < nseq) acc[m * NT] += op.term(tp, seq0 + b, o, SeqView{smem + b * LP});
       }
     }
   }
@@ -314,7 +347,7 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB)
     const int idx = threadIdx.x + m * NT;
     if (idx < B * nout) {
       const int b = idx / nout, o = idx % nout;
-      if (seq0 + b < nseq) op.store(seq0 + b, o, ctx[m], acc[m]);
+      if (seq0 + b < nseq) op.store(seq0 + b, o, acc[m * NT]);
     }
   }
 }
@@ -325,13 +358,14 @@ int launch_pass_accum(const Op& op, const float2* tw, cudaStream_t s) {
   const int nblk = (op.nseq() + C::B - 1) / C::B;
   if (nblk == 0) return FR_OK;
   auto kern = fft_pass_accum_kernel<LEN, DIR, Op>;
+  constexpr size_t smem = C::SMEM + (size_t)C::B * LEN / 2 * sizeof(float);
   static bool attr = false;
   if (!attr) {
-    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr = true;
   }
-  kern<<<nblk, C::NT, C::SMEM, s>>>(op, tw);
+  kern<<<nblk, C::NT, smem, s>>>(op, tw);
   FR_LAUNCHED();
   return FR_OK;
 }
@@ -353,19 +387,16 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB_SUM)
   float2 r[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    const int idx = threadIdx.x + k * NT;
-    const int b = idx / L, i = idx % L;
+    int b, i;
+    load_pos<L>(k, &b, &i);
     r[k] = (seq0 + b < nseq) ? op.load(seq0 + b, i) : make_float2(0.f, 0.f);
   }
   for (int t = 0; t < nterm; ++t) {
     if (t > 0) __syncthreads();  // the previous transform's outputs have been read
+    float2 x[PER];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int idx = threadIdx.x + k * NT;
-      smem[(idx / L) * LP + spad(idx % L)] = op.prep(t, r[k]);
-    }
-    __syncthreads();
-    fft_stages<L, 0, DIR>(smem, tw);
+    for (int k = 0; k < PER; ++k) x[k] = op.prep(t, r[k]);
+    fft_from_regs<L, DIR>(smem, x, tw, [] {});
     if constexpr (Op::TRANSPOSED) {
       for (int idx = threadIdx.x; idx < B * nout; idx += NT) {
         const int o = idx / B, b = idx % B;
@@ -407,6 +438,16 @@ __device__ __forceinline__ void store_run(float2* dst, const float2* v, int n) {
   } else {
     for (int g = 0; g < n; ++g) dst[g] = v[g];
   }
+}
+
+// a[t] of a small parameter array with every index static (no copy of the array to local memory)
+template <class T, int N>
+__device__ __forceinline__ T pick_static(const T (&a)[N], int t) {
+  T r = a[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k)
+    if (t == k) r = a[k];
+  return r;
 }
 
 // Defaults for the optional parts of an op.

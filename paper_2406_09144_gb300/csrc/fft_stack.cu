@@ -131,9 +131,6 @@ struct G1SparseOp : OpBase {
 };
 
 struct G2StackOp {
-  struct Ctx {
-    int32_t tq;
-  };
   const float2* b1[STACK_K];   // [nx][ncomp_k]
   const int* comp[STACK_K];    // [ntv] compact tile-row index or -1
   int ncomp[STACK_K];          // nrows_k * TILE
@@ -143,22 +140,31 @@ struct G2StackOp {
   const float* corr;
   const int32_t* tq;
   int nx, ny, Nv, accumulate;
+  struct Trans {
+    const float2* b1;
+    const int* comp;
+    int ncomp;
+    long long k64;
+  };
   __host__ __device__ int nseq() const { return nx; }
   __host__ __device__ int nout() const { return ny; }
   __device__ int ntrans() const { return nt; }
-  __device__ float2 load(int t, int jx, int v) const {
-    const int c = __ldg(&comp[t][v / TILE]);
-    if (c < 0) return make_float2(0.f, 0.f);
-    return b1[t][(size_t)jx * ncomp[t] + c * TILE + (v & (TILE - 1))];
+  __device__ Trans trans(int t) const {
+    return Trans{pick_static(b1, t), pick_static(comp, t), pick_static(ncomp, t),
+                 pick_static(k64, t)};
   }
-  __device__ Ctx ctx(int jx, int jy) const { return Ctx{__ldg(&tq[jx * ny + jy])}; }
-  __device__ float term(int t, const Ctx& c, int jy, SeqView s) const {
+  __device__ float2 load(const Trans& p, int jx, int v) const {
+    const int c = __ldg(&p.comp[v / TILE]);
+    if (c < 0) return make_float2(0.f, 0.f);
+    return p.b1[(size_t)jx * p.ncomp + c * TILE + (v & (TILE - 1))];
+  }
+  __device__ float term(const Trans& p, int jx, int jy, SeqView s) const {
     const float2 z = s[wrap(jy - (ny >> 1), Nv)];
     float cs, sn;
-    plane_phase(c.tq, k64[t], &cs, &sn);
+    plane_phase(__ldg(&tq[jx * ny + jy]), p.k64, &cs, &sn);
     return z.x * cs - z.y * sn;  // Re(z exp(+2 pi i w_k (t - t_c)))
   }
-  __device__ void store(int jx, int jy, const Ctx&, float acc) const {
+  __device__ void store(int jx, int jy, float acc) const {
     const int pix = jx * ny + jy;
     const float val = acc * __ldg(&corr[pix]);
     dirty[pix] = accumulate ? dirty[pix] + val : val;
