@@ -96,6 +96,12 @@ int fr_plan_create(const double *uvw, int64_t nrow, const double *freqs, int32_t
 /* R, Eq. (rime): sky [nsky][nx][ny] (device) -> vis [nrow][nchan] (device, overwritten). */
 int fr_degrid(fr_plan_t plan, const float *sky, fr_cf32 *vis, void *stream);
 
+/* N^-1 R: R of Eq. (rime) followed by the inverse noise covariance of Eq. (ham), i.e. every
+ * visibility times its weight (the plan's weights; 1 without weights; dropped visibilities 0).
+ * It is the adjoint of fr_grid with weights (R^dag N^-1 = (N^-1 R)^dag for the real sky): the
+ * backward pass of a weighted gridding call. Layouts and errors as fr_degrid. */
+int fr_degrid_weighted(fr_plan_t plan, const float *sky, fr_cf32 *vis, void *stream);
+
 /* R^dag (N^-1 if apply_weights != 0), Eq. (clean): vis [nrow][nchan] (device) ->
  * dirty [nsky][nx][ny] (device, overwritten): D_j = Re sum_k w_k y_k exp(+2 pi i phase_kj) / n_j. */
 int fr_grid(fr_plan_t plan, const fr_cf32 *vis, int32_t apply_weights, float *dirty, void *stream);
@@ -190,6 +196,13 @@ int fr_noise_apply_inverse(fr_plan_t plan, const float *x, int32_t batch, float 
 int fr_fast_likelihood_grad(fr_plan_t plan, const float *sky, const float *dirty, int32_t batch,
                             float *grad, double *value, void *stream);
 
+/* The same as fr_fast_likelihood_grad, and with ninv_resid non-NULL also N'^-1 r (device
+ * float32 [batch][nsky][nx][ny], the vector the likelihood's gradient with respect to the dirty
+ * image d is made of: dH/dd = N'^-1 r). ninv_resid may alias neither input nor grad. */
+int fr_fast_likelihood_grad_resid(fr_plan_t plan, const float *sky, const float *dirty,
+                                  int32_t batch, float *grad, float *ninv_resid, double *value,
+                                  void *stream);
+
 /* Allocation-free PSF convolution. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory, such as code embedded in an application that owns
  * the whole device-memory budget through its own pool, or code running where a cudaMalloc would
@@ -201,7 +214,8 @@ int fr_fast_likelihood_grad(fr_plan_t plan, const float *sky, const float *dirty
  *   psf   device float32 [2nx][2ny], offset (a, b) stored at (a + nx, b + ny) as fr_dirty_psf
  *         writes it (row 0 and column 0 are not used)
  *   sky   device float32 [batch][nx][ny];  out: device float32 [batch][nx][ny]
- *   nx, ny powers of two >= 16 with nx * ny <= 2^20 (FR_EINVAL with a message otherwise)
+ *   nx, ny powers of two in [16, 8192] with nx * ny <= 2^20 (FR_EINVAL with a message
+ *         otherwise, before any work is queued)
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture. All calls share the one array and it keeps
  * the last call's contents; each call writes every intermediate before reading it. Calls that
@@ -261,6 +275,14 @@ const char *fr_profile_category(int32_t cat);
  * (unnormalised). Returns FR_EINVAL unless 2 <= n <= 16384 with n = 2^k 3^a 5^b. Test
  * support; needs no GPU. */
 int fr_selftest_fft_host(float *data, int32_t n, int32_t batch, int32_t dir);
+
+/* Test support for the error path of the bounded device waits (no counterpart in the paper):
+ * launches on `stream` one CTA that arms its mbarrier for a transfer exactly as the degridder
+ * does but issues no copy, so its bounded wait gives up (after about 0.3 s); the CTA records
+ * the timeout in the plan's status word and returns with no copy in flight. The next
+ * fr_plan_check on that stream then returns FR_ETIMEOUT and clears the word. Nothing faults and
+ * the context stays usable. */
+int fr_selftest_wait_timeout(fr_plan_t plan, void *stream);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,7 @@ from .measurement import (  # noqa: F401
     grid,
     psf,
     psf_apply,
+    psf_apply_at,
     psf_window,
     truncate_psf,
     psf_apply_truncated,

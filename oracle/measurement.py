@@ -179,6 +179,26 @@ def psf_apply(psf_img, sky):
     return out
 
 
+def psf_apply_at(psf_img, sky, pix):
+    """The linear convolution of psf_apply at chosen output pixels only (Sec. 3.3.2), each an
+    O(nx ny) sum, for checks of large images:
+
+        out(p) = sum_{q in sky} PSF(p - q) s(q),   p = (pix // ny, pix % ny)
+
+    psf_img [2nx, 2ny] (offset (a, b) at index (a + nx, b + ny)), sky [nx, ny]; float64 [n].
+    """
+    P = np.asarray(psf_img, dtype=np.float64)
+    s = np.asarray(sky, dtype=np.float64)
+    nx, ny = s.shape
+    out = np.empty(len(pix))
+    for i, k in enumerate(np.asarray(pix, dtype=np.int64)):
+        px, py = int(k) // ny, int(k) % ny
+        # offsets p - q for q in [0, nx) x [0, ny): index (px - qx + nx, py - qy + ny)
+        window = P[px + 1:px + nx + 1, py + 1:py + ny + 1][::-1, ::-1]
+        out[i] = float(np.sum(window * s))
+    return out
+
+
 def psf_window(nx, ny, lx, ly):
     """Half-widths (hx, hy) of the PSF window a zero-padded lx x ly grid holds without
     wrap-around (reduced padding, Sec. 3.3.2): hx = min(lx - nx, nx - 1), hy likewise.

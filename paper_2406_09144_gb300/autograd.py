@@ -4,32 +4,21 @@ PyTorch's convention for a real loss L of a complex tensor z is grad_z = dL/dRe 
 With it:
   * Degrid  y = R s (Eq. rime), s real: grad_s = Re(R^H grad_y) = R^dagger grad_y, i.e. the
     gridding kernel without weights;
-  * Grid    d = R^dagger (N^-1) y (Eq. clean): grad_y = N^-1 R grad_d, i.e. the degridding kernel
-    followed by the weights;
+  * Grid    d = R^dagger (N^-1) y (Eq. clean): grad_y = N^-1 R grad_d (fr_degrid_weighted);
   * PsfLikelihood / ExactLikelihood  L_b = 1/2 s_b.(A s_b) - s_b.d_b with A = PSF * (Sec. 3.3.2)
     or R^dagger N^-1 R: grad_s = (A s - d) * grad_L (A is self-adjoint), grad_d = -s * grad_L.
     The forward kernel already produces A s - d, so backward costs no extra launch.
   * FastLikelihood  H_b = 1/2 r_b.(N'^-1 r_b), r = d - PSF * s (Eq. ham_new, Sec. 3.3.3, after
-    Plan.noise_fit): grad_s = -PSF * (N'^-1 r) * grad_H (from the forward kernel), and
-    grad_d = N'^-1 r * grad_H (N'^-1 symmetric; computed only when asked for).
-All arithmetic runs in the library's CUDA kernels through binding.Plan.
+    Plan.noise_fit): grad_s = -PSF * (N'^-1 r) * grad_H and grad_d = N'^-1 r * grad_H (N'^-1
+    symmetric); the forward kernel returns both vectors (fr_fast_likelihood_grad_resid).
+All operator arithmetic runs in the library's CUDA kernels through binding.Plan; backward only
+scales the saved vectors by the incoming gradient.
 """
 from __future__ import annotations
 
 import torch
 
 from .binding import Plan
-
-
-def _weights(plan: Plan, device):
-    w = getattr(plan, "_weights_dev", None)
-    if w is None or w.device != device:
-        import numpy as np
-        src = plan._weights_host if getattr(plan, "_weights_host", None) is not None else \
-            np.ones(plan.vis_shape, dtype=np.float32)
-        w = torch.tensor(np.array(src, dtype=np.float32), device=device)
-        plan._weights_dev = w
-    return w
 
 
 class Degrid(torch.autograd.Function):
@@ -56,10 +45,7 @@ class Grid(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_dirty):
-        g = ctx.plan.degrid(grad_dirty.contiguous())
-        if ctx.apply_weights:
-            g = g * _weights(ctx.plan, g.device)
-        return g, None, None
+        return ctx.plan.degrid(grad_dirty.contiguous(), weighted=ctx.apply_weights), None, None
 
 
 class PsfLikelihood(torch.autograd.Function):
@@ -85,22 +71,23 @@ class FastLikelihood(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, sky, dirty, plan):
-        value, grad = plan.fast_likelihood_grad(sky.contiguous(), dirty.contiguous())
-        ctx.plan = plan
-        ctx.save_for_backward(sky, dirty, grad)
+        if ctx.needs_input_grad[1]:
+            value, grad, nr = plan.fast_likelihood_grad(sky.contiguous(), dirty.contiguous(),
+                                                        want_ninv_resid=True)
+        else:
+            value, grad = plan.fast_likelihood_grad(sky.contiguous(), dirty.contiguous())
+            nr = None
+        ctx.save_for_backward(sky, grad, nr)
         return torch.as_tensor(value, dtype=torch.float64, device=sky.device)
 
     @staticmethod
     def backward(ctx, grad_value):
-        sky, dirty, grad = ctx.saved_tensors
+        sky, grad, nr = ctx.saved_tensors
         gv = grad_value.to(torch.float32).view(-1, *([1] * (sky.dim() - 1)))
         if sky.dim() == 3:
             gv = gv.view(*([1] * sky.dim()))
         gs = grad * gv if ctx.needs_input_grad[0] else None
-        gd = None
-        if ctx.needs_input_grad[1]:
-            r = dirty.contiguous() - ctx.plan.psf_apply(sky.contiguous())
-            gd = ctx.plan.noise_apply_inverse(r) * gv
+        gd = nr * gv if ctx.needs_input_grad[1] else None
         return gs, gd, None
 
 

@@ -15,6 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfastresolve.so")
 
 FR_WTERM, FR_NTERM, FR_MFS, FR_DROP_OOB, FR_NO_PSF, FR_DETERMINISTIC = 1, 2, 4, 8, 16, 32
+FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EUNSUPPORTED, FR_ETIMEOUT = -1, -2, -3, -4, -5
 ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EUNSUPPORTED", -5: "FR_ETIMEOUT"}
 
 EXPORTS = ["fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
@@ -22,7 +23,8 @@ EXPORTS = ["fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_app
            "fr_plan_check", "fr_plan_destroy", "fr_strerror", "fr_last_error", "fr_launch_count",
            "fr_selftest_fft_host", "fr_psf_convolve_noalloc", "fr_noise_fit", "fr_noise_kernel",
            "fr_noise_apply_inverse", "fr_fast_likelihood_grad", "fr_psf_set_padding",
-           "fr_psf_padding"]
+           "fr_psf_padding", "fr_degrid_weighted", "fr_fast_likelihood_grad_resid",
+           "fr_selftest_wait_timeout"]
 
 
 class FastResolveError(RuntimeError):
@@ -59,6 +61,8 @@ def load(path: str = LIB_PATH):
     P, I32, I64, D, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint32
     lib.fr_plan_create.argtypes = [P, I64, P, I32, P, I32, I32, D, D, D, U32, P, ctypes.POINTER(P)]
     lib.fr_degrid.argtypes = [P, P, P, P]
+    lib.fr_degrid_weighted.argtypes = [P, P, P, P]
+    lib.fr_fast_likelihood_grad_resid.argtypes = [P, P, P, I32, P, P, P, P]
     lib.fr_grid.argtypes = [P, P, I32, P, P]
     lib.fr_dirty_psf.argtypes = [P, P, P, P, P, P]
     lib.fr_psf_apply.argtypes = [P, P, I32, P, P]
@@ -82,6 +86,7 @@ def load(path: str = LIB_PATH):
     lib.fr_launch_count.argtypes = [ctypes.c_int]
     lib.fr_launch_count.restype = ctypes.c_uint64
     lib.fr_selftest_fft_host.argtypes = [P, I32, I32, I32]
+    lib.fr_selftest_wait_timeout.argtypes = [P, P]
     lib.fr_profile_enable.argtypes = [ctypes.c_int]
     lib.fr_profile_enable.restype = None
     lib.fr_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -93,7 +98,8 @@ def load(path: str = LIB_PATH):
     lib.fr_psf_convolve_noalloc.restype = ctypes.c_int
     for name in ("fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
                  "fr_likelihood_grad", "fr_major_cycle", "fr_plan_get_info", "fr_plan_footprint",
-                 "fr_plan_check", "fr_selftest_fft_host", "fr_psf_set_padding", "fr_psf_padding"):
+                 "fr_plan_check", "fr_selftest_fft_host", "fr_psf_set_padding", "fr_psf_padding",
+                 "fr_degrid_weighted", "fr_fast_likelihood_grad_resid", "fr_selftest_wait_timeout"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -205,7 +211,6 @@ class Plan:
             weights = np.ascontiguousarray(np.broadcast_to(weights, (self.nrow, self.nchan)),
                                            dtype=np.float32)
             wptr = weights.ctypes.data
-        self._weights_host = weights  # kept for the adjoint of the weighted gridder
         flags = ((FR_WTERM if wterm else 0) | (FR_NTERM if nterm else 0) | (FR_MFS if mfs else 0)
                  | (FR_DROP_OOB if drop_oob else 0) | (FR_NO_PSF if no_psf else 0)
                  | (FR_DETERMINISTIC if deterministic else 0))
@@ -258,13 +263,15 @@ class Plan:
         return (self.nrow, self.nchan)
 
     # ------------------------------------------------------------------ operators
-    def degrid(self, sky, out=None, stream=None):
-        """R (Eq. rime): sky [nsky, nx, ny] float32 -> vis [nrow, nchan] complex64."""
+    def degrid(self, sky, out=None, stream=None, weighted=False):
+        """R (Eq. rime): sky [nsky, nx, ny] float32 -> vis [nrow, nchan] complex64; with
+        weighted=True N^-1 R (every visibility times its weight)."""
         torch = _torch()
         if out is None:
             out = torch.empty(self.vis_shape, dtype=torch.complex64, device=sky.device)
-        check(load().fr_degrid(self._h, _dev(sky, torch.float32, self.sky_shape, "sky"),
-                               _dev(out, torch.complex64, self.vis_shape, "vis"), _stream_ptr(stream)))
+        fn = load().fr_degrid_weighted if weighted else load().fr_degrid
+        check(fn(self._h, _dev(sky, torch.float32, self.sky_shape, "sky"),
+                 _dev(out, torch.complex64, self.vis_shape, "vis"), _stream_ptr(stream)))
         return out
 
     def grid(self, vis, apply_weights=True, out=None, stream=None):
@@ -368,17 +375,23 @@ class Plan:
                                             _dev(out, torch.float32, shape, "out"), _stream_ptr(stream)))
         return out
 
-    def fast_likelihood_grad(self, sky, dirty, grad=None, want_value=True, stream=None):
-        """Eq. ham_new: value = 1/2 r.(N'^-1 r), grad = -PSF * (N'^-1 r), r = d - PSF * sky."""
+    def fast_likelihood_grad(self, sky, dirty, grad=None, want_value=True, stream=None,
+                             want_ninv_resid=False):
+        """Eq. ham_new: value = 1/2 r.(N'^-1 r), grad = -PSF * (N'^-1 r), r = d - PSF * sky;
+        with want_ninv_resid=True also returns N'^-1 r (the gradient with respect to d)."""
         torch = _torch()
         batch, shape = self._batch_shape(sky)
         if grad is None:
             grad = torch.empty(shape, dtype=torch.float32, device=sky.device)
         val = np.zeros(batch, dtype=np.float64)
-        check(load().fr_fast_likelihood_grad(
+        nr = torch.empty(shape, dtype=torch.float32, device=sky.device) if want_ninv_resid else None
+        check(load().fr_fast_likelihood_grad_resid(
             self._h, _dev(sky, torch.float32, shape, "sky"), _dev(dirty, torch.float32, shape, "dirty"),
             batch, _dev(grad, torch.float32, shape, "grad"),
+            _dev(nr, torch.float32, shape, "ninv_resid") if nr is not None else None,
             val.ctypes.data if want_value else None, _stream_ptr(stream)))
+        if want_ninv_resid:
+            return (val if want_value else None), grad, nr
         return (val if want_value else None), grad
 
     def _batch_shape(self, sky):

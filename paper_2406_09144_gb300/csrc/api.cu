@@ -167,6 +167,27 @@ __global__ void __launch_bounds__(RED_T) chi2_kernel(const float2* vis, const fl
   if (threadIdx.x == 0) atomicAdd(acc, v);
 }
 
+// vis[user index] *= weight for every kept visibility (sorted order -> user index)
+__global__ void __launch_bounds__(RED_T) weight_vis_kernel(const uint32_t* perm, const float* wgt,
+                                                           int64_t n, float2* vis) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float wv = wgt[i];
+    float2* v = vis + (perm[i] & 0x7fffffffu);
+    float2 x = *v;
+    x.x *= wv;
+    x.y *= wv;
+    *v = x;
+  }
+}
+
+// out = -x
+__global__ void __launch_bounds__(RED_T) negate_kernel(const float* x, size_t n, float* out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = -x[i];
+}
+
 __global__ void sum_weights_kernel(const float* w, int64_t b, int64_t e, double* acc) {
   double v = 0.0;
   for (int64_t i = b + blockIdx.x * (int64_t)RED_T + threadIdx.x; i < e;
@@ -1049,6 +1070,26 @@ int fr_degrid(fr_plan_t p, const float* sky, fr_cf32* vis, void* stream) {
   return run_degrid(p, p->geo, p->lay, w, sky, (float2*)vis, s);
 }
 
+int fr_degrid_weighted(fr_plan_t p, const float* sky, fr_cf32* vis, void* stream) {
+  if (!p || !sky || !vis) {
+    set_error("plan, sky and vis must be non-null");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  FR_TRY(run_degrid(p, p->geo, p->lay, w, sky, (float2*)vis, s));
+  // N^-1: each kept visibility times its weight (dropped ones are already zero)
+  const int64_t n = p->lay.nsorted;
+  if (n > 0) {
+    ProfScope ps(PC_REDUCE, s, (double)n * 16.0);
+    weight_vis_kernel<<<nblocks((size_t)n), RED_T, 0, s>>>(p->lay.perm, p->lay.wgt, n,
+                                                           (float2*)vis);
+    FR_LAUNCHED();
+  }
+  return FR_OK;
+}
+
 int fr_grid(fr_plan_t p, const fr_cf32* vis, int32_t apply_weights, float* dirty, void* stream) {
   if (!p || !vis || !dirty) {
     set_error("plan, vis and dirty must be non-null");
@@ -1339,6 +1380,12 @@ int fr_noise_apply_inverse(fr_plan_t p, const float* x, int32_t batch, float* ou
 
 int fr_fast_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, int32_t batch,
                             float* grad, double* value, void* stream) {
+  return fr_fast_likelihood_grad_resid(p, sky, dirty, batch, grad, nullptr, value, stream);
+}
+
+int fr_fast_likelihood_grad_resid(fr_plan_t p, const float* sky, const float* dirty,
+                                  int32_t batch, float* grad, float* ninv_resid, double* value,
+                                  void* stream) {
   if (!p || !sky || !dirty || !grad || batch < 1) {
     set_error("plan, sky, dirty, grad must be non-null and batch >= 1");
     return FR_EINVAL;
@@ -1366,6 +1413,11 @@ int fr_fast_likelihood_grad(fr_plan_t p, const float* sky, const float* dirty, i
                               twiddles_of(p, g.nx), s));
   // grad = -PSF * (N'^-1 r) = PSF * u (the PSF passes without a dirty image leave red alone)
   FR_TRY(psf_common(p, w->img_b, batch, grad, nullptr, nullptr, s));
+  if (ninv_resid) {  // N'^-1 r = -u
+    ProfScope ps(PC_REDUCE, s, (double)n * 8.0);
+    negate_kernel<<<nblocks(n), RED_T, 0, s>>>(w->img_b, n, ninv_resid);
+    FR_LAUNCHED();
+  }
   if (value) {
     FR_CUDA_TRY(cudaMemcpyAsync(value, w->red, batch * sizeof(double), cudaMemcpyDeviceToHost, s));
     FR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1493,6 +1545,14 @@ int fr_plan_check(fr_plan_t p, void* stream) {
     return FR_ETIMEOUT;
   }
   return FR_OK;
+}
+
+int fr_selftest_wait_timeout(fr_plan_t p, void* stream) {
+  if (!p) {
+    set_error("plan must be non-null");
+    return FR_EINVAL;
+  }
+  return selftest_wait_timeout(p->status, (cudaStream_t)stream);
 }
 
 int fr_selftest_fft_host(float* data, int32_t n, int32_t batch, int32_t dir) {

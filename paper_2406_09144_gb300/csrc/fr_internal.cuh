@@ -371,6 +371,8 @@ int grid_plane(const Geometry& geo, const VisLayout& lay, int g, int p, const fl
                float2* grid, const DetArgs& det, cudaStream_t s);
 int grid_prepare(const Geometry& geo, const VisLayout& lay, const float2* vis, int apply_weights,
                  float2* ysorted, cudaStream_t s);
+// one CTA whose bounded mbarrier wait runs out (no copy issued): sets ST_TIMEOUT in *status
+int selftest_wait_timeout(int* status, cudaStream_t s);
 int make_tables(Geometry* geo, const std::vector<double>& inv_phi_u,
                 const std::vector<double>& inv_phi_v, cudaStream_t s);
 void kernel_ft_tables(const Geometry& geo, std::vector<double>& inv_u, std::vector<double>& inv_v);

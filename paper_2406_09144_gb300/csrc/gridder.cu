@@ -1077,6 +1077,28 @@ __global__ void __launch_bounds__(256) degrid_kernel(const __grid_constant__ CUt
   }
 }
 
+// Self-test of the bounded wait (no copy, no fault): one CTA arms its mbarrier for a transfer the
+// way degrid_kernel does, but issues no copy, so the phase never completes; mbar_wait_bounded
+// gives up, the CTA records ST_TIMEOUT in the status word and returns with nothing in flight.
+__global__ void wait_timeout_kernel(int* status) {
+  __shared__ __align__(8) uint64_t mbar;
+  const uint32_t bar = smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(1024u)
+                 : "memory");
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+int selftest_wait_timeout(int* status, cudaStream_t s) {
+  wait_timeout_kernel<<<1, 32, 0, s>>>(status);
+  FR_LAUNCHED();
+  return FR_OK;
+}
+
 // ------------------------------------------------------------------------------ grid
 // Gridder: one warp spreads one visibility at a time, lane l owning footprint cells
 // l, l + 32, ... (row a = idx / W, column b = idx % W), into the warp's private shared-memory

@@ -11,7 +11,7 @@
 // size that is part of the library image, so no call allocates anything.
 //
 // The array is 32 MiB. Every GPU that loads the library holds it until the process exits. It
-// fits images with nx * ny <= 2^20 pixels (nx, ny powers of two, at least 16).
+// fits images with nx * ny <= 2^20 pixels (nx, ny powers of two in [16, 8192]).
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -71,8 +71,9 @@ extern "C" int fr_psf_convolve_noalloc(const float* psf, const float* sky, int32
     set_error("psf, sky and out must be non-null and batch >= 1");
     return FR_EINVAL;
   }
-  if (nx < 16 || ny < 16 || (nx & (nx - 1)) || (ny & (ny - 1))) {
-    set_error("nx, ny must be powers of two >= 16 (got %d x %d)", nx, ny);
+  if (nx < 16 || ny < 16 || nx > 8192 || ny > 8192 || (nx & (nx - 1)) || (ny & (ny - 1))) {
+    // the padded transforms of 2nx and 2ny points must be lengths the FFT passes take
+    set_error("nx, ny must be powers of two in [16, 8192] (got %d x %d)", nx, ny);
     return FR_EINVAL;
   }
   // scratch: twiddles (2ny, 2nx), transfer TT [ny+1][2nx] f32, then a region used first for the

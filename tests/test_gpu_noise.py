@@ -2,8 +2,9 @@
 against the FP64 oracle (oracle/noise.py), through the C ABI.
 
 Tolerances: the kernel K inherits the NUFFT error of the exact N'(I_delta), one R and one
-R^dagger at eps = 1e-5 (relative L2 <= 5 eps against the oracle's argmin); N'^-1 and the
-likelihood with a given kernel are FP32 FFT arithmetic (<= 2e-6 and 1e-5 relative)."""
+R^dagger at eps = 1e-5 (<= 2 eps), amplified by at most rho = sqrt(N) |N'(I_delta)| / |K|
+(derived in the fit test; rho is about 1.0-1.1 here); N'^-1 and the likelihood with a given
+kernel are FP32 FFT arithmetic (<= 2e-6 and 1e-5 relative)."""
 import numpy as np
 import pytest
 
@@ -51,7 +52,18 @@ def test_noise_kernel_fit_matches_oracle_argmin(wc, nchan, per, nx, ny):
     n_delta = noise.noise_cov_of_delta(obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, nx, ny,
                                        eps_noise, weights=w, nsky=plan.nsky, wterm=obs.wterm)
     K_ref = noise.fit_noise_kernel(n_delta, eps_noise)
-    assert rel(K, K_ref) <= 5e-5, rel(K, K_ref)
+    # The loss of Sec. 3.3.3 separates per frequency: with D = FFT(I_delta), |D_k| = 1 and
+    # z = FFT(N'(I_delta)) conj(D), its minimiser over K >= eps is K_k = max(Re z_k, eps),
+    # 1-Lipschitz in z_k. By Parseval |K - K_ref| <= |z - z_ref| = sqrt(N) |N' - N'_ref| (I_delta),
+    # so rel(K) <= rho rel(N'(I_delta)) with rho = sqrt(N) |N'_ref(I_delta)| / |K_ref|. The
+    # library's N'(I_delta) is one R and one R^dagger N^-1 of the plan (<= 2 eps), measured here.
+    delta = noise.centre_delta(plan.nsky, nx, ny)
+    n_gpu = plan.grid(plan.degrid(dev(delta))).cpu().numpy() + eps_noise * delta
+    rn = rel(n_gpu, n_delta)
+    rho = np.sqrt(nx * ny) * np.linalg.norm(n_delta) / np.linalg.norm(K_ref)
+    assert rn <= 2e-5, rn
+    assert rel(K, K_ref) <= rho * rn * 1.01 + 1e-6, (rel(K, K_ref), rho, rn)
+    assert rel(K, K_ref) <= 2e-5 * rho * 1.01 + 1e-6, (rel(K, K_ref), rho)
     assert np.all(K >= np.float32(eps_noise) * (1 - 1e-6))
     ref_logdet = 0.5 * np.log(2 * np.pi * K_ref).reshape(plan.nsky, -1).sum(1)
     assert np.allclose(logdet, ref_logdet, rtol=1e-5)

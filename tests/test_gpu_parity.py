@@ -315,48 +315,136 @@ def test_plan_info_and_footprint():
     plan.check()
 
 
-# ------------------------------------------------------------------ full size, sampled
+# ------------------------------------------------------------------ the PSF chain, oracle PSF
+
+@pytest.mark.parametrize("nchan,per", [(1, False), (2, True)])
+def test_psf_convolution_chain_against_oracle_psf(nchan, per):
+    """The whole PSF path against the oracle alone: the FP64 oracle PSF (Sec. 3.3.2, direct
+    sums) convolved with each sky by the oracle's direct linear convolution, against
+    fr_psf_apply, whose PSF the library grids itself (NUFFT at eps) and whose convolution runs
+    on its own FFT passes."""
+    nx, ny = 64, 48
+    obs = synth.random_observation(2000, nchan, nx, ny, 2e-3, seed=70, per_channel_sky=per)
+    plan = make_plan(obs, mfs=not per)
+    w32 = obs.weights.astype(np.float32)
+    P = oracle.psf(obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, nx, ny, weights=w32,
+                   nsky=plan.nsky)
+    sky = synth.random_skies(2 * plan.nsky, nx, ny, seed=71).reshape(2, plan.nsky, nx, ny)
+    got = plan.psf_apply(dev(sky)).cpu().numpy()
+    ref = np.stack([oracle.psf_apply(P[k:k + 1], sky[:, k]) for k in range(plan.nsky)], axis=1)
+    assert rel(got, ref) <= EPS, rel(got, ref)
+
+
+# ------------------------------------------------------------------ full size
+
+NVIS_SAMPLE = 10_000   # sampled visibilities, each an O(N_pix) FP64 direct sum
+NPIX_SAMPLE = 1_000    # sampled pixels, each an O(N_vis) FP64 direct sum
+
+
+@pytest.mark.slow
+def test_small_full_brute_force():
+    """Plain method, small (128^2, 1 channel at 1.4 GHz, 505,440 visibilities, w = 0): every
+    output of R, R^dagger N^-1 and the PSF convolution against the FP64 direct sums. At w = 0
+    with 1/n = 1 the PSF convolution equals R^dagger N^-1 R exactly (Sec. 3.3.2), so its oracle
+    is the direct R followed by the direct R^dagger N^-1."""
+    obs = synth.observation("small")
+    assert obs.nrow == 505_440 and not obs.wterm
+    plan = make_plan(obs)
+    n = obs.nx
+    sky = synth.sky_image(n, n, seed=0)[None]
+    rows, chans = np.arange(obs.nrow), np.zeros(obs.nrow, int)
+    vis = plan.degrid(dev(sky)).cpu().numpy()
+    ref = cdft.degrid_at(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, rows, chans,
+                         wterm=False)
+    assert rel(vis[:, 0], ref) <= EPS, rel(vis[:, 0], ref)
+    w32 = obs.weights.astype(np.float32)
+    pix = np.arange(n * n)
+    y = synth.complex_gaussian((obs.nrow, 1), seed=1)
+    d = plan.grid(dev(y, torch.complex64)).cpu().numpy()
+    refd = cdft.grid_at(y, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, n, n,
+                        np.zeros(n * n, int), pix, weights=w32, wterm=False)
+    assert rel(d.reshape(-1), refd) <= EPS, rel(d.reshape(-1), refd)
+    conv = plan.psf_apply(dev(sky[None])).cpu().numpy()[0, 0]
+    v0 = cdft.degrid_at(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, rows, chans,
+                        wterm=False, nterm=False)
+    refc = cdft.grid_at(v0[:, None], obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, n, n,
+                        np.zeros(n * n, int), pix, weights=w32, wterm=False, nterm=False)
+    assert rel(conv.reshape(-1), refc) <= EPS, rel(conv.reshape(-1), refc)
+
+
+def _sampled_psf_checks(plan, obs, sky, dirty, rng, npix_psf, npix_conv):
+    """The PSF image at sampled offsets against the oracle's direct sums (<= eps), and the
+    likelihood gradient PSF * s - d of the benchmark's call at sampled pixels against the
+    oracle's direct linear convolution of that PSF image (<= 2e-6: FP32 FFTs only)."""
+    nx, ny = obs.nx, obs.ny
+    w32 = obs.weights.astype(np.float32)
+    _, grad = plan.likelihood_grad(dev(sky[None]), dev(dirty[None]), want_value=False)
+    grad = grad.cpu().numpy()[0]
+    _, psf, _ = plan.dirty_psf(want_dirty=False)
+    for k in range(plan.nsky):
+        P = psf[k].cpu().numpy().astype(np.float64)
+        a = rng.integers(-nx + 1, nx, npix_psf)
+        b = rng.integers(-ny + 1, ny, npix_psf)
+        refp = cdft.psf_at(obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, np.full(npix_psf, k),
+                           a, b, weights=w32, nsky=plan.nsky)
+        assert rel(P[a + nx, b + ny], refp) <= EPS, (k, rel(P[a + nx, b + ny], refp))
+        pix = rng.integers(0, nx * ny, npix_conv)
+        refc = oracle.psf_apply_at(P, sky[k], pix) - dirty[k].reshape(-1)[pix]
+        assert rel(grad[k].reshape(-1)[pix], refc) <= 2e-6, (k, rel(grad[k].reshape(-1)[pix], refc))
+
 
 @pytest.mark.slow
 def test_vla_full_size_sampled():
-    """VLA-like workload at full size (1024^2, 5,054,400 rows, w-terms): sampled outputs against
-    the FP64 direct sums, in the launch configuration the benchmark times."""
+    """VLA-like workload at full size (1024^2, 5,054,400 visibilities, w-terms, PSF convolution
+    on the 2048^2 padded grid) in the launch configuration the benchmark times: 10^4 sampled
+    visibilities of R and 10^3 sampled pixels of R^dagger N^-1 against the FP64 direct sums,
+    and the PSF and the likelihood gradient at sampled points."""
     obs = synth.observation("vla")
     plan = make_plan(obs)
     rng = np.random.default_rng(0)
-    sky = synth.sky_image(1024, 1024, seed=0)[None]
+    n = obs.nx
+    sky = synth.sky_image(n, n, seed=0)[None]
     vis = plan.degrid(dev(sky)).cpu().numpy()
-    rows = rng.integers(0, obs.nrow, 300)
-    ref = cdft.degrid_at(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, rows, np.zeros(300, int))
-    assert rel(vis[rows, 0], ref) <= 2 * EPS
+    rows = rng.integers(0, obs.nrow, NVIS_SAMPLE)
+    ref = cdft.degrid_at(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, rows,
+                         np.zeros(NVIS_SAMPLE, int))
+    assert rel(vis[rows, 0], ref) <= EPS, rel(vis[rows, 0], ref)
     y = synth.complex_gaussian((obs.nrow, 1), seed=1)
     d = plan.grid(dev(y, torch.complex64)).cpu().numpy()
-    pix = rng.integers(0, 1024 * 1024, 40)
+    pix = rng.integers(0, n * n, NPIX_SAMPLE)
     w32 = obs.weights.astype(np.float32)
-    refd = cdft.grid_at(y, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, 1024, 1024,
-                        np.zeros(40, int), pix, weights=w32)
-    assert rel(d.reshape(-1)[pix], refd) <= 2 * EPS
+    refd = cdft.grid_at(y, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, n, n,
+                        np.zeros(NPIX_SAMPLE, int), pix, weights=w32)
+    assert rel(d.reshape(-1)[pix], refd) <= EPS, rel(d.reshape(-1)[pix], refd)
+    _sampled_psf_checks(plan, obs, sky, d.reshape(1, n, n), rng, NPIX_SAMPLE, 300)
 
 
 @pytest.mark.slow
-def test_meerkat_top_channel_full_size_sampled():
-    """Largest image the API takes (4096^2, 8192^2 grid) with the MeerKAT-like top channel:
-    w-stacking over 30 planes, 7,257,600 visibilities; sampled outputs against the FP64 direct
-    sums in the benchmark's launch configuration."""
-    obs = synth.observation("meerkat1")
+def test_meerkat_all_channels_full_size_sampled():
+    """MeerKAT-like multi-channel workload at full size, the benchmark's default: 8 channels of
+    4096^2 skies (w-stacking on 8192^2 grids, 58,060,800 visibilities) and the PSF likelihood on
+    8192^2 padded grids, in the benchmark's launch configuration. 10^4 visibilities sampled over
+    all rows and channels, 10^3 pixels over all 8 images, against the FP64 direct sums; the PSF
+    images and the likelihood gradient at sampled points."""
+    obs = synth.observation("meerkat")
     plan = make_plan(obs, mfs=not obs.per_channel_sky)
-    assert plan.info()["wplanes_total"] > plan.info()["support"]
+    assert plan.nsky == 8 and plan.info()["wplanes_max"] > plan.info()["support"]
     rng = np.random.default_rng(2)
-    sky = synth.sky_image(4096, 4096, seed=3)[None]
+    n = obs.nx
+    sky = synth.random_skies(8, n, n, seed=3)
     vis = plan.degrid(dev(sky)).cpu().numpy()
-    rows = rng.integers(0, obs.nrow, 120)
-    ref = cdft.degrid_at(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, rows,
-                         np.zeros(120, int))
-    assert rel(vis[rows, 0], ref) <= 2 * EPS
-    y = synth.complex_gaussian((obs.nrow, 1), seed=4)
+    rows = rng.integers(0, obs.nrow, NVIS_SAMPLE)
+    chans = rng.integers(0, 8, NVIS_SAMPLE)
+    ref = cdft.degrid_at(sky, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, rows, chans)
+    assert rel(vis[rows, chans], ref) <= EPS, rel(vis[rows, chans], ref)
+    del vis
+    y = synth.complex_gaussian((obs.nrow, 8), seed=4)
     d = plan.grid(dev(y, torch.complex64)).cpu().numpy()
-    pix = rng.integers(0, 4096 * 4096, 24)
+    imgs = rng.integers(0, 8, NPIX_SAMPLE)
+    pix = rng.integers(0, n * n, NPIX_SAMPLE)
     w32 = obs.weights.astype(np.float32)
-    refd = cdft.grid_at(y, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, 4096, 4096,
-                        np.zeros(24, int), pix, weights=w32)
-    assert rel(d.reshape(-1)[pix], refd) <= 2 * EPS
+    refd = cdft.grid_at(y, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, n, n, imgs, pix,
+                        weights=w32, nsky=8)
+    got = d.reshape(8, -1)[imgs, pix]
+    assert rel(got, refd) <= EPS, rel(got, refd)
+    _sampled_psf_checks(plan, obs, sky, d, rng, 200, 40)

@@ -180,6 +180,18 @@ def test_psf_apply_equals_scipy_linear_convolution():
     assert _rel(oracle.psf_apply(P[None], s[None])[0], ref) < 1e-12
 
 
+def test_sampled_psf_convolution_equals_scipy_linear_convolution():
+    """psf_apply_at (single output pixels, for large images) against the same library
+    convolution, at every pixel of a small rectangular image including its corners."""
+    rng = np.random.default_rng(12)
+    nx, ny = 7, 12
+    P = rng.standard_normal((2 * nx, 2 * ny))
+    s = rng.standard_normal((nx, ny))
+    ref = scipy.signal.convolve2d(s, P, mode="full")[nx:2 * nx, ny:2 * ny]
+    got = oracle.psf_apply_at(P, s, np.arange(nx * ny)).reshape(nx, ny)
+    assert _rel(got, ref) < 1e-12
+
+
 # ---------------------------------------------------- reduced padding (truncated PSF, Sec. 3.3.2)
 
 def test_truncated_psf_with_full_padding_is_the_exact_convolution():

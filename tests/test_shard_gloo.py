@@ -86,3 +86,47 @@ def test_shard_range_covers_everything_once(n, world):
         assert 0 <= a <= b <= n
         seen.extend(range(a, b))
     assert seen == list(range(n))
+
+
+def _channel_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    from paper_2406_09144_gb300 import synth
+    from paper_2406_09144_gb300.shard import channel_slice
+    obs = synth.random_observation(80, 4, 10, 10, 2e-2, seed=9, wmax_cycles=1.0,
+                                   per_channel_sky=True)
+    vis = synth.complex_gaussian((obs.nrow, obs.nchan), seed=10)
+    c0, c1 = channel_shard(obs.nchan, world, rank)
+    mine = channel_slice(obs, c0, c1)
+    # each rank images its own channels from its own data: no collective on the data path
+    dirty = oracle.grid(vis[:, c0:c1], mine.uvw, mine.freqs, mine.pixsize, mine.pixsize, 10, 10,
+                        weights=mine.weights, nsky=c1 - c0)
+    nvis = torch.tensor([float(mine.nvis)], dtype=torch.float64)
+    dist.all_reduce(nvis)  # bench-side bookkeeping only: the job's visibility count
+    out[rank] = (dirty, (c0, c1), float(nvis.item()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_channel_sharded_imaging_equals_single_process():
+    """The benchmark's multi-GPU split of per-channel skies: ranks take disjoint channel ranges
+    (shard.channel_slice), image them independently, and together give the single-process
+    per-channel result; the visibility counts add up to the whole job's."""
+    import oracle
+    from paper_2406_09144_gb300 import synth
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_channel_worker, args=(world, _free_port(), out), nprocs=world,
+                       start_method="spawn", join=True)
+    obs = synth.random_observation(80, 4, 10, 10, 2e-2, seed=9, wmax_cycles=1.0,
+                                   per_channel_sky=True)
+    vis = synth.complex_gaussian((obs.nrow, obs.nchan), seed=10)
+    ref = oracle.grid(vis, obs.uvw, obs.freqs, obs.pixsize, obs.pixsize, 10, 10,
+                      weights=obs.weights, nsky=4)
+    got = np.concatenate([out[r][0] for r in range(world)])
+    assert [out[r][1] for r in range(world)] == [(0, 2), (2, 4)]
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    assert all(out[r][2] == obs.nvis for r in range(world))
