@@ -1101,16 +1101,16 @@ int selftest_wait_timeout(int* status, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------ grid
 // Gridder: one warp spreads one visibility at a time, lane l owning footprint cells
-// l, l + 32, ... (row a = idx / W, column b = idx % W), into the warp's private shared-memory
-// sub-grid, so no two threads ever update the same cell concurrently and no shared atomics are
-// needed. Lanes 0..W-1 evaluate phi(du - a), lanes W..2W-1 phi(dv - b); every lane fetches its
-// two factors by shuffle. The warps' sub-grids are summed at the end and the non-zero cells
-// added to the global grid with one vector atomic each.
+// l, l + 32, ... (row a = idx / W, column b = idx % W). Runs of visibilities with the same
+// footprint origin are summed in registers and added to the CTA's one shared-memory sub-grid
+// with shared-memory atomics (float adds, or 64-bit integer adds in fixed point under
+// FR_DETERMINISTIC); the non-zero cells are then added to the global grid with one vector
+// atomic each. One sub-grid per CTA (11.5 KB at W = 7) keeps several CTAs resident per SM.
 constexpr int GRID_WARPS = 8;
 
-template <int W>
+template <int W, bool DET>
 constexpr size_t grid_smem_bytes() {
-  return (size_t)GRID_WARPS * (TILE + W - 1) * ((TILE + W) & ~1) * sizeof(float2);
+  return (size_t)(TILE + W - 1) * ((TILE + W) & ~1) * (DET ? sizeof(longlong2) : sizeof(float2));
 }
 
 // Counting sort of a work item's visibilities by footprint origin (rv * TILE + ru) into
@@ -1246,7 +1246,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   constexpr int NIT = (CELLS + 31) / 32;
   constexpr int NT = GRID_WARPS * 32;
   constexpr int NKEY = TILE * TILE;
-  // [GRID_WARPS][SUB] per-warp sub-grids; DET: one fixed-point sub-grid [SUB] (longlong2)
+  // one sub-grid [SUB] per CTA: float2, or fixed-point longlong2 under DET
   extern __shared__ __align__(16) float2 sub[];
   longlong2* subq = reinterpret_cast<longlong2*>(sub);
   __shared__ int hist[NKEY];
@@ -1258,11 +1258,10 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   const int n = it.y;
   // each warp takes a contiguous segment of the sorted order, a multiple of 32 long
   const int seg = (((n + GRID_WARPS - 1) / GRID_WARPS) + 31) & ~31;
-  const int nused = n > 0 ? (n + seg - 1) / seg : 0;
   if constexpr (DET) {
     for (int i = threadIdx.x; i < SUB; i += NT) subq[i] = longlong2{0, 0};
   } else {
-    for (int i = threadIdx.x; i < nused * SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < SUB; i += NT) sub[i] = make_float2(0.f, 0.f);
   }
   const float scalef = DET ? (float)det_scale(det.maxbits, det.n) : 0.f;
   if (presorted)
@@ -1270,7 +1269,6 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   else
     sort_by_origin<STACK_CHUNK>(m, it, tu, tv, hist, order, wsum);
 
-  float2* mysub = sub + warp * SUB;
   int off[NIT], cu[NIT], cv[NIT];
 #pragma unroll
   for (int k = 0; k < NIT; ++k) {
@@ -1302,11 +1300,9 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
         if constexpr (DET) {
           fixed_add_q(subq + cur + off[k], accq[k]);
         } else {
-          float2* c = mysub + cur + off[k];
-          float2 g = *c;
-          g.x += acc[k].x;
-          g.y += acc[k].y;
-          *c = g;
+          float* c = reinterpret_cast<float*>(sub + cur + off[k]);
+          atomicAdd(c, acc[k].x);
+          atomicAdd(c + 1, acc[k].y);
         }
       }
   };
@@ -1382,13 +1378,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
       const longlong2 q = subq[idx];
       if (q.x != 0 || q.y != 0) fixed_add_q(&det.gridq[(size_t)gv * Nu + gu], q);
     } else {
-      // the warps' sub-grids are summed in warp order
-      float2 acc = sub[idx];
-      for (int w = 1; w < nused; ++w) {
-        const float2 o = sub[w * SUB + idx];
-        acc.x += o.x;
-        acc.y += o.y;
-      }
+      const float2 acc = sub[idx];
       if (acc.x == 0.f && acc.y == 0.f) continue;
       atomicAdd(&grid[(size_t)gv * Nu + gu], acc);
     }
@@ -1487,7 +1477,7 @@ template <int W, bool DET>
 static int launch_grid_det(const Geometry& geo, const VisLayout& lay, int64_t i0, int64_t n, int p,
                            const float2* y, float2* grid, const DetArgs& det, cudaStream_t s) {
   MetaPtrs m{lay.cell, lay.du, lay.dv, lay.dw, lay.ph, lay.perm};
-  constexpr size_t smem = grid_smem_bytes<W>();
+  constexpr size_t smem = grid_smem_bytes<W, DET>();
   static bool attr = false;
   if (!attr) {
     FR_CUDA_TRY(cudaFuncSetAttribute(grid_kernel<W, DET>,
