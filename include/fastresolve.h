@@ -203,6 +203,30 @@ int fr_fast_likelihood_grad_resid(fr_plan_t plan, const float *sky, const float 
                                   int32_t batch, float *grad, float *ninv_resid, double *value,
                                   void *stream);
 
+/* PSF convolutions of several plans in one launch per pass (serving: many jobs' minor-cycle
+ * convolutions of Sec. 3.3.2 batched into shared launches). The plans must have PSFs and equal
+ * nx, ny and PSF padding (fr_psf_padding); their images form one flat batch, and each image is
+ * convolved with its own plan's PSF exactly as fr_psf_apply does it (same passes, same
+ * arithmetic).
+ *   plans    host array of nplans (1 <= nplans <= 16) plan handles
+ *   skies    host array of device pointers, plan j's float32 [batches[j]][nsky_j][nx][ny]
+ *   batches  host int32 [nplans], each >= 1
+ *   outs     host array of device pointers, plan j's output, same layout as its sky
+ *   scratch  device memory owned by the caller, 16-byte aligned, at least
+ *            fr_psf_group_scratch_bytes bytes; the call allocates nothing
+ * FR_EINVAL for mismatched plans, null pointers or a short or misaligned scratch. */
+int fr_psf_group_scratch_bytes(const fr_plan_t *plans, int32_t nplans, const int32_t *batches,
+                               size_t *bytes);
+int fr_psf_apply_group(const fr_plan_t *plans, int32_t nplans, const float *const *skies,
+                       const int32_t *batches, float *const *outs, void *scratch,
+                       size_t scratch_bytes, void *stream);
+
+/* Allocates the per-stream workspace of `plan` for calls on `stream` (fr_degrid, fr_grid,
+ * fr_dirty_psf and the PSF convolutions of up to `batch` skies) without computing anything, so
+ * that later calls on that stream allocate nothing (a server prepares a job this way before
+ * capturing its calls in a CUDA graph). Optional: the calls allocate on first use otherwise. */
+int fr_plan_prepare(fr_plan_t plan, int32_t batch, void *stream);
+
 /* Allocation-free PSF convolution. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory, such as code embedded in an application that owns
  * the whole device-memory budget through its own pool, or code running where a cudaMalloc would
@@ -272,8 +296,9 @@ const char *fr_profile_category(int32_t cat);
 /* Host-only check of the FFT passes' Stockham index and butterfly arithmetic: transforms
  * `batch` sequences of n complex values in place (interleaved float32 re, im) on the CPU
  * with the same stage code and radix schedule the kernels use. dir = -1 forward, +1 inverse
- * (unnormalised). Returns FR_EINVAL unless 2 <= n <= 16384 with n = 2^k 3^a 5^b. Test
- * support; needs no GPU. */
+ * (unnormalised), on the schedule of 16 points per thread; dir = -2 / +2 the same on the
+ * schedule of 32 points per thread (a radix-32 opening stage for powers of two >= 512).
+ * Returns FR_EINVAL unless 2 <= n <= 16384 with n = 2^k 3^a 5^b. Test support; needs no GPU. */
 int fr_selftest_fft_host(float *data, int32_t n, int32_t batch, int32_t dir);
 
 /* Test support for the error path of the bounded device waits (no counterpart in the paper):

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <algorithm>
 #include <memory>
+#include <vector>
 
 #include "fr_internal.cuh"
 
@@ -959,18 +960,19 @@ static void host_stage(const float2* in, float2* out, const float2* tw, int L, i
 }
 
 template <int DIR>
-static void host_fft(float2* buf, float2* tmp, const float2* tw, int L) {
+static void host_fft(float2* buf, float2* tmp, const float2* tw, int L, int P) {
   int Ns = 1;
   float2* a = buf;
   float2* b = tmp;
-  for (int st = 0; st < fft_num_stages(L); ++st) {
-    const int R = fft_radix(L, st);
+  for (int st = 0; st < fft_num_stages(L, P); ++st) {
+    const int R = fft_radix(L, st, P);
     switch (R) {
       case 2: host_stage<2, DIR>(a, b, tw, L, Ns); break;
       case 3: host_stage<3, DIR>(a, b, tw, L, Ns); break;
       case 4: host_stage<4, DIR>(a, b, tw, L, Ns); break;
       case 5: host_stage<5, DIR>(a, b, tw, L, Ns); break;
       case 8: host_stage<8, DIR>(a, b, tw, L, Ns); break;
+      case 32: host_stage<32, DIR>(a, b, tw, L, Ns); break;
       default: host_stage<16, DIR>(a, b, tw, L, Ns); break;
     }
     Ns *= R;
@@ -1176,6 +1178,113 @@ int fr_psf_apply(fr_plan_t p, const float* sky, int32_t batch, float* out, void*
     return FR_EINVAL;
   }
   return psf_common(p, sky, batch, out, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+// plans of one grouped PSF convolution: 1..16 of them, with PSFs, equal image sizes and padded
+// lengths; total images of the group in *nimg
+static int psf_group_check(const fr_plan_t* plans, int32_t n, const int32_t* batches,
+                           int* nimg) {
+  if (!plans || !batches || n < 1 || n > 16) {
+    set_error("a grouped PSF convolution takes 1 to 16 plans with their batches");
+    return FR_EINVAL;
+  }
+  *nimg = 0;
+  for (int j = 0; j < n; ++j) {
+    const fr_plan* p = plans[j];
+    if (!p || batches[j] < 1) {
+      set_error("plan %d is null or its batch is < 1", j);
+      return FR_EINVAL;
+    }
+    if (!p->has_psf) {
+      set_error("plan %d was created with FR_NO_PSF", j);
+      return FR_EINVAL;
+    }
+    if (p->geo.nx != plans[0]->geo.nx || p->geo.ny != plans[0]->geo.ny ||
+        p->psf_lx != plans[0]->psf_lx || p->psf_ly != plans[0]->psf_ly) {
+      set_error("plan %d differs from plan 0 in image size or PSF padding", j);
+      return FR_EINVAL;
+    }
+    *nimg += batches[j] * p->nsky;
+  }
+  return FR_OK;
+}
+
+int fr_psf_group_scratch_bytes(const fr_plan_t* plans, int32_t nplans, const int32_t* batches,
+                               size_t* bytes) {
+  int nimg = 0;
+  FR_TRY(psf_group_check(plans, nplans, batches, &nimg));
+  if (!bytes) {
+    set_error("bytes must be non-null");
+    return FR_EINVAL;
+  }
+  *bytes = psf_h_need(plans[0], nimg) * sizeof(float2);
+  return FR_OK;
+}
+
+int fr_psf_apply_group(const fr_plan_t* plans, int32_t nplans, const float* const* skies,
+                       const int32_t* batches, float* const* outs, void* scratch,
+                       size_t scratch_bytes, void* stream) {
+  int nimg = 0;
+  FR_TRY(psf_group_check(plans, nplans, batches, &nimg));
+  if (!skies || !outs || !scratch) {
+    set_error("skies, outs and scratch must be non-null");
+    return FR_EINVAL;
+  }
+  const fr_plan* p0 = plans[0];
+  const size_t need = psf_h_need(p0, nimg) * sizeof(float2);
+  if (scratch_bytes < need || ((uintptr_t)scratch & 15)) {
+    set_error("scratch must be 16-byte aligned and hold %zu bytes (got %zu)", need, scratch_bytes);
+    return FR_EINVAL;
+  }
+  std::vector<const float*> tr(nplans);
+  std::vector<int> nsky(nplans), ni(nplans);
+  for (int j = 0; j < nplans; ++j) {
+    if (!skies[j] || !outs[j]) {
+      set_error("sky and out of plan %d must be non-null", j);
+      return FR_EINVAL;
+    }
+    tr[j] = plans[j]->transfer;
+    nsky[j] = plans[j]->nsky;
+    ni[j] = batches[j] * plans[j]->nsky;
+  }
+  PsfGroupArgs g;
+  g.njobs = nplans;
+  g.nx = p0->geo.nx;
+  g.ny = p0->geo.ny;
+  g.lx = p0->psf_lx;
+  g.ly = p0->psf_ly;
+  g.hp = psf_pitch(g.ly);
+  g.sky = skies;
+  g.out = outs;
+  g.transfer = tr.data();
+  g.nsky = nsky.data();
+  g.nimg = ni.data();
+  float2* h = (float2*)scratch;
+  float2* ht = h + (size_t)nimg * g.nx * g.hp;
+  fr_plan* pm = const_cast<fr_plan*>(p0);
+  return psf_group_passes(g, h, ht, twiddles_of(pm, g.ly), twiddles_of(pm, g.lx),
+                          (cudaStream_t)stream);
+}
+
+int fr_plan_prepare(fr_plan_t p, int32_t batch, void* stream) {
+  if (!p || batch < 1) {
+    set_error("plan must be non-null and batch >= 1");
+    return FR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w;
+  FR_TRY(get_ws(p, s, &w));
+  const Geometry& g = p->geo;
+  if (use_term_grids(g)) {
+    FR_TRY(ws_reserve_terms(g, w, s));
+    FR_TRY(ws_reserve_terms_g(g, w, s));
+  }
+  if (use_stack(p)) FR_TRY(ws_reserve_stack(p, w));
+  if (p->flags & FR_DETERMINISTIC)
+    FR_TRY(ws_reserve_det(w, (use_term_grids(g) ? (size_t)g.nterms : 1) * g.Nu * g.Nv, s));
+  if (p->has_psf) FR_TRY(ws_reserve_h(w, psf_h_need(p, batch * p->nsky)));
+  FR_TRY(ws_reserve_red(w, (size_t)std::max(batch, 4)));
+  return FR_OK;
 }
 
 int fr_psf_set_padding(fr_plan_t p, int32_t lx, int32_t ly, void* stream) {
@@ -1556,7 +1665,7 @@ int fr_selftest_wait_timeout(fr_plan_t p, void* stream) {
 }
 
 int fr_selftest_fft_host(float* data, int32_t n, int32_t batch, int32_t dir) {
-  if (!data || n < 2 || n > 16384 || batch < 1 || (dir != 1 && dir != -1) ||
+  if (!data || n < 2 || n > 16384 || batch < 1 || (dir != 1 && dir != -1 && dir != 2 && dir != -2) ||
       strip_factor(strip_factor(odd_part(n), 5), 3) != 1) {
     set_error("bad arguments to fr_selftest_fft_host");
     return FR_EINVAL;
@@ -1570,10 +1679,11 @@ int fr_selftest_fft_host(float* data, int32_t n, int32_t batch, int32_t dir) {
   for (int q = 0; q < batch; ++q) {
     float2* x = reinterpret_cast<float2*>(data) + (size_t)q * L;
     for (int i = 0; i < L; ++i) a[spad(i)] = x[i];
+    const int P = (dir == 2 || dir == -2) ? 32 : 16;
     if (dir < 0)
-      host_fft<-1>(a.data(), b.data(), tw.data(), L);
+      host_fft<-1>(a.data(), b.data(), tw.data(), L, P);
     else
-      host_fft<1>(a.data(), b.data(), tw.data(), L);
+      host_fft<1>(a.data(), b.data(), tw.data(), L, P);
     for (int i = 0; i < L; ++i) x[i] = a[spad(i)];
   }
   return FR_OK;

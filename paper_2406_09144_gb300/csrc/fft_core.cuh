@@ -1,4 +1,4 @@
-// Radix-2/3/4/5/8/16 Stockham FFT building blocks shared by every FFT pass kernel.
+// Radix-2/3/4/5/8/16/32 Stockham FFT building blocks shared by every FFT pass kernel.
 //
 // The FFT passes implement the FFT[...] / FFT^-1[...] of the padded PSF convolution
 // (Sec. 3.3.2) and the oversampled-grid transforms of the measurement operator R (Eq. rime)
@@ -41,7 +41,7 @@ FR_HD float2 mul_i(float2 a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// In-register DFTs of size 2, 3, 4, 5, 8, 16 with exponent sign DIR (-1 forward, +1 inverse).
+// In-register DFTs of size 2, 3, 4, 5, 8, 16, 32 with exponent sign DIR (-1 forward, +1 inverse).
 // Input and output in natural order.
 // ---------------------------------------------------------------------------------------
 template <int DIR>
@@ -134,6 +134,53 @@ FR_HD void dft16(float2* v) {
   }
 }
 
+// a * exp(DIR 2 pi i k / 32) for k in [0, 16): cos and sin of k pi / 16, folded after unrolling
+template <int DIR>
+FR_HD float2 tw32(float2 a, int k) {
+  constexpr float C[16] = {1.f,
+                           0.98078528040323044913f,
+                           0.92387953251128675613f,
+                           0.83146961230254523708f,
+                           0.70710678118654752440f,
+                           0.55557023301960222474f,
+                           0.38268343236508977173f,
+                           0.19509032201612826785f,
+                           0.f,
+                           -0.19509032201612826785f,
+                           -0.38268343236508977173f,
+                           -0.55557023301960222474f,
+                           -0.70710678118654752440f,
+                           -0.83146961230254523708f,
+                           -0.92387953251128675613f,
+                           -0.98078528040323044913f};
+  if (k == 0) return a;
+  if (k == 8) return mul_i<DIR>(a);
+  const float c = C[k];
+  // sin(k pi/16) = -cos((k+8) pi/16) for k < 8 and cos((k-8) pi/16) for k > 8
+  const float s = DIR * C[(k + 8) & 15] * (k < 8 ? -1.f : 1.f);
+  return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// DFT_32 as 2 x 16 (decimation in time): E, O = DFT_16 of the even and odd inputs,
+// X_k = E_k + w^k O_k, X_(k+16) = E_k - w^k O_k, w = exp(DIR 2 pi i / 32)
+template <int DIR>
+FR_HD void dft32(float2* v) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) {
+    e[n] = v[2 * n];
+    o[n] = v[2 * n + 1];
+  }
+  dft16<DIR>(e);
+  dft16<DIR>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float2 t = tw32<DIR>(o[k], k);
+    v[k] = cadd(e[k], t);
+    v[k + 16] = csub(e[k], t);
+  }
+}
+
 // DFT_3: X_k = sum_n x_n w^(nk), w = exp(DIR 2 pi i / 3) = -1/2 + DIR i sqrt(3)/2
 template <int DIR>
 FR_HD void dft3(float2* v) {
@@ -180,8 +227,10 @@ FR_HD void dft_r(float2* v) {
     dft4<DIR>(v[0], v[1], v[2], v[3]);
   } else if constexpr (R == 8) {
     dft8<DIR>(v);
+  } else if constexpr (R == 32) {
+    dft32<DIR>(v);
   } else {
-    static_assert(R == 16, "radix must be 2, 3, 4, 5, 8 or 16");
+    static_assert(R == 16, "radix must be 2, 3, 4, 5, 8, 16 or 32");
     dft16<DIR>(v);
   }
 }
@@ -206,13 +255,25 @@ constexpr bool fft_length_ok(int L) {
   return L >= 16 && L % 16 == 0 && strip_factor(strip_factor(odd_part(L), 5), 3) == 1;
 }
 constexpr int odd_stages(int L) { return count_factor(odd_part(L), 5) + count_factor(odd_part(L), 3); }
-constexpr int fft_num_stages(int L) { return odd_stages(L) + num_stages(pow2_exp(L)); }
-constexpr int fft_radix(int L, int s) {
-  return s < count_factor(odd_part(L), 5) ? 5
-         : s < odd_stages(L)              ? 3
-                                          : 1 << stage_bits(pow2_exp(L), s - odd_stages(L));
+// Schedules for P points per thread (16, or 32 for power-of-two lengths of at least 512): with
+// P = 32 the power-of-two part opens with one radix-32 stage (8192 = 32 x 16 x 16: three stages
+// instead of four of at most 16), with P = 16 every stage is of radix 16 or less.
+constexpr int lead_bits(int L, int P) {
+  return (P == 32 && odd_part(L) == 1 && pow2_exp(L) >= 9) ? 5 : 0;
 }
-constexpr int fft_ns_before(int L, int st) { return st == 0 ? 1 : fft_radix(L, st - 1) * fft_ns_before(L, st - 1); }
+constexpr int fft_num_stages(int L, int P = 16) {
+  return odd_stages(L) + (lead_bits(L, P) ? 1 : 0) + num_stages(pow2_exp(L) - lead_bits(L, P));
+}
+constexpr int fft_radix(int L, int s, int P = 16) {
+  return s < count_factor(odd_part(L), 5)                ? 5
+         : s < odd_stages(L)                             ? 3
+         : (lead_bits(L, P) > 0 && s == odd_stages(L))   ? (1 << lead_bits(L, P))
+                                                         : 1 << stage_bits(pow2_exp(L) - lead_bits(L, P),
+                                                                           s - odd_stages(L) - (lead_bits(L, P) ? 1 : 0));
+}
+constexpr int fft_ns_before(int L, int st, int P = 16) {
+  return st == 0 ? 1 : fft_radix(L, st - 1, P) * fft_ns_before(L, st - 1, P);
+}
 
 // Shared-memory padding: one float2 of padding after every 16 elements breaks the
 // power-of-two strides of the Stockham scatter.

@@ -1,8 +1,8 @@
 // Shared-memory FFT engine and the generic FFT pass kernel.
 //
 // Every pass reads the sequences it transforms from contiguous memory: a CTA loads B
-// sequences of length L (a supported length of fft_core.cuh; register-staged, 16 complex values per thread, all loads in
-// flight before the first shared-memory store), runs the Stockham stages of fft_core.cuh
+// sequences of length L (a supported length of fft_core.cuh; register-staged, 16 complex values
+// per thread, 32 at L = 8192, all loads in flight before the first shared-memory store), runs the Stockham stages of fft_core.cuh
 // on them in shared memory (sequence b at b * LP, element i at spad(i)), and hands them to the
 // pass's store, which writes either along the sequence (row-major) or across the B sequences
 // (transposed: consecutive threads write consecutive sequences of one output index). The
@@ -15,14 +15,18 @@ namespace fr {
 
 constexpr int pow2_floor(int x) { return x < 2 ? 1 : 2 * pow2_floor(x / 2); }
 
-template <int LEN>
+// Pass configuration of length LEN at P points per thread (16; 32 for the ops that ask for it
+// at L = 8192, see op_pts).
+template <int LEN, int P = 16>
 struct FftCfg {
   static_assert(fft_length_ok(LEN), "unsupported FFT length");
+  static_assert(P == 16 || P == 32, "16 or 32 points per thread");
   static constexpr int L = LEN;
   // L >= 8192 runs one sequence per CTA so that two CTAs share an SM and overlap their load,
   // transform and store phases; 4096 <= L < 8192 keeps two (16-byte transposed stores)
   static constexpr int B = (L >= 8192) ? 1 : (L >= 4096 ? 2 : pow2_floor(4096 / L));
-  static constexpr int NT = (B * L) / 16;     // threads: 16 points each
+  static constexpr int PTS = P;
+  static constexpr int NT = (B * L) / PTS;
   static constexpr int LP = spad_len(L) + 1;  // odd stride between sequences
   static constexpr size_t SMEM = size_t(B) * LP * sizeof(float2);
   // CTAs per SM the register budget is sized for: four at L = 2048 (64 registers, no spills);
@@ -32,21 +36,25 @@ struct FftCfg {
   // the 3 2^k and 5 2^k lengths (160- to 768-thread CTAs) target 64 registers outright
   // (measured 18 % faster at 1536 than the power-of-two rule, which let 110 registers through)
   static constexpr bool POW2 = (L & (L - 1)) == 0;
-  static constexpr int MINB =
-      POW2 ? cap(NT >= 1024 ? 1 : (NT >= 512 || L < 2048 ? 2 : 4)) : FIT64;
-  static constexpr int MINB_SUM = cap(NT >= 512 ? 1 : 2);  // multi-output passes
+  // 32 points a thread hold 64 registers of data alone: two CTAs per SM (128 registers)
+  static constexpr int MINB = PTS == 32 ? 2
+                              : POW2    ? cap(NT >= 1024 ? 1 : (NT >= 512 || L < 2048 ? 2 : 4))
+                                        : FIT64;
+  static constexpr int MINB_SUM = PTS == 32 ? 1 : cap(NT >= 512 ? 1 : 2);  // multi-output passes
   // two-transform passes; the mixed lengths one CTA below the 64-register count (measured
   // fastest at 1280 and 1536: 72 and 80 registers, small spills)
-  static constexpr int MINB_TWO = POW2 ? cap(NT >= 1024 ? 1 : 2) : (FIT64 > 1 ? FIT64 - 1 : 1);
+  static constexpr int MINB_TWO = PTS == 32 ? 2
+                                  : POW2    ? cap(NT >= 1024 ? 1 : 2)
+                                            : (FIT64 > 1 ? FIT64 - 1 : 1);
 };
 
-template <int L, int ST, int DIR>
+template <int L, int ST, int DIR, int P = 16>
 __device__ __forceinline__ void fft_stages(float2* s, const float2* __restrict__ tw) {
-  if constexpr (ST < fft_num_stages(L)) {
-    using C = FftCfg<L>;
+  if constexpr (ST < fft_num_stages(L, P)) {
+    using C = FftCfg<L, P>;
     constexpr int B = C::B, NT = C::NT, LP = C::LP;
-    constexpr int R = fft_radix(L, ST);
-    constexpr int NS = fft_ns_before(L, ST);
+    constexpr int R = fft_radix(L, ST, P);
+    constexpr int NS = fft_ns_before(L, ST, P);
     constexpr int LR = L / R;
     constexpr int NTASK = B * LR;
     // power-of-two radices split evenly (16 / R tasks per thread); radix 3 and 5 take
@@ -82,30 +90,31 @@ __device__ __forceinline__ void fft_stages(float2* s, const float2* __restrict__
       }
     }
     __syncthreads();
-    fft_stages<L, ST + 1, DIR>(s, tw);
+    fft_stages<L, ST + 1, DIR, P>(s, tw);
   }
 }
 
-// The first stage of the power-of-two lengths whose schedule opens with radix 16 runs on the
-// values a thread loaded itself: thread t takes sequence b = t / (L/16) and task j = t % (L/16),
-// loads x[j + k L/16] (k < 16, consecutive threads on consecutive elements), transforms them
-// in registers and writes the stage's outputs, so that stage costs no shared-memory round trip
-// and no barrier. Other lengths load idx = t + k NT (sequence idx / L, element idx % L) and run
-// every stage in shared memory.
-template <int L>
+// The first stage of the power-of-two lengths whose schedule opens with a radix equal to the
+// points per thread P (16, or 32 at 8192) runs on the values a thread loaded itself: thread t
+// takes sequence b = t / (L/P) and task j = t % (L/P), loads x[j + k L/P] (k < P, consecutive
+// threads on consecutive elements), transforms them in registers and writes the stage's
+// outputs, so that stage costs no shared-memory round trip and no barrier. Other lengths load
+// idx = t + k NT (sequence idx / L, element idx % L) and run every stage in shared memory.
+template <int L, int P = 16>
 constexpr bool fuse_first() {
-  return FftCfg<L>::POW2 && fft_radix(L, 0) == 16 && FftCfg<L>::B * L / FftCfg<L>::NT == 16;
+  using C = FftCfg<L, P>;
+  return C::POW2 && fft_radix(L, 0, P) == P && C::B * L / C::NT == P;
 }
 
 // sequence (within the CTA) and element of the k-th value a thread loads
-template <int L>
+template <int L, int P = 16>
 __device__ __forceinline__ void load_pos(int k, int* b, int* i) {
-  if constexpr (fuse_first<L>()) {
-    constexpr int Q = L / 16;
+  if constexpr (fuse_first<L, P>()) {
+    constexpr int Q = L / P;
     *b = threadIdx.x / Q;
     *i = threadIdx.x % Q + k * Q;
   } else {
-    const int idx = threadIdx.x + k * FftCfg<L>::NT;
+    const int idx = threadIdx.x + k * FftCfg<L, P>::NT;
     *b = idx / L;
     *i = idx % L;
   }
@@ -113,23 +122,23 @@ __device__ __forceinline__ void load_pos(int k, int* b, int* i) {
 
 // The transform of the loaded values r (load_pos order) into shared memory, in natural order;
 // `landed` runs once every thread's values are in shared memory (before the remaining stages).
-template <int L, int DIR, class F>
+template <int L, int DIR, int P = 16, class F>
 __device__ __forceinline__ void fft_from_regs(float2* s, float2* r, const float2* __restrict__ tw,
                                               F landed) {
-  using C = FftCfg<L>;
-  if constexpr (fuse_first<L>()) {
-    constexpr int Q = L / 16;
+  using C = FftCfg<L, P>;
+  if constexpr (fuse_first<L, P>()) {
+    constexpr int Q = L / P;
     const int b = threadIdx.x / Q, j = threadIdx.x % Q;
-    float2 v[16];
+    float2 v[P];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = r[k];
-    dft16<DIR>(v);
+    for (int k = 0; k < P; ++k) v[k] = r[k];
+    dft_r<P, DIR>(v);
     float2* dst = s + b * C::LP;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) dst[spad(16 * j + k)] = v[k];
+    for (int k = 0; k < P; ++k) dst[spad(P * j + k)] = v[k];
     __syncthreads();
     landed();
-    fft_stages<L, 1, DIR>(s, tw);
+    fft_stages<L, 1, DIR, P>(s, tw);
   } else {
     constexpr int PER = C::B * L / C::NT;
 #pragma unroll
@@ -139,8 +148,17 @@ __device__ __forceinline__ void fft_from_regs(float2* s, float2* r, const float2
     }
     __syncthreads();
     landed();
-    fft_stages<L, 0, DIR>(s, tw);
+    fft_stages<L, 0, DIR, P>(s, tw);
   }
+}
+
+// Points per thread of an op's pass at length L: the two-transform passes at 8192 (forward,
+// pointwise product, inverse in one CTA) run 32 (three stages per transform; measured 25 %
+// faster than four), everything else 16 (twice the resident warps for the latency of the
+// loads, measured faster for the single-transform passes).
+template <int L, class Op>
+constexpr int op_pts() {
+  return (Op::TWO && L == 8192) ? 32 : 16;
 }
 
 // Read-only view of one sequence in shared memory.
@@ -196,10 +214,12 @@ __device__ __forceinline__ const float2* cluster_map(const float2* p, uint32_t r
 //   double store(int seq, int o, SeqView v)   o < nout(); per-thread results are summed
 //   void finish(int seq0, double acc)
 template <int LEN, int DIR, int DIR2, class Op>
-__global__ void __launch_bounds__(FftCfg<LEN>::NT,
-                                  Op::TWO ? FftCfg<LEN>::MINB_TWO : FftCfg<LEN>::MINB)
+__global__ void __launch_bounds__(FftCfg<LEN, op_pts<LEN, Op>()>::NT,
+                                  Op::TWO ? FftCfg<LEN, op_pts<LEN, Op>()>::MINB_TWO
+                                          : FftCfg<LEN, op_pts<LEN, Op>()>::MINB)
     fft_pass_kernel(Op op, const float2* __restrict__ tw) {
-  using C = FftCfg<LEN>;
+  constexpr int P = op_pts<LEN, Op>();
+  using C = FftCfg<LEN, P>;
   constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
   constexpr int PER = B * L / NT;
   extern __shared__ float2 smem[];
@@ -209,16 +229,16 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT,
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     int b, i;
-    load_pos<L>(k, &b, &i);
+    load_pos<L, P>(k, &b, &i);
     r[k] = (seq0 + b < nseq) ? op.load(seq0 + b, i) : make_float2(0.f, 0.f);
   }
-  fft_from_regs<L, DIR>(smem, r, tw, [&] {
+  fft_from_regs<L, DIR, P>(smem, r, tw, [&] {
     if (seq0 < nseq) op.after_load(seq0, min(B, nseq - seq0));
   });
   if constexpr (Op::TWO) {
     op.template mid<B, NT, L, LP>(smem, seq0);
     __syncthreads();
-    fft_stages<L, 0, DIR2>(smem, tw);
+    fft_stages<L, 0, DIR2, P>(smem, tw);
   }
   const int nout = op.nout();
   double acc = 0.0;
@@ -264,7 +284,7 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT,
 
 template <int LEN, int DIR, int DIR2, class Op>
 int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
-  using C = FftCfg<LEN>;
+  using C = FftCfg<LEN, op_pts<LEN, Op>()>;
   const int nblk = (op.nseq() + C::B - 1) / C::B;
   if (nblk == 0 || nimg == 0) return FR_OK;
   auto kern = fft_pass_kernel<LEN, DIR, DIR2, Op>;

@@ -83,8 +83,9 @@ FFT_LENGTHS = [1 << lg for lg in range(1, 15)] + [3, 5, 6, 10, 48, 80, 96, 1536,
 
 
 @pytest.mark.parametrize("n", FFT_LENGTHS)
-@pytest.mark.parametrize("direction", [-1, 1])
+@pytest.mark.parametrize("direction", [-1, 1, -2, 2])
 def test_host_fft_stages_match_numpy(lib, n, direction):
+    """Both stage schedules (16 points per thread, and +-2: 32 with a radix-32 opening stage)."""
     rng = np.random.default_rng(n)
     x = (rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))).astype(np.complex64)
     got = binding.selftest_fft_host(x, direction)
