@@ -24,7 +24,8 @@ EXPORTS = ["fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_app
            "fr_selftest_fft_host", "fr_psf_convolve_noalloc", "fr_noise_fit", "fr_noise_kernel",
            "fr_noise_apply_inverse", "fr_fast_likelihood_grad", "fr_psf_set_padding",
            "fr_psf_padding", "fr_degrid_weighted", "fr_fast_likelihood_grad_resid",
-           "fr_selftest_wait_timeout"]
+           "fr_selftest_wait_timeout", "fr_psf_group_scratch_bytes", "fr_psf_apply_group",
+           "fr_plan_prepare"]
 
 
 class FastResolveError(RuntimeError):
@@ -87,6 +88,9 @@ def load(path: str = LIB_PATH):
     lib.fr_launch_count.restype = ctypes.c_uint64
     lib.fr_selftest_fft_host.argtypes = [P, I32, I32, I32]
     lib.fr_selftest_wait_timeout.argtypes = [P, P]
+    lib.fr_psf_group_scratch_bytes.argtypes = [P, I32, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.fr_psf_apply_group.argtypes = [P, I32, P, P, P, P, ctypes.c_size_t, P]
+    lib.fr_plan_prepare.argtypes = [P, I32, P]
     lib.fr_profile_enable.argtypes = [ctypes.c_int]
     lib.fr_profile_enable.restype = None
     lib.fr_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -99,7 +103,8 @@ def load(path: str = LIB_PATH):
     for name in ("fr_plan_create", "fr_degrid", "fr_grid", "fr_dirty_psf", "fr_psf_apply",
                  "fr_likelihood_grad", "fr_major_cycle", "fr_plan_get_info", "fr_plan_footprint",
                  "fr_plan_check", "fr_selftest_fft_host", "fr_psf_set_padding", "fr_psf_padding",
-                 "fr_degrid_weighted", "fr_fast_likelihood_grad_resid", "fr_selftest_wait_timeout"):
+                 "fr_degrid_weighted", "fr_fast_likelihood_grad_resid", "fr_selftest_wait_timeout",
+                 "fr_psf_group_scratch_bytes", "fr_psf_apply_group", "fr_plan_prepare"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -108,6 +113,39 @@ def load(path: str = LIB_PATH):
 def check(code: int):
     if code != 0:
         raise FastResolveError(code, load().fr_last_error().decode(errors="replace"))
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])
+    return arr
+
+
+def psf_group_scratch_bytes(plans, batches) -> int:
+    """Scratch bytes of psf_apply_group for these plans and batches."""
+    hs = _ptr_array([p._h.value for p in plans])
+    bs = (ctypes.c_int32 * len(batches))(*[int(b) for b in batches])
+    n = ctypes.c_size_t()
+    check(load().fr_psf_group_scratch_bytes(hs, len(plans), bs, ctypes.byref(n)))
+    return int(n.value)
+
+
+def psf_apply_group(plans, skies, outs, scratch, stream=None):
+    """PSF convolutions of several plans (equal image size and PSF padding) in one launch per
+    pass: skies[j], outs[j] [batch_j, nsky_j, nx, ny] float32 on the device; scratch a uint8
+    device tensor of at least psf_group_scratch_bytes bytes."""
+    torch = _torch()
+    batches = []
+    for p, s, o in zip(plans, skies, outs):
+        b, shape = p._batch_shape(s)
+        _dev(s, torch.float32, shape, "sky")
+        _dev(o, torch.float32, shape, "out")
+        batches.append(b)
+    hs = _ptr_array([p._h.value for p in plans])
+    bs = (ctypes.c_int32 * len(plans))(*batches)
+    sp = _ptr_array([s.data_ptr() for s in skies])
+    op = _ptr_array([o.data_ptr() for o in outs])
+    check(load().fr_psf_apply_group(hs, len(plans), sp, bs, op, ctypes.c_void_p(scratch.data_ptr()),
+                                    scratch.numel() * scratch.element_size(), _stream_ptr(stream)))
 
 
 def launch_count(reset: bool = False) -> int:
@@ -252,6 +290,10 @@ class Plan:
 
     def check(self, stream=None):
         check(load().fr_plan_check(self._h, _stream_ptr(stream)))
+
+    def prepare(self, batch=1, stream=None):
+        """Allocate the per-stream workspace for calls on `stream` without computing."""
+        check(load().fr_plan_prepare(self._h, int(batch), _stream_ptr(stream)))
 
     # ------------------------------------------------------------------ shapes
     @property

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfastresolve.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "gridder.cu", "wterms.cu", "fft_grid.cu", "fft_stack.cu", "fft_psf.cu", "noise.cu",
-           "noise_extra.cu",
+           "noise_extra.cu", "fft_psf_group.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

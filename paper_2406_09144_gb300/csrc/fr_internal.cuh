@@ -320,6 +320,20 @@ struct PsfArgs {
   const float* dirty;   // likelihood mode (grad = conv - dirty), else null
   double* value;        // likelihood mode: [nimg / nsky] accumulators, else null
 };
+// PSF convolutions of several plans with equal nx, ny, lx, ly as one flat batch (one launch
+// per pass): plan j contributes nimg[j] = batch_j nsky[j] images, its skies, outputs and
+// transfer function (host arrays of njobs entries)
+struct PsfGroupArgs {
+  int njobs = 0;
+  int nx = 0, ny = 0, lx = 0, ly = 0, hp = 0;
+  const float* const* sky = nullptr;
+  float* const* out = nullptr;
+  const float* const* transfer = nullptr;
+  const int* nsky = nullptr;
+  const int* nimg = nullptr;
+};
+int psf_group_passes(const PsfGroupArgs& g, float2* h, float2* ht, const float2* tw_rows,
+                     const float2* tw_cols, cudaStream_t s);
 // h: [nimg][nx][hp] half spectra, ht: [nimg][ly/2+1][nx] transposed half spectra; tw_rows
 // and tw_cols are the twiddle tables of lengths ly and lx
 int psf_apply_passes(const PsfArgs& a, float2* h, float2* ht, const float2* tw_rows,

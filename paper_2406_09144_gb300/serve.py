@@ -16,10 +16,15 @@ Scheduler (host logic, `Scheduler`):
     device; a finished job releases its slot and memory immediately.
 
 GPU executor (`GpuExecutor`): at admission it builds the job's plan (sorted visibilities, PSF
-transfer function; resident until the job retires), uploads the inputs, makes one eager call
-(which also sizes the per-stream workspace) and captures the job's operator call into a CUDA
-graph; every later call is one graph launch. `run_sequential` is the baseline: one job at a
-time, plain per-call launches, one stream.
+transfer function; resident until the job retires) and uploads the inputs.
+  * PSF-convolution jobs share launches: the calls issued in one scheduling round by jobs with
+    the same image size and PSF padding are run together, up to 16 jobs per call, by one
+    fr_psf_apply_group (three kernel launches for the whole group instead of three per job),
+    on a stream of their own with a caller-owned scratch buffer;
+  * major-cycle jobs (degridding then gridding, many launches per call over the w-planes)
+    reserve their per-stream workspace without computing (fr_plan_prepare) and capture one call
+    into a CUDA graph, so every call is one graph launch on the job's own stream.
+`run_sequential` is the baseline: one job at a time, plain per-call launches, one stream.
 """
 from __future__ import annotations
 
@@ -133,7 +138,8 @@ class Scheduler:
                 self.peak_active = max(self.peak_active, len(active))
                 self.log.append(("admit", r.rid, r.t_admit, used))
                 progressed = True
-            # issue the next call of every job whose previous call finished
+            # issue the next call of every job whose previous call finished (calls that the
+            # executor batches are launched together by flush() below)
             for rid in list(active):
                 r, h, done, est = active[rid]
                 if not self.ex.ready(h):
@@ -149,6 +155,9 @@ class Scheduler:
                     del active[rid]
                     self.log.append(("done", rid, r.t_done, used))
                     progressed = True
+            flush = getattr(self.ex, "flush", None)
+            if flush is not None:
+                flush()
             if not progressed:
                 if self.realtime and not active and not waiting and pending:
                     time.sleep(max(0.0, min(0.002, pending[0].arrival - (self.clock() - t0))))
@@ -223,10 +232,15 @@ class _GateSection:
         return False
 
 
-class GpuExecutor:
-    """Runs admitted jobs on their own CUDA streams; one captured CUDA graph per job call."""
+_PENDING = object()  # a grouped call queued for the next flush
 
-    def __init__(self, device="cuda", graphs: bool = True, eps: float = 1e-5, workers: int = 2):
+
+class GpuExecutor:
+    """Runs admitted jobs on their own CUDA streams (major cycles: one captured CUDA graph per
+    call) and batches the PSF-convolution calls of compatible jobs into shared launches."""
+
+    def __init__(self, device="cuda", graphs: bool = True, eps: float = 1e-5, workers: int = 2,
+                 group_psf: bool = True):
         import concurrent.futures
         import threading
         import torch
@@ -245,6 +259,13 @@ class GpuExecutor:
         self.graveyard_bytes = 0
         self.graveyard_limit = 32 << 30
         self.gate = CaptureGate()
+        self.group_psf = group_psf
+        self.pending_psf = []
+        self.group_stream = None
+        self.scratch = None
+        # kernel launches per operator call: grouped PSF calls and their jobs, graph kernels
+        self.stats = {"group_calls": 0, "group_jobs": 0, "group_kernels": 0,
+                      "graph_calls": 0, "graph_kernels": 0}
 
     def _stream(self):
         with self.lock:
@@ -257,10 +278,11 @@ class GpuExecutor:
 
     def _build(self, r: Request):
         torch = self.torch
-        from .binding import Plan
+        from .binding import Plan, launch_count
         torch.cuda.set_device(self.device)
         s = self._stream()
-        h = {"req": r, "stream": s, "event": None, "graph": None}
+        h = {"req": r, "stream": s, "event": None, "graph": None, "grouped": False, "key": None,
+             "graph_kernels": 0}
         with torch.cuda.stream(s):
             plan = Plan(r.uvw, r.freqs, r.nx, r.ny, r.pixsize, weights=r.weights, eps=self.eps,
                         mfs=r.mfs, stream=s)
@@ -271,6 +293,11 @@ class GpuExecutor:
 
                 def call():
                     plan.psf_apply(sky, out=out, stream=s)
+                if self.group_psf:
+                    h["grouped"] = True
+                    h["key"] = (r.nx, r.ny) + tuple(plan.psf_padding)
+                else:
+                    plan.prepare(sky.shape[0], stream=s)
             else:
                 vis = torch.empty(plan.vis_shape, dtype=torch.complex64, device=self.device)
                 out = torch.empty(plan.sky_shape, dtype=torch.float32, device=self.device)
@@ -278,11 +305,13 @@ class GpuExecutor:
                 def call():
                     plan.degrid(sky, out=vis, stream=s)
                     plan.grid(vis, out=out, stream=s)
-            call()  # eager: sizes the per-stream workspace before any capture
-            if self.graphs:
+                # the per-stream workspace, sized without computing: nothing allocates later
+                plan.prepare(1, stream=s)
+            if self.graphs and not h["grouped"]:
                 g = torch.cuda.CUDAGraph()
                 # thread-local capture: other threads keep building plans meanwhile; plan and
                 # graph destruction (device-synchronising) waits for the capture to end
+                k0 = launch_count()
                 with self.gate.capture():
                     g.capture_begin(capture_error_mode="thread_local")
                     try:
@@ -290,6 +319,7 @@ class GpuExecutor:
                     finally:
                         g.capture_end()
                 h["graph"] = g
+                h["graph_kernels"] = launch_count() - k0
         h.update(plan=plan, sky=sky, out=out, call=call)
         ev = torch.cuda.Event()
         ev.record(s)
@@ -305,20 +335,64 @@ class GpuExecutor:
 
     def ready(self, hh) -> bool:
         h = self._handle(hh)
-        return h is not None and (h["event"] is None or h["event"].query())
+        if h is None or h["event"] is _PENDING:
+            return False
+        return h["event"] is None or h["event"].query()
 
     def issue(self, hh):
         torch = self.torch
         h = self._handle(hh)
+        if h["grouped"]:
+            h["event"] = _PENDING  # runs with the other queued PSF calls at the next flush
+            self.pending_psf.append(h)
+            return
         s = h["stream"]
         with torch.cuda.stream(s):
             if h["graph"] is not None:
                 h["graph"].replay()
+                self.stats["graph_calls"] += 1
+                self.stats["graph_kernels"] += h["graph_kernels"]
             else:
                 h["call"]()
             ev = torch.cuda.Event()
             ev.record(s)
             h["event"] = ev
+
+    def flush(self):
+        """Runs the queued PSF calls: one grouped call per (image size, PSF padding) and up to
+        16 jobs, on the executor's group stream. Every queued job's previous work has finished
+        (the scheduler issues a call only once ready() says so), so the group needs no waits."""
+        if not self.pending_psf:
+            return
+        torch = self.torch
+        from .binding import psf_apply_group, psf_group_scratch_bytes
+        groups = collections.OrderedDict()
+        for h in self.pending_psf:
+            groups.setdefault(h["key"], []).append(h)
+        self.pending_psf = []
+        if self.group_stream is None:
+            self.group_stream = torch.cuda.Stream(device=self.device)
+        gs = self.group_stream
+        for hs in groups.values():
+            for i in range(0, len(hs), 16):
+                part = hs[i:i + 16]
+                plans = [h["plan"] for h in part]
+                need = psf_group_scratch_bytes(plans, [h["sky"].shape[0] for h in part])
+                with torch.cuda.stream(gs):
+                    if self.scratch is None or self.scratch.numel() < need:
+                        self.scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
+                    for h in part:  # used on this stream too: keep them alive until it is done
+                        h["sky"].record_stream(gs)
+                        h["out"].record_stream(gs)
+                    psf_apply_group(plans, [h["sky"] for h in part], [h["out"] for h in part],
+                                    self.scratch, stream=gs)
+                    ev = torch.cuda.Event()
+                    ev.record(gs)
+                for h in part:
+                    h["event"] = ev
+                self.stats["group_calls"] += 1
+                self.stats["group_jobs"] += len(part)
+                self.stats["group_kernels"] += 3
 
     def finish(self, hh):
         h = self._handle(hh)
@@ -343,10 +417,11 @@ class GpuExecutor:
             self.graveyard_bytes = 0
 
 
-def run_sequential(requests, device="cuda", eps=1e-5):
-    """Baseline: each job alone, in arrival order, plain launches on one stream."""
+def run_sequential(requests, device="cuda", eps=1e-5, stats=None):
+    """Baseline: each job alone, in arrival order, plain launches on one stream. With a dict
+    `stats`, counts the operator calls and their kernel launches."""
     import torch
-    from .binding import Plan
+    from .binding import Plan, launch_count
     reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
     t0 = time.perf_counter()
     for r in reqs:
@@ -356,11 +431,16 @@ def run_sequential(requests, device="cuda", eps=1e-5):
         r.t_admit = time.perf_counter() - t0
         plan = Plan(r.uvw, r.freqs, r.nx, r.ny, r.pixsize, weights=r.weights, eps=eps, mfs=r.mfs)
         sky = torch.as_tensor(np.ascontiguousarray(r.sky), dtype=torch.float32).to(device)
+        k0 = launch_count()
         for _ in range(r.ncalls):
             if r.kind == "psf":
                 out = plan.psf_apply(sky)
             else:
                 out = plan.grid(plan.degrid(sky))
+        if stats is not None:
+            key = "psf" if r.kind == "psf" else "major"
+            stats[key + "_calls"] = stats.get(key + "_calls", 0) + r.ncalls
+            stats[key + "_kernels"] = stats.get(key + "_kernels", 0) + launch_count() - k0
         r.result = out.cpu().numpy()
         plan.close()
         r.t_done = time.perf_counter() - t0
@@ -439,8 +519,9 @@ def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float
     torch.cuda.synchronize()
 
     seq = _copy_requests(base)
+    seq_stats = {}
     t0 = time.perf_counter()
-    run_sequential(seq)
+    run_sequential(seq, stats=seq_stats)
     torch.cuda.synchronize()
     seq_wall = time.perf_counter() - t0
     srv = _copy_requests(base)
@@ -467,7 +548,17 @@ def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float
     s_seq = summarize(seq, seq_wall)
     s_srv = summarize(srv, srv_wall)
     s_arr = summarize(arr, arr_wall)
+    st = ex1.stats
+    launches = {
+        "per_request_psf_kernels_per_call": seq_stats.get("psf_kernels", 0) / max(seq_stats.get("psf_calls", 0), 1),
+        "server_psf_kernels_per_call": st["group_kernels"] / max(st["group_jobs"], 1),
+        "server_psf_jobs_per_shared_launch": st["group_jobs"] / max(st["group_calls"], 1),
+        "per_request_major_kernels_per_call": seq_stats.get("major_kernels", 0) / max(seq_stats.get("major_calls", 0), 1),
+        "server_major_kernels_per_call": st["graph_kernels"] / max(st["graph_calls"], 1),
+        "server_major_host_launches_per_call": 1.0,
+    }
     return {
+        "launches": launches,
         "workload": f"{n} jobs, images {kw.get('sizes', (256, 512, 1024, 2048, 4096))}, "
                     f"visibilities log-uniform {kw.get('nvis_range', (1e4, 2e7))}, 1-"
                     f"{kw.get('nchan_max', 8)} channels, half PSF-convolution / half major-cycle, "

@@ -37,3 +37,63 @@ def test_results_alone_equal_results_in_the_mix(sizes):
         d = np.linalg.norm(a.result - b.result) / np.linalg.norm(a.result)
         assert d <= 1e-6, (a.rid, a.kind, d)
         assert b.arrival <= b.t_admit <= b.t_done
+
+
+def test_grouped_psf_convolution_equals_per_plan_calls():
+    """fr_psf_apply_group: the PSF convolutions of several plans (equal image size and padding,
+    different PSFs, sky counts and batches) in one launch per pass equal each plan's own
+    fr_psf_apply."""
+    from paper_2406_09144_gb300 import build, synth
+    from paper_2406_09144_gb300.binding import (FastResolveError, Plan, psf_apply_group,
+                                                psf_group_scratch_bytes)
+    build.build()
+    nx, ny = 96, 64
+    plans, skies = [], []
+    for j, (nchan, mfs, batch) in enumerate([(1, True, 2), (3, False, 1), (2, True, 3)]):
+        obs = synth.random_observation(900 + 100 * j, nchan, nx, ny, 2e-3, seed=90 + j)
+        p = Plan(obs.uvw, obs.freqs, nx, ny, obs.pixsize, weights=obs.weights, eps=1e-5, mfs=mfs)
+        plans.append(p)
+        skies.append(torch.tensor(synth.random_skies(batch * p.nsky, nx, ny, seed=20 + j)
+                                  .reshape(batch, p.nsky, nx, ny), dtype=torch.float32,
+                                  device="cuda"))
+    need = psf_group_scratch_bytes(plans, [s.shape[0] for s in skies])
+    scratch = torch.empty(need, dtype=torch.uint8, device="cuda")
+    outs = [torch.full_like(s, float("nan")) for s in skies]
+    psf_apply_group(plans, skies, outs, scratch)
+    for p, s, o in zip(plans, skies, outs):
+        ref = p.psf_apply(s)
+        d = (torch.linalg.vector_norm((o - ref).double()) / torch.linalg.vector_norm(ref.double()))
+        assert float(d) <= 1e-6, float(d)
+    # plans of another image size cannot share the launches
+    obs = synth.random_observation(500, 1, 64, 64, 2e-3, seed=99)
+    other = Plan(obs.uvw, obs.freqs, 64, 64, obs.pixsize, eps=1e-5)
+    sk = torch.zeros((1, 1, 64, 64), device="cuda")
+    with pytest.raises(FastResolveError):
+        psf_apply_group([plans[0], other], [skies[0], sk], [outs[0], sk.clone()], scratch)
+
+
+def test_server_shares_psf_launches_across_jobs():
+    """PSF-convolution jobs of one image size present together are run by shared launches
+    (several jobs per grouped call), with results equal to the jobs run alone."""
+    from paper_2406_09144_gb300 import build
+    from paper_2406_09144_gb300.serve import (GpuExecutor, Scheduler, _copy_requests,
+                                              estimate_bytes, make_requests, run_sequential)
+    build.build()
+    base = [r for r in make_requests(24, seed=500, sizes=(128,), nvis_range=(2e3, 2e4),
+                                     nchan_max=2, ncalls=4) if r.kind == "psf"]
+    assert len(base) >= 4
+    alone = run_sequential(_copy_requests(base))
+    mix = _copy_requests(base)
+    for r in mix:
+        r.arrival = 0.0
+    ex = GpuExecutor(graphs=True)
+    sch = Scheduler(ex, 4 * sum(estimate_bytes(r) for r in base), max_active=len(base))
+    sch.run(mix)
+    torch.cuda.synchronize()
+    ex.close_finished()
+    st = ex.stats
+    assert st["group_jobs"] == sum(r.ncalls for r in base)
+    assert st["group_jobs"] >= 2 * st["group_calls"], st
+    for a, b in zip(alone, mix):
+        d = np.linalg.norm(a.result - b.result) / np.linalg.norm(a.result)
+        assert d <= 1e-6, (a.rid, d)
