@@ -261,6 +261,11 @@ class GpuExecutor:
         self.gate = CaptureGate()
         self.group_psf = group_psf
         self.pending_psf = []
+        # jobs of each PSF group key that have issued calls and not finished: a key's queued
+        # calls wait (at most group_wait_s) while another of its jobs still has a call in
+        # flight, so jobs that started apart fall into step and share launches
+        self.group_members = collections.defaultdict(dict)
+        self.group_wait_s = 2e-3
         self.group_stream = None
         self.scratch = None
         # kernel launches per operator call: grouped PSF calls and their jobs, graph kernels
@@ -343,7 +348,9 @@ class GpuExecutor:
         torch = self.torch
         h = self._handle(hh)
         if h["grouped"]:
-            h["event"] = _PENDING  # runs with the other queued PSF calls at the next flush
+            h["event"] = _PENDING  # runs with the other queued PSF calls at a flush
+            h["pending_since"] = time.perf_counter()
+            self.group_members[h["key"]][id(h)] = h
             self.pending_psf.append(h)
             return
         s = h["stream"]
@@ -369,7 +376,17 @@ class GpuExecutor:
         groups = collections.OrderedDict()
         for h in self.pending_psf:
             groups.setdefault(h["key"], []).append(h)
-        self.pending_psf = []
+        now = time.perf_counter()
+        keep = []
+        for key in list(groups):
+            hs = groups[key]
+            in_flight = any(m["event"] is not _PENDING and m["event"] is not None and
+                            not m["event"].query() for m in self.group_members[key].values())
+            oldest = min(h["pending_since"] for h in hs)
+            if in_flight and len(hs) < 16 and now - oldest < self.group_wait_s:
+                keep.extend(hs)  # wait for the job in flight to join
+                del groups[key]
+        self.pending_psf = keep
         if self.group_stream is None:
             self.group_stream = torch.cuda.Stream(device=self.device)
         gs = self.group_stream
@@ -397,6 +414,8 @@ class GpuExecutor:
     def finish(self, hh):
         h = self._handle(hh)
         h["event"].synchronize()
+        if h["grouped"]:
+            self.group_members[h["key"]].pop(id(h), None)
         h["req"].result = h["out"].cpu().numpy()
         # destroying a plan frees device memory, which synchronises the whole device; finished
         # plans are parked and destroyed together once enough of them accumulate (or at close)
