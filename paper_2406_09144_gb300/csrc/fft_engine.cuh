@@ -161,6 +161,137 @@ constexpr int op_pts() {
   return (Op::TWO && L == 8192) ? 32 : 16;
 }
 
+// The same stages, except that the last one hands its outputs to sink(b, i, value) (sequence b
+// of the CTA, output index i in natural order) instead of writing them back to shared memory:
+// its task j of sequence b produces outputs i = j + r L/R, so consecutive threads hold
+// consecutive outputs and a row-major store from the sink is coalesced. Saves the last
+// shared-memory round trip and its two barriers. Shared memory is left as the stage read it.
+template <int L, int ST, int DIR, int P, class Sink>
+__device__ __forceinline__ void fft_stages_direct(float2* s, const float2* __restrict__ tw,
+                                                  Sink sink) {
+  constexpr int S = fft_num_stages(L, P);
+  if constexpr (ST < S - 1) {
+    using C = FftCfg<L, P>;
+    constexpr int B = C::B, NT = C::NT, LP = C::LP;
+    constexpr int R = fft_radix(L, ST, P);
+    constexpr int NS = fft_ns_before(L, ST, P);
+    constexpr int LR = L / R;
+    constexpr int NTASK = B * LR;
+    constexpr bool EVEN = NTASK % NT == 0;
+    constexpr int TPT = (NTASK + NT - 1) / NT;
+    constexpr int TSTEP = L / (NS * R);
+    float2 v[TPT][R];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int t = threadIdx.x + q * NT;
+      if (EVEN || t < NTASK) {
+        const int b = t / LR, j = t % LR;
+        const int k = (NS & (NS - 1)) == 0 ? (j & (NS - 1)) : j % NS;
+        const float2* src = s + b * LP;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = src[spad(j + r * LR)];
+        if constexpr (ST > 0) apply_twiddles<R, DIR>(v[q], tw, k, TSTEP);
+        dft_r<R, DIR>(v[q]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int t = threadIdx.x + q * NT;
+      if (EVEN || t < NTASK) {
+        const int b = t / LR, j = t % LR;
+        const int k = (NS & (NS - 1)) == 0 ? (j & (NS - 1)) : j % NS;
+        float2* dst = s + b * LP;
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[spad(base + r * NS)] = v[q][r];
+      }
+    }
+    __syncthreads();
+    fft_stages_direct<L, ST + 1, DIR, P>(s, tw, sink);
+  } else if constexpr (ST == S - 1) {
+    using C = FftCfg<L, P>;
+    constexpr int B = C::B, NT = C::NT, LP = C::LP;
+    constexpr int R = fft_radix(L, ST, P);
+    constexpr int NS = fft_ns_before(L, ST, P);
+    constexpr int LR = L / R;
+    static_assert(NS * R == L && NS == LR, "last stage");
+    constexpr int NTASK = B * LR;
+    constexpr bool EVEN = NTASK % NT == 0;
+    constexpr int TPT = (NTASK + NT - 1) / NT;
+    // one task at a time: the sink's work per output stays out of the other task's registers
+#pragma unroll 1
+    for (int q = 0; q < TPT; ++q) {
+      const int t = threadIdx.x + q * NT;
+      if (EVEN || t < NTASK) {
+        const int b = t / LR, j = t % LR;
+        const float2* src = s + b * LP;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[spad(j + r * LR)];
+        if constexpr (ST > 0) apply_twiddles<R, DIR>(v, tw, j, 1);
+        dft_r<R, DIR>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sink(b, j + r * LR, v[r]);
+      }
+    }
+  }
+}
+
+// Each (sequence, output index) pair that fft_stages_direct hands to the sink, for this thread,
+// in the same order: f(b, i) for the thread's tasks of the last stage.
+template <int L, int P, class F>
+__device__ __forceinline__ void for_direct_outputs(F f) {
+  using C = FftCfg<L, P>;
+  constexpr int S = fft_num_stages(L, P);
+  constexpr int R = fft_radix(L, S - 1, P);
+  constexpr int LR = L / R, NT = C::NT;
+  constexpr int NTASK = C::B * LR;
+  constexpr bool EVEN = NTASK % NT == 0;
+  constexpr int TPT = (NTASK + NT - 1) / NT;
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const int t = threadIdx.x + q * NT;
+    if (EVEN || t < NTASK) {
+      const int b = t / LR, j = t % LR;
+#pragma unroll
+      for (int r = 0; r < R; ++r) f(b, j + r * LR);
+    }
+  }
+}
+
+// fft_from_regs whose last stage goes to sink(b, i, value) (fft_stages_direct)
+template <int L, int DIR, int P = 16, class F, class Sink>
+__device__ __forceinline__ void fft_from_regs_direct(float2* s, float2* r,
+                                                     const float2* __restrict__ tw, F landed,
+                                                     Sink sink) {
+  using C = FftCfg<L, P>;
+  if constexpr (fuse_first<L, P>()) {
+    constexpr int Q = L / P;
+    const int b = threadIdx.x / Q, j = threadIdx.x % Q;
+    float2 v[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) v[k] = r[k];
+    dft_r<P, DIR>(v);
+    float2* dst = s + b * C::LP;
+#pragma unroll
+    for (int k = 0; k < P; ++k) dst[spad(P * j + k)] = v[k];
+    __syncthreads();
+    landed();
+    fft_stages_direct<L, 1, DIR, P>(s, tw, sink);
+  } else {
+    constexpr int PER = C::B * L / C::NT;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = threadIdx.x + k * C::NT;
+      s[(idx / L) * C::LP + spad(idx % L)] = r[k];
+    }
+    __syncthreads();
+    landed();
+    fft_stages_direct<L, 0, DIR, P>(s, tw, sink);
+  }
+}
+
 // Read-only view of one sequence in shared memory.
 struct SeqView {
   const float2* p;
@@ -231,6 +362,17 @@ __global__ void __launch_bounds__(FftCfg<LEN, op_pts<LEN, Op>()>::NT,
     int b, i;
     load_pos<L, P>(k, &b, &i);
     r[k] = (seq0 + b < nseq) ? op.load(seq0 + b, i) : make_float2(0.f, 0.f);
+  }
+  if constexpr (Op::DIRECT && !Op::TWO && !Op::TRANSPOSED) {
+    // row-major outputs straight from the last stage
+    double dacc = 0.0;
+    fft_from_regs_direct<L, DIR, P>(
+        smem, r, tw, [&] { if (seq0 < nseq) op.after_load(seq0, min(B, nseq - seq0)); },
+        [&](int b, int i, float2 v) {
+          if (seq0 + b < nseq) dacc += op.direct(seq0 + b, i, v);
+        });
+    op.finish(seq0, dacc);
+    return;
   }
   fft_from_regs<L, DIR, P>(smem, r, tw, [&] {
     if (seq0 < nseq) op.after_load(seq0, min(B, nseq - seq0));
@@ -319,32 +461,35 @@ int launch_pass(const Op& op, int nimg, const float2* tw, cudaStream_t s) {
 }
 
 // Multi-input pass: op.ntrans() transforms per sequence, each of its own input, whose outputs
-// are combined per output element in registers and written once (row-major mapping;
-// blockIdx.x selects B sequences).
+// are combined per output element and written once (row-major mapping; blockIdx.x selects B
+// sequences). The last stage of every transform hands its outputs to the combination directly
+// (fft_stages_direct); each output's running sum sits in shared memory after the sequences, in
+// a slot only the thread holding that output ever touches.
 //   Trans trans(int t)                              transform t's parameters
 //   float2 load(const Trans&, int seq, int i)       element i of its input
-//   float term(const Trans&, int seq, int o, SeqView v)   its contribution to output o
+//   int out_of(int i)                               output of transform index i, or -1
+//   float term(const Trans&, int seq, int o, float2 z)   its contribution to output o
 //   void store(int seq, int o, float acc)
-// Outputs per sequence nout() <= L / 2 (each thread owns at most PER / 2 of them).
+// Outputs per sequence nout() <= L / 2.
 template <int LEN, int DIR, class Op>
 __global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB)
     fft_pass_accum_kernel(Op op, const float2* __restrict__ tw) {
   using C = FftCfg<LEN>;
   constexpr int L = C::L, B = C::B, NT = C::NT, LP = C::LP;
   constexpr int PER = B * L / NT;
-  constexpr int MAXO = PER / 2;
+  constexpr int HALF = L / 2;
   extern __shared__ float2 smem[];
-  // the sums live in shared memory after the sequences (each thread its own MAXO slots), so no
-  // registers stay live across the transforms
-  float* acc = reinterpret_cast<float*>(smem + B * LP) + threadIdx.x;
-  const int nseq = op.nseq(), nout = op.nout(), ntr = op.ntrans();
+  float* acc = reinterpret_cast<float*>(smem + B * LP);  // [B][L / 2]
+  const int nseq = op.nseq(), ntr = op.ntrans();
   const int seq0 = blockIdx.x * B;
-#pragma unroll
-  for (int m = 0; m < MAXO; ++m) acc[m * NT] = 0.f;
+  for_direct_outputs<L, 16>([&](int b, int i) {
+    const int o = op.out_of(i);
+    if (o >= 0) acc[b * HALF + o] = 0.f;
+  });
 #pragma unroll 1
   for (int t = 0; t < ntr; ++t) {
     const typename Op::Trans tp = op.trans(t);
-    if (t > 0) __syncthreads();  // the previous transform's outputs have been read
+    if (t > 0) __syncthreads();  // the previous transform's last stage has read its inputs
     float2 r[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
@@ -352,24 +497,15 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB)
       load_pos<L>(k, &b, &i);
       r[k] = (seq0 + b < nseq) ? op.load(tp, seq0 + b, i) : make_float2(0.f, 0.f);
     }
-    fft_from_regs<L, DIR>(smem, r, tw, [] {});
-#pragma unroll
-    for (int m = 0; m < MAXO; ++m) {
-      const int idx = threadIdx.x + m * NT;
-      if (idx < B * nout) {
-        const int b = idx / nout, o = idx % nout;
-        if (seq0 + b < nseq) acc[m * NT] += op.term(tp, seq0 + b, o, SeqView{smem + b * LP});
-      }
-    }
+    fft_from_regs_direct<L, DIR>(smem, r, tw, [] {}, [&](int b, int i, float2 z) {
+      const int o = op.out_of(i);
+      if (o >= 0 && seq0 + b < nseq) acc[b * HALF + o] += op.term(tp, seq0 + b, o, z);
+    });
   }
-#pragma unroll
-  for (int m = 0; m < MAXO; ++m) {
-    const int idx = threadIdx.x + m * NT;
-    if (idx < B * nout) {
-      const int b = idx / nout, o = idx % nout;
-      if (seq0 + b < nseq) op.store(seq0 + b, o, acc[m * NT]);
-    }
-  }
+  for_direct_outputs<L, 16>([&](int b, int i) {
+    const int o = op.out_of(i);
+    if (o >= 0 && seq0 + b < nseq) op.store(seq0 + b, o, acc[b * HALF + o]);
+  });
 }
 
 template <int LEN, int DIR, class Op>
@@ -476,6 +612,10 @@ struct OpBase {
   static constexpr bool TWO = false;
   static constexpr bool GROUP = false;
   static constexpr bool SEQ_Y = false;
+  // row-major ops with DIRECT provide double direct(int seq, int i, float2 value): the store of
+  // transform output i (natural order), called once per output from the last stage; the
+  // returned values are summed per thread for finish() as store()'s are
+  static constexpr bool DIRECT = false;
   __device__ void after_load(int, int) const {}
   template <int B, int NT, int L, int LP>
   __device__ void mid(float2*, int) const {}

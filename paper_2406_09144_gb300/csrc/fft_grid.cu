@@ -112,6 +112,11 @@ struct D2Op : OpBase {
     grid[blockIdx.y * grid_stride + (size_t)(vb0 + q) * Nu + u] = s[u];
     return 0.0;
   }
+  static constexpr bool DIRECT = true;  // band columns only
+  __device__ double direct(int q, int u, float2 z) const {
+    if (u >= ub0 && u < ub0 + nub) grid[blockIdx.y * grid_stride + (size_t)(vb0 + q) * Nu + u] = z;
+    return 0.0;
+  }
 };
 
 // D1 for all expansion terms from one load: raw element (sky * corr, tau), term t's input
@@ -264,7 +269,16 @@ struct G2Op : OpBase {
     return b1[(size_t)jx * Nv + i];
   }
   __device__ double store(int jx, int jy, SeqView s) const {
-    const float2 z = s[wrap(jy - (ny >> 1), Nv)];
+    return out(jx, jy, s[wrap(jy - (ny >> 1), Nv)]);
+  }
+  // transform index i holds image column jy = i + ny/2 (mod Nv) inside the crop
+  static constexpr bool DIRECT = true;
+  __device__ double direct(int jx, int i, float2 z) const {
+    const int hy = ny >> 1;
+    const int jy = i < hy ? i + hy : (i >= Nv - hy ? i - Nv + hy : -1);
+    return jy >= 0 ? out(jx, jy, z) : 0.0;
+  }
+  __device__ double out(int jx, int jy, float2 z) const {
     const int pix = jx * ny + jy;
     float val;
     if (wterm && taylor) {
@@ -302,11 +316,19 @@ struct G2TermsAddOp : OpBase {
     return b1[blockIdx.y * b1_stride + (size_t)jx * Nv + i];
   }
   __device__ double store(int jx, int jy, SeqView s) const {
-    const int i = wrap(jy - (ny >> 1), Nv);
+    return out(jx, jy, s[wrap(jy - (ny >> 1), Nv)]);
+  }
+  static constexpr bool DIRECT = true;
+  __device__ double direct(int jx, int i, float2 z) const {
+    const int hy = ny >> 1;
+    const int jy = i < hy ? i + hy : (i >= Nv - hy ? i - Nv + hy : -1);
+    return jy >= 0 ? out(jx, jy, z) : 0.0;
+  }
+  __device__ double out(int jx, int jy, float2 z) const {
     const int pix = jx * ny + jy;
     const int t = blockIdx.y;
     atomicAdd(&dirty[pix],
-              s[i].x * taylor_factor(__ldg(&tq[pix]), t, c_inv_fact[t]) * __ldg(&corr[pix]));
+              z.x * taylor_factor(__ldg(&tq[pix]), t, c_inv_fact[t]) * __ldg(&corr[pix]));
     return 0.0;
   }
 };

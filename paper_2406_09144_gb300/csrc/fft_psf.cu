@@ -137,8 +137,10 @@ struct P3Op : OpBase {
     const int per = nx * nsky;
     return rho0 / per == rho1 / per;
   }
-  __device__ double store(int r, int n, SeqView v) const {
-    const float2 z = v[n];
+  __device__ double store(int r, int n, SeqView v) const { return out_at(r, n, v[n]); }
+  static constexpr bool DIRECT = true;  // outputs [0, ny) of the transform: the crop
+  __device__ double direct(int r, int i, float2 z) const { return i < ny ? out_at(r, i, z) : 0.0; }
+  __device__ double out_at(int r, int n, float2 z) const {
     const size_t a0 = (size_t)(2 * r) * ny + n, a1 = a0 + ny;
     if (!dirty) {
       out[a0] = z.x;

@@ -88,9 +88,11 @@ struct D2SparseOp : OpBase {
       return make_float2(0.f, 0.f);
     return b1t[(size_t)q * nx + jx];
   }
-  __device__ double store(int q, int u, SeqView s) const {
+  __device__ double store(int q, int u, SeqView s) const { return direct(q, u, s[u]); }
+  static constexpr bool DIRECT = true;
+  __device__ double direct(int q, int u, float2 z) const {
     const int v = compact_row_v(rows, q);
-    if (tile_on(bits, ntw, v, u)) grid[(size_t)v * Nu + u] = s[u];
+    if (tile_on(bits, ntw, v, u)) grid[(size_t)v * Nu + u] = z;
     return 0.0;
   }
 };
@@ -158,8 +160,14 @@ struct G2StackOp {
     if (c < 0) return make_float2(0.f, 0.f);
     return p.b1[(size_t)jx * p.ncomp + c * TILE + (v & (TILE - 1))];
   }
-  __device__ float term(const Trans& p, int jx, int jy, SeqView s) const {
-    const float2 z = s[wrap(jy - (ny >> 1), Nv)];
+  // transform index i holds image column jy when i = jy - ny/2 (mod Nv): the crop
+  __device__ int out_of(int i) const {
+    const int hy = ny >> 1;
+    if (i < hy) return i + hy;
+    if (i >= Nv - hy) return i - Nv + hy;
+    return -1;
+  }
+  __device__ float term(const Trans& p, int jx, int jy, float2 z) const {
     float cs, sn;
     plane_phase(__ldg(&tq[jx * ny + jy]), p.k64, &cs, &sn);
     return z.x * cs - z.y * sn;  // Re(z exp(+2 pi i w_k (t - t_c)))
