@@ -518,7 +518,8 @@ struct Temps {
 };
 }  // namespace
 
-static int presort_items(VisLayout* lay, int64_t N, bool wterm, cudaStream_t s);
+static int presort_items(VisLayout* lay, int64_t N, bool wterm, cudaStream_t s,
+                         const int4* sort_items, int64_t nsort);
 
 int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const double* h_freqs,
                  const double* d_freqs, int nchan, const float* d_weights, int ngroups,
@@ -746,12 +747,38 @@ int build_layout(const Geometry& geo, const double* d_uvw, int64_t nrow, const d
     emit_items<<<grid1d(E), 256, 0, s>>>(ia, E);
     FR_LAUNCHED();
   }
-  // Without w-stacking every work item is a fixed chunk of one tile's range, so each chunk can be
-  // ordered by footprint origin once here instead of in every gridding call. (With w-stacking the
-  // item ranges of neighbouring planes overlap with different chunk boundaries.)
+  // Without w-stacking every work item is a fixed chunk of one tile's range, so each chunk is
+  // ordered by footprint origin once here instead of in every gridding call. With w-stacking a
+  // plane's items span the buckets of W first planes, with chunk boundaries that differ from
+  // plane to plane: there every (tile, first plane) bucket is ordered instead, in chunks of up
+  // to ITEM_CHUNK, so a work item is a few origin-sorted runs and no call sorts.
   lay->presorted = false;
   if (!stack && lay->nitems > 0) {
-    FR_TRY(presort_items(lay, N, wterm, s));
+    FR_TRY(presort_items(lay, N, wterm, s, nullptr, 0));
+    lay->presorted = true;
+  } else if (stack && lay->nitems > 0) {
+    ItemArgs sa = ia;
+    sa.W = 1;  // one first plane per range: the (group, plane, tile) buckets themselves
+    sa.chunk = ITEM_CHUNK;
+    int *d_sc, *d_soff;
+    FR_TRY(t.alloc(&d_sc, E));
+    FR_TRY(t.alloc(&d_soff, E + 1));
+    sa.chunks = d_sc;
+    sa.item_off = d_soff;
+    count_items<<<grid1d(E), 256, 0, s>>>(sa, E);
+    FR_LAUNCHED();
+    FR_TRY(exclusive_scan(d_sc, d_soff, E, s));
+    int nsort = 0;
+    FR_CUDA_TRY(cudaMemcpyAsync(&nsort, d_soff + E, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (nsort > 0) {
+      int4* sitems;
+      FR_TRY(t.alloc(&sitems, nsort));
+      sa.items = sitems;
+      emit_items<<<grid1d(E), 256, 0, s>>>(sa, E);
+      FR_LAUNCHED();
+      FR_TRY(presort_items(lay, N, wterm, s, sitems, nsort));
+    }
     lay->presorted = true;
   }
   // visibility visits per (group, plane), for launch accounting
@@ -1199,7 +1226,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) presort_kernel(const int4* __
   }
 }
 
-static int presort_items(VisLayout* lay, int64_t N, bool wterm, cudaStream_t s) {
+static int presort_items(VisLayout* lay, int64_t N, bool wterm, cudaStream_t s,
+                         const int4* sort_items, int64_t nsort) {
   Temps t(s);
   SortArrays in{lay->cell, lay->du, lay->dv, wterm ? lay->dw : nullptr,
                 wterm ? lay->ph : nullptr, lay->perm, lay->wgt};
@@ -1213,7 +1241,11 @@ static int presort_items(VisLayout* lay, int64_t N, bool wterm, cudaStream_t s) 
     FR_TRY(t.alloc(&out.dw, N));
     FR_TRY(t.alloc(&out.ph, N));
   }
-  presort_kernel<<<(unsigned)lay->nitems, GRID_WARPS * 32, 0, s>>>(lay->items, in, out);
+  if (!sort_items) {
+    sort_items = lay->items;
+    nsort = lay->nitems;
+  }
+  presort_kernel<<<(unsigned)nsort, GRID_WARPS * 32, 0, s>>>(sort_items, in, out);
   FR_LAUNCHED();
   const size_t b = (size_t)N * 4;
   FR_CUDA_TRY(cudaMemcpyAsync(lay->cell, out.cell, b, cudaMemcpyDeviceToDevice, s));
