@@ -48,6 +48,28 @@ struct FftCfg {
                                             : (FIT64 > 1 ? FIT64 - 1 : 1);
 };
 
+// Stage twiddles w^(r k) of a power-of-two length: w^k = exp(DIR 2 pi i k tstep / L) from one
+// sincospif (the argument 2 k tstep / L is exact in FP32), its powers w^(k 2^e) by squaring and
+// the others by products (twiddle_rec), so no stage waits on a table load; other lengths load
+// their twiddles from the table (apply_twiddles).
+template <int L, int R, int DIR>
+__device__ __forceinline__ void stage_twiddles(float2* v, const float2* __restrict__ tw, int k,
+                                               int tstep) {
+  if constexpr ((L & (L - 1)) == 0 && (R & (R - 1)) == 0) {
+    constexpr int LB = ilog2(R);
+    float2 pw[LB];
+    float sn, cs;
+    sincospif((float)(2 * k * tstep) * (1.f / (float)L), &sn, &cs);
+    pw[0] = make_float2(cs, DIR < 0 ? -sn : sn);
+#pragma unroll
+    for (int e = 1; e < LB; ++e) pw[e] = cmul(pw[e - 1], pw[e - 1]);
+    float2 wr[R];
+    twiddle_rec<R, 1>(v, pw, wr);
+  } else {
+    apply_twiddles<R, DIR>(v, tw, k, tstep);
+  }
+}
+
 template <int L, int ST, int DIR, int P = 16>
 __device__ __forceinline__ void fft_stages(float2* s, const float2* __restrict__ tw) {
   if constexpr (ST < fft_num_stages(L, P)) {
@@ -72,7 +94,7 @@ __device__ __forceinline__ void fft_stages(float2* s, const float2* __restrict__
         const float2* src = s + b * LP;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[q][r] = src[spad(j + r * LR)];
-        if constexpr (ST > 0) apply_twiddles<R, DIR>(v[q], tw, k, TSTEP);
+        if constexpr (ST > 0) stage_twiddles<L, R, DIR>(v[q], tw, k, TSTEP);
         dft_r<R, DIR>(v[q]);
       }
     }
@@ -190,7 +212,7 @@ __device__ __forceinline__ void fft_stages_direct(float2* s, const float2* __res
         const float2* src = s + b * LP;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[q][r] = src[spad(j + r * LR)];
-        if constexpr (ST > 0) apply_twiddles<R, DIR>(v[q], tw, k, TSTEP);
+        if constexpr (ST > 0) stage_twiddles<L, R, DIR>(v[q], tw, k, TSTEP);
         dft_r<R, DIR>(v[q]);
       }
     }
@@ -229,7 +251,7 @@ __device__ __forceinline__ void fft_stages_direct(float2* s, const float2* __res
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[spad(j + r * LR)];
-        if constexpr (ST > 0) apply_twiddles<R, DIR>(v, tw, j, 1);
+        if constexpr (ST > 0) stage_twiddles<L, R, DIR>(v, tw, j, 1);
         dft_r<R, DIR>(v);
 #pragma unroll
         for (int r = 0; r < R; ++r) sink(b, j + r * LR, v[r]);
