@@ -657,7 +657,8 @@ def main():
         from paper_2406_09144_gb300 import serve
         del model, grad, resid
         torch.cuda.empty_cache()
-        sv = serve.bench(args.serving_jobs, sizes=(256, 512, 1024, 2048), nvis_range=(1e4, 5e6))
+        sv = serve.bench(args.serving_jobs, max_active=16, workers=4, sizes=(256, 512, 1024, 2048),
+                          nvis_range=(1e4, 5e6))
         pa = sv["server_poisson"]
         serving = {"workload": sv["workload"], "throughput_gain": sv["throughput_gain"],
                    "server_jobs_per_s": sv["server_closed"]["req_per_s"],

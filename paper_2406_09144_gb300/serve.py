@@ -519,7 +519,7 @@ def _copy_requests(reqs):
 
 
 def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float = 0.8,
-          seed: int = 100, **kw) -> dict:
+          seed: int = 100, workers: int = 2, **kw) -> dict:
     """Serving benchmark: (1) plain per-request launches, one job at a time, all jobs present
     at t = 0 -> capacity; (2) the continuous-batching server on the same jobs at t = 0 ->
     throughput; (3) the server under Poisson arrivals at `load` x the sequential capacity ->
@@ -544,7 +544,7 @@ def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float
     torch.cuda.synchronize()
     seq_wall = time.perf_counter() - t0
     srv = _copy_requests(base)
-    ex1 = GpuExecutor(graphs=True)
+    ex1 = GpuExecutor(graphs=True, workers=workers)
     sch = Scheduler(ex1, budget, max_active)
     t0 = time.perf_counter()
     sch.run(srv)
@@ -557,7 +557,7 @@ def bench(n: int = 64, max_active: int = 8, budget_gb: float = 96.0, load: float
         worst = max(worst, d)
     rate = load * n / seq_wall
     arr = poisson_arrivals(_copy_requests(base), rate, seed=seed)
-    ex2 = GpuExecutor(graphs=True)
+    ex2 = GpuExecutor(graphs=True, workers=workers)
     sch2 = Scheduler(ex2, budget, max_active)
     t0 = time.perf_counter()
     sch2.run(arr)
@@ -596,10 +596,11 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--workers", type=int, default=2)
     ap.add_argument("--budget-gb", type=float, default=96.0)
     ap.add_argument("--max-size", type=int, default=4096)
     ap.add_argument("--max-nvis", type=float, default=2e7)
     a = ap.parse_args()
     sizes = tuple(s for s in (256, 512, 1024, 2048, 4096) if s <= a.max_size)
-    print(json.dumps(bench(a.n, a.max_active, a.budget_gb, sizes=sizes,
+    print(json.dumps(bench(a.n, a.max_active, a.budget_gb, sizes=sizes, workers=a.workers,
                            nvis_range=(1e4, a.max_nvis))))
