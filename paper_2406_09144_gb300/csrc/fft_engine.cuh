@@ -52,6 +52,18 @@ struct FftCfg {
 // sincospif (the argument 2 k tstep / L is exact in FP32), its powers w^(k 2^e) by squaring and
 // the others by products (twiddle_rec), so no stage waits on a table load; other lengths load
 // their twiddles from the table (apply_twiddles).
+// Bulk L2 prefetch of a contiguous range: one instruction, no registers held, nothing to wait
+// for. The instruction takes a 16-byte aligned address and a multiple of 16 bytes; other ranges
+// (rows of images whose side is not a multiple of 4) are left alone.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  if ((((uintptr_t)p) & 15) != 0 || (bytes & 15) != 0 || bytes == 0) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// A pass's CTAs start in index order, about two per SM at a time: the CTA PF_AHEAD indices on
+// starts roughly when this one ends, so this one prefetches that CTA's input into L2.
+constexpr int PF_AHEAD = 2 * 152;
+
 template <int L, int R, int DIR>
 __device__ __forceinline__ void stage_twiddles(float2* v, const float2* __restrict__ tw, int k,
                                                int tstep) {
@@ -378,6 +390,12 @@ __global__ void __launch_bounds__(FftCfg<LEN, op_pts<LEN, Op>()>::NT,
   extern __shared__ float2 smem[];
   const int nseq = op.nseq();
   const int seq0 = (Op::SEQ_Y ? blockIdx.y : blockIdx.x) * B;
+  if constexpr (Op::PREFETCH) {
+    // SEQ_Y passes start the CTAs of all images of one sequence block together
+    const int ahead = Op::SEQ_Y ? (PF_AHEAD + (int)gridDim.x - 1) / (int)gridDim.x : PF_AHEAD;
+    if (threadIdx.x < B && seq0 + ahead * B + (int)threadIdx.x < nseq)
+      op.prefetch(seq0 + ahead * B + threadIdx.x);
+  }
   float2 r[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
@@ -504,6 +522,8 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB)
   float* acc = reinterpret_cast<float*>(smem + B * LP);  // [B][L / 2]
   const int nseq = op.nseq(), ntr = op.ntrans();
   const int seq0 = blockIdx.x * B;
+  if (threadIdx.x < B && seq0 + PF_AHEAD * B + (int)threadIdx.x < nseq)
+    op.prefetch(seq0 + PF_AHEAD * B + threadIdx.x);
   for_direct_outputs<L, 16>([&](int b, int i) {
     const int o = op.out_of(i);
     if (o >= 0) acc[b * HALF + o] = 0.f;
@@ -642,7 +662,11 @@ struct OpBase {
   template <int B, int NT, int L, int LP>
   __device__ void mid(float2*, int) const {}
   __device__ void finish(int, double) const {}
+  // ops with PREFETCH provide void prefetch(int seq): L2 prefetches of that sequence's input
+  static constexpr bool PREFETCH = false;
+  __device__ void prefetch(int) const {}
 };
+
 
 // Dispatch a templated functor (templated on the length) on a runtime log2 length in [5, 14].
 #define FR_LOG2_DISPATCH(log2l, F, ...)                      \

@@ -30,6 +30,15 @@ struct D1StackOp : OpBase {
   static constexpr bool TRANSPOSED = true;
   static constexpr bool GROUP = true;
   static constexpr bool SEQ_Y = true;  // blockIdx.x = plane of the batch
+  static constexpr bool PREFETCH = true;
+  __device__ void prefetch(int jx) const {
+    if (blockIdx.x != 0) return;  // the row is shared by the batch's planes
+    const size_t o = (size_t)jx * ny;
+    const uint32_t b = (uint32_t)ny * 4;
+    l2_prefetch(sky + o, b);
+    l2_prefetch(corr + o, b);
+    l2_prefetch(tq + o, b);
+  }
   const float* sky;
   const float* corr;
   const int32_t* tq;
@@ -69,6 +78,10 @@ struct D1StackOp : OpBase {
 };
 
 struct D2SparseOp : OpBase {
+  static constexpr bool PREFETCH = true;
+  __device__ void prefetch(int q) const {
+    l2_prefetch(b1t + (size_t)q * nx, (uint32_t)nx * sizeof(float2));
+  }
   const float2* b1t;  // [nrows * TILE][nx]
   float2* grid;       // [Nv][Nu]
   const int* rows;
@@ -151,6 +164,12 @@ struct G2StackOp {
   __host__ __device__ int nseq() const { return nx; }
   __host__ __device__ int nout() const { return ny; }
   __device__ int ntrans() const { return nt; }
+  __device__ void prefetch(int jx) const {
+#pragma unroll
+    for (int k = 0; k < STACK_K; ++k)
+      if (k < nt && ncomp[k] > 0)
+        l2_prefetch(b1[k] + (size_t)jx * ncomp[k], (uint32_t)ncomp[k] * sizeof(float2));
+  }
   __device__ Trans trans(int t) const {
     return Trans{pick_static(b1, t), pick_static(comp, t), pick_static(ncomp, t),
                  pick_static(k64, t)};
