@@ -522,8 +522,10 @@ __global__ void __launch_bounds__(FftCfg<LEN>::NT, FftCfg<LEN>::MINB)
   float* acc = reinterpret_cast<float*>(smem + B * LP);  // [B][L / 2]
   const int nseq = op.nseq(), ntr = op.ntrans();
   const int seq0 = blockIdx.x * B;
-  if (threadIdx.x < B && seq0 + PF_AHEAD * B + (int)threadIdx.x < nseq)
-    op.prefetch(seq0 + PF_AHEAD * B + threadIdx.x);
+  if constexpr (Op::PREFETCH) {
+    if (threadIdx.x < B && seq0 + PF_AHEAD * B + (int)threadIdx.x < nseq)
+      op.prefetch(seq0 + PF_AHEAD * B + threadIdx.x);
+  }
   for_direct_outputs<L, 16>([&](int b, int i) {
     const int o = op.out_of(i);
     if (o >= 0) acc[b * HALF + o] = 0.f;

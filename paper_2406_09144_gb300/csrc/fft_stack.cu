@@ -164,12 +164,10 @@ struct G2StackOp {
   __host__ __device__ int nseq() const { return nx; }
   __host__ __device__ int nout() const { return ny; }
   __device__ int ntrans() const { return nt; }
-  __device__ void prefetch(int jx) const {
-#pragma unroll
-    for (int k = 0; k < STACK_K; ++k)
-      if (k < nt && ncomp[k] > 0)
-        l2_prefetch(b1[k] + (size_t)jx * ncomp[k], (uint32_t)ncomp[k] * sizeof(float2));
-  }
+  // no L2 prefetch: a wave ahead of this pass is 8 planes' rows for 304 CTAs (about 66 MB),
+  // which measured as evicted before use (DRAM reads 1.24 -> 2.11 GB per launch)
+  static constexpr bool PREFETCH = false;
+  __device__ void prefetch(int) const {}
   __device__ Trans trans(int t) const {
     return Trans{pick_static(b1, t), pick_static(comp, t), pick_static(ncomp, t),
                  pick_static(k64, t)};
