@@ -128,11 +128,15 @@ struct G1SparseOp : OpBase {
   }
   __device__ void after_load(int seq0, int nb) const {
     // the gridder wrote only the occupied tiles: zeroing them restores an all-zero grid
-    const int n = nb * Nu;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int r = i / Nu, u = i - (i / Nu) * Nu;
+    // (row index and tile-row bitmap hoisted per sequence; the unrolled loop issues its bitmap
+    // loads independently)
+    for (int r = 0; r < nb; ++r) {
       const int v = compact_row_v(rows, seq0 + r);
-      if (tile_on(bits, ntw, v, u)) grid[(size_t)v * Nu + u] = make_float2(0.f, 0.f);
+      const uint32_t* rb = bits + (v / TILE) * ntw;
+      float2* row = grid + (size_t)v * Nu;
+#pragma unroll 4
+      for (int u = threadIdx.x; u < Nu; u += blockDim.x)
+        if ((__ldg(&rb[u / (32 * TILE)]) >> ((u / TILE) & 31)) & 1u) row[u] = make_float2(0.f, 0.f);
     }
   }
   __device__ double store(int q, int o, SeqView s) const {
