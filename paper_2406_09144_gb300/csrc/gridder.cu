@@ -1288,8 +1288,9 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
   const int4 it = items[blockIdx.x];
   const int tu = it.z >> 16, tv = it.z & 0xffff;
   const int n = it.y;
-  // each warp takes a contiguous segment of the sorted order, a multiple of 32 long
-  const int seg = (((n + GRID_WARPS - 1) / GRID_WARPS) + 31) & ~31;
+  // each warp takes a contiguous segment of the sorted order, the item split evenly (a w-plane's
+  // items average about 135 visibilities: segments of 32 would leave three warps idle)
+  const int seg = (n + GRID_WARPS - 1) / GRID_WARPS;
   if constexpr (DET) {
     for (int i = threadIdx.x; i < SUB; i += NT) subq[i] = longlong2{0, 0};
   } else {
@@ -1390,8 +1391,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) grid_kernel(const int4* __res
             accq[k].x += to_fixed_f(wgt * v.x, scalef);
             accq[k].y += to_fixed_f(wgt * v.y, scalef);
           } else {
-            acc[k].x = fmaf(wgt, v.x, acc[k].x);
-            acc[k].y = fmaf(wgt, v.y, acc[k].y);
+            acc[k] = ffma2(make_float2(wgt, wgt), v, acc[k]);
           }
         }
       }
