@@ -19,11 +19,13 @@ namespace fr {
 //      Re(Z_k exp(+2 pi i w_k (t - t_c))) are summed per pixel in registers and written once.
 // Cells outside the occupied tiles are never read by the degridder of that plane (its
 // footprints lie inside them) and never written by its gridder, so all of this is exact.
+// (grid and sequence indices are non-negative: unsigned shifts, not signed divisions)
+__device__ __forceinline__ unsigned tdiv(int x) { return (unsigned)x / TILE; }
 __device__ __forceinline__ bool tile_on(const uint32_t* bits, int ntw, int v, int u) {
-  return (__ldg(&bits[(v / TILE) * ntw + (u / TILE) / 32]) >> ((u / TILE) & 31)) & 1u;
+  return (__ldg(&bits[tdiv(v) * ntw + tdiv(u) / 32]) >> (tdiv(u) & 31)) & 1u;
 }
 __device__ __forceinline__ int compact_row_v(const int* rows, int o) {
-  return __ldg(&rows[o / TILE]) * TILE + (o & (TILE - 1));
+  return __ldg(&rows[tdiv(o)]) * TILE + (o & (TILE - 1));
 }
 
 struct D1StackOp : OpBase {
@@ -132,11 +134,11 @@ struct G1SparseOp : OpBase {
     // loads independently)
     for (int r = 0; r < nb; ++r) {
       const int v = compact_row_v(rows, seq0 + r);
-      const uint32_t* rb = bits + (v / TILE) * ntw;
+      const uint32_t* rb = bits + tdiv(v) * ntw;
       float2* row = grid + (size_t)v * Nu;
 #pragma unroll 4
       for (int u = threadIdx.x; u < Nu; u += blockDim.x)
-        if ((__ldg(&rb[u / (32 * TILE)]) >> ((u / TILE) & 31)) & 1u) row[u] = make_float2(0.f, 0.f);
+        if ((__ldg(&rb[tdiv(u) / 32]) >> (tdiv(u) & 31)) & 1u) row[u] = make_float2(0.f, 0.f);
     }
   }
   __device__ double store(int q, int o, SeqView s) const {
@@ -177,7 +179,7 @@ struct G2StackOp {
                  pick_static(k64, t)};
   }
   __device__ float2 load(const Trans& p, int jx, int v) const {
-    const int c = __ldg(&p.comp[v / TILE]);
+    const int c = __ldg(&p.comp[tdiv(v)]);
     if (c < 0) return make_float2(0.f, 0.f);
     return p.b1[(size_t)jx * p.ncomp + c * TILE + (v & (TILE - 1))];
   }
