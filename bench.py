@@ -582,7 +582,7 @@ def main():
             tg += e[1].elapsed_time(e[2])
             tp += e[2].elapsed_time(e[3])
         k = args.steps
-        tab2 = {"workload": "MeerKAT-like top channel (1712 MHz, 7,257,600 visibilities, w-terms) "
+        tab2 = {"workload": "MeerKAT-like top channel (1658.5 MHz, 7,257,600 visibilities, w-terms) "
                             "imaged at 3600^2 pixels of 2 arcsec (Tab. 2's field)",
                 "grid": [i3["grid_nu"], i3["grid_nv"]], "psf_padding": list(p3.psf_padding),
                 "wplanes_total": i3["wplanes_total"], "plan_s": p3_s,
